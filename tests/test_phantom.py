@@ -1,0 +1,70 @@
+"""The seeded input generator: shapes, determinism and the stated D kernel."""
+import math
+
+import numpy as np
+
+from paper_0908_4421_gb300 import phantom
+
+
+def test_tiny_shapes_and_structures(tiny_case):
+    c = tiny_case
+    assert c.m == 23760 and c.n == 432          # 40x40x30 grid at 5 mm, 5 beams, 5 mm beamlets
+    assert c.row_ptr[0] == 0 and np.all(np.diff(c.row_ptr) >= 0)
+    assert c.col.dtype == np.int32 and c.val.dtype == np.float32
+    counts = [int(((c.mask >> b) & 1).sum()) for b in range(4)]
+    assert counts[3] == c.m                      # every row is a body voxel
+    assert all(k > 0 for k in counts)
+    assert c.n_structures == 4
+
+
+def test_rows_sorted_and_cut(tiny_case):
+    c = tiny_case
+    assert np.all(c.val >= np.float32(c.spec.cutoff * (1 - 1e-7)))
+    assert np.all(c.val <= 1.0)
+    for j in range(0, c.m, 97):
+        cols = c.col[c.row_ptr[j]:c.row_ptr[j + 1]]
+        assert np.all(np.diff(cols) > 0)
+    assert c.col.min() >= 0 and c.col.max() < c.n
+
+
+def test_kernel_formula_spot_check(tiny_case):
+    """D_ij = exp(-mu depth) exp(-rho^2 / (2 sigma^2)) at a few entries, recomputed from the geometry."""
+    c, s = tiny_case, tiny_case.spec
+    rng = np.random.Generator(np.random.PCG64(0))
+    for k in rng.choice(c.nnz, size=50, replace=False):
+        j = int(np.searchsorted(c.row_ptr, k, side="right") - 1)
+        i = int(c.col[k])
+        x, y, z = map(float, c.voxels[j])
+        b, uc, vc = map(float, c.beamlets[i])
+        th = math.radians(s.angle0_deg + 360.0 * int(b) / s.n_beams)
+        u = x * math.cos(th) - y * math.sin(th)
+        dx, dy = -math.sin(th), -math.cos(th)
+        # entry point: largest t with (x - t dx, y - t dy) on the ellipse
+        a2, b2 = s.body_axes[0] ** 2, s.body_axes[1] ** 2
+        A = dx * dx / a2 + dy * dy / b2
+        B = x * dx / a2 + y * dy / b2
+        C = x * x / a2 + y * y / b2 - 1
+        t = (B + math.sqrt(max(0.0, B * B - A * C))) / A
+        expect = math.exp(-s.mu_per_mm * t) * math.exp(-((u - uc) ** 2 + (z - vc) ** 2) / (2 * s.sigma_mm ** 2))
+        assert abs(float(c.val[k]) - expect) <= 6e-8 * expect  # FP32 rounding of the stored value
+
+
+def test_deterministic():
+    a = phantom.make_case(phantom.TINY_5MM_5BEAM)
+    b = phantom.make_case(phantom.TINY_5MM_5BEAM)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val, b.val) and np.array_equal(a.mask, b.mask)
+
+
+def test_jitter_is_seeded():
+    s1 = phantom.jittered_spec(3, shift_mm=5.0)
+    s2 = phantom.jittered_spec(3, shift_mm=5.0)
+    s3 = phantom.jittered_spec(4, shift_mm=5.0)
+    assert s1 == s2 and s1 != s3
+    assert s1.spacing in (2.5, 4.0, 5.0) and s1.n_beams in (5, 7, 9) and s1.beamlet_mm in (5.0, 10.0)
+
+
+def test_random_case_ragged():
+    c = phantom.random_case(0, m=50, n=9, density=0.2, empty_rows=5, long_rows=3)
+    lens = np.diff(c.row_ptr)
+    assert (lens == 0).sum() >= 5 and (lens == 9).sum() >= 3
