@@ -1,0 +1,225 @@
+/*
+ * imrt.h -- C ABI of the GB300 fluence-map optimiser.
+ *
+ * Method: Men et al., "GPU-based ultra fast IMRT plan optimization"
+ * (arXiv:0908.4421).
+ *   Sec. 2.1, Eq. (1)-(2): minimise G(x) = sum_j F_j(z_j), z = D x, x >= 0,
+ *       F_j the sum of one-sided quadratic penalties of every structure that
+ *       contains voxel j: c * max(0, T_under - z)^2 (under-dose term) and
+ *       c * max(0, z - T_over)^2 (over-dose term), c = w / |V_s|.
+ *   Sec. 2.2, Eq. (3)-(5), steps 1-5: gradient projection
+ *       x_{k+1} = max(0, x_k - lambda grad G(x_k)) with Armijo's rule: lambda
+ *       starts at lambda0 every iteration and is divided by alpha until
+ *       G(x_{k+1}) < G(x_k) - (eps / lambda) ||x_{k+1} - x_k||^2; stop when
+ *       |G_new - G_old| / G_new < delta.
+ *   Sec. 2.3: the dose z = D x (one voxel per row), the objective reduction,
+ *       the gradient D^T r (one beamlet per row) and the fluence update run
+ *       as GPU kernels; D is stored as CSR.
+ *
+ * All arithmetic of the solve runs in CUDA kernels (sm_103a). The host only
+ * validates inputs, plans the data layout, and launches work.
+ *
+ * Conventions shared by every entry point:
+ *   - Status: every function returns an imrt_status; on failure
+ *     imrt_last_error() returns a message (thread-local, valid until the next
+ *     call on the same thread). No function throws across the ABI.
+ *   - Pointers: "host or device" arguments are classified with
+ *     cudaPointerGetAttributes; host memory may be pageable or pinned.
+ *   - Streams: work is enqueued on imrt_options.stream (a cudaStream_t; NULL
+ *     means the legacy default stream). Every call returns after its work on
+ *     that stream has finished.
+ *   - Threads: one thread at a time per plan; distinct plans are independent.
+ *   - Voxel order: every voxel array at the ABI (structures, z_out) is in the
+ *     caller's row order of D. Beamlet arrays (x0, x_out, g_out) follow D's
+ *     column order.
+ */
+#ifndef IMRT_H
+#define IMRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct imrt_plan imrt_plan; /* opaque; owns all of its device memory */
+
+typedef enum {
+    IMRT_OK = 0,
+    IMRT_EINVAL = 1,       /* malformed argument (sizes, CSR structure, options) */
+    IMRT_ENOMEM = 2,       /* a device or pinned-host allocation failed */
+    IMRT_ECUDA = 3,        /* a CUDA runtime call failed */
+    IMRT_ELINESEARCH = 4,  /* more than max_backtracks halvings in one iteration */
+    IMRT_ENUMERIC = 5,     /* a non-finite dose or objective appeared */
+    IMRT_ETIMEOUT = 6,     /* the solve ran past imrt_options.timeout_ms */
+    IMRT_ECANCELLED = 7,   /* plan_cancel() was called during the solve */
+    IMRT_EUNSUPPORTED = 8  /* valid request this build does not support (size limits) */
+} imrt_status;
+
+typedef enum {
+    IMRT_STOP_NONE = 0,
+    IMRT_STOP_REL = 1,        /* relative objective change below delta (Sec. 2.2, step 5) */
+    IMRT_STOP_MAXITER = 2,    /* max_iter accepted steps */
+    IMRT_STOP_EXACT = 3,      /* G reached exactly 0 */
+    IMRT_STOP_STATIONARY = 4  /* the projected step had zero length: x is stationary */
+} imrt_stop;
+
+typedef enum {
+    IMRT_FP32 = 0,    /* FP32 values, int32 indices (the paper's CSR precision, Sec. 3.2) */
+    IMRT_FP16 = 1,    /* FP16 values scaled per beamlet (FP32 scale), 16-bit beamlet indices */
+    IMRT_BF16 = 2,    /* BF16 values scaled per beamlet */
+    IMRT_FP8E4M3 = 3  /* FP8 e4m3 values scaled per beamlet */
+} imrt_precision;
+
+typedef enum {
+    IMRT_MODE_GRAPH = 0, /* whole solve as one CUDA graph; Armijo control on the device */
+    IMRT_MODE_HOST = 1   /* host loop, one status read-back per Armijo trial */
+} imrt_mode;
+
+/* Voxel-major D (rows = voxels, columns = beamlets), CSR (Sec. 2.3). */
+typedef struct {
+    int32_t m;               /* voxels (rows), >= 1 */
+    int32_t n;               /* beamlets (columns), >= 1 */
+    int64_t nnz;             /* row_ptr[m] */
+    const int64_t* row_ptr;  /* m + 1 offsets, row_ptr[0] = 0, non-decreasing */
+    const int32_t* col_idx;  /* nnz beamlet indices in [0, n), strictly increasing within a row */
+    const float* val;        /* nnz dose-deposition coefficients D_ij (finite) */
+    int32_t on_device;       /* 1: the three arrays are device pointers; 0: host */
+} imrt_csr;
+
+typedef struct {
+    double eps;             /* Armijo parameter epsilon in (0, 1) (Eq. (5)); default 1e-4 */
+    double alpha;           /* step divisor alpha > 1 (Sec. 2.2, step 4); default 2 */
+    double lambda0;         /* initial step (Sec. 2.2, step 2); <= 0 selects 8 / L, L = 2 lambda_max(D^T C D) */
+    double delta;           /* relative-change stop tolerance (step 5); default 1e-6 */
+    int32_t max_iter;       /* accepted-step cap; default 200 */
+    int32_t max_backtracks; /* halvings allowed per iteration; default 50 */
+    int32_t x_init;         /* 0: s * ones with mean PTV dose = T_under; 1: zeros; 2: x0 argument */
+    int32_t precision;      /* imrt_precision of the stored D; default IMRT_FP32 */
+    int32_t k_trials;       /* Armijo step sizes evaluated per pass over D: 1, 2, 4 or 8; default 1 */
+    int32_t mode;           /* imrt_mode; default IMRT_MODE_GRAPH */
+    int32_t profile;        /* 1: time every forward and transposed-product launch with CUDA events */
+    int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
+    int32_t polish_iter;    /* reduced precision: FP32-D iterations after the first stop; default 50 */
+    int32_t reserved;
+    double timeout_ms;      /* 0: none; else the device loop stops with IMRT_ETIMEOUT */
+    void* stream;           /* cudaStream_t */
+} imrt_options;
+
+typedef struct {
+    int32_t status;            /* imrt_status of the solve */
+    int32_t stop_reason;       /* imrt_stop */
+    int32_t iterations;        /* accepted steps */
+    int32_t backtracks;        /* rejected trials, summed over iterations */
+    int32_t passes;            /* forward passes over D (each evaluates k_trials step sizes) */
+    int32_t grad_passes;       /* transposed passes over D */
+    int32_t launches;          /* kernels launched by the solve */
+    int32_t polish_iterations; /* FP32-D iterations after a reduced-precision solve */
+    double objective;          /* G at the returned x */
+    double initial_objective;  /* G(x_1) */
+    double kkt;                /* ||x - max(0, x - g)||_inf / max(1, ||g(x_1)||_inf) */
+    double rel_change;         /* last |G_new - G_old| / G_new */
+    double lambda0;            /* the initial step used */
+    double ms;                 /* host wall time of plan_solve */
+    double fwd_ms;             /* profile: summed forward-pass kernel time (CUDA events) */
+    double bwd_ms;             /* profile: summed transposed-pass kernel time */
+    int32_t fwd_launches;      /* profile: timed forward launches */
+    int32_t bwd_launches;      /* profile: timed transposed launches */
+} imrt_result;
+
+typedef struct {
+    int32_t m, n, n_structures, n_slices;
+    int64_t nnz;
+    int64_t sell_entries;      /* stored (padded) entries of the voxel-major copy */
+    int64_t t_entries;         /* stored (padded) entries of the beamlet-major copy */
+    int64_t fwd_bytes;         /* algorithmic bytes of one forward pass (CSR-equivalent) */
+    int64_t bwd_bytes;         /* algorithmic bytes of one transposed pass */
+    int64_t device_bytes;      /* device memory held by the plan */
+    int32_t fwd_grid, fwd_block, bwd_grid, bwd_block;
+    int32_t precision, k_trials;
+    double lambda0_rule;       /* 8 / L from the power iteration (computed at plan_create) */
+    double x1_scale;           /* s of the x_init = 0 rule */
+} imrt_plan_info;
+
+/* Fills *opt with the defaults listed above. */
+void imrt_default_options(imrt_options* opt);
+
+/*
+ * Builds a plan: copies D into plan-owned device memory in two layouts (a
+ * voxel-major SELL-32-sigma copy for z = D x and a beamlet-major copy for
+ * D^T r), the structure masks, the term coefficients c = w / |V_s| (Eq. (1)),
+ * the lambda0 rule and the x_init = 0 scale.
+ *   D           voxel-major CSR (host or device, see imrt_csr.on_device).
+ *   structures  m bytes (host or device): bit s set => voxel in structure s.
+ *   n_structures 1..8.
+ *   thresholds  host, [n_structures][2] = (T_under, T_over) in Gy; NaN => no term.
+ *   weights     host, [n_structures][2] = (w_under, w_over) >= 0; 0 => no term.
+ *   opt         options (NULL => defaults); copied into the plan.
+ *   out         receives the plan; NULL on failure.
+ * The caller may free every input when this returns.
+ * Errors: IMRT_EINVAL (bad sizes or CSR structure, bad options),
+ * IMRT_EUNSUPPORTED (n above the shared-memory limit), IMRT_ENOMEM, IMRT_ECUDA.
+ */
+imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
+                        const float* thresholds, const float* weights, const imrt_options* opt,
+                        imrt_plan** out);
+
+/* Replaces the plan's options (the stream, step parameters, mode, trace...). */
+imrt_status plan_set_options(imrt_plan* plan, const imrt_options* opt);
+
+/*
+ * Runs the projected-gradient Armijo loop (Sec. 2.2, steps 1-5) from x_1.
+ *   x0   n beamlet intensities (host or device), read only when x_init = 2;
+ *        must be >= 0. May be NULL otherwise.
+ *   res  receives the result (host pointer, required).
+ * Returns res->status. On IMRT_ELINESEARCH, ETIMEOUT or ECANCELLED the plan
+ * keeps the last accepted x (plan_get_x).
+ */
+imrt_status plan_solve(imrt_plan* plan, const float* x0, imrt_result* res);
+
+/* z = D x (Sec. 2.1). x: n (host or device), NULL => the plan's current x. z_out: m (host or device). */
+imrt_status plan_dose(imrt_plan* plan, const float* x, float* z_out);
+
+/*
+ * One evaluation at x (Eq. (1)-(4)): G in FP64 (host pointer), and optionally
+ * z (m) and g = grad G = D^T r (n), host or device pointers, NULL to skip.
+ * x: n (host or device), NULL => the plan's current x.
+ */
+imrt_status plan_eval(imrt_plan* plan, const float* x, double* G, float* z_out, float* g_out);
+
+/* Copies the plan's current x (n floats) to x_out (host or device). */
+imrt_status plan_get_x(imrt_plan* plan, float* x_out);
+
+/*
+ * Copies the last solve's trace (requires imrt_options.trace >= 1).
+ * G: iterations + 1 doubles; lambda: iterations doubles; backtracks:
+ * iterations int32; xs: (iterations + 1) * n floats (trace = 2 only).
+ * All host pointers; any may be NULL. cap bounds the iterations copied.
+ */
+imrt_status plan_get_trace(imrt_plan* plan, int32_t cap, double* G, double* lambda, int32_t* backtracks,
+                           float* xs);
+
+/* Sizes, layouts, launch shapes and per-pass algorithmic bytes. */
+imrt_status plan_info(const imrt_plan* plan, imrt_plan_info* info);
+
+/*
+ * Asks a running solve on another thread to stop (IMRT_ECANCELLED). The flag
+ * lives in mapped pinned host memory that the device controller polls once
+ * per Armijo trial; plan_solve clears it on entry.
+ */
+imrt_status plan_cancel(imrt_plan* plan);
+
+/* Frees the plan and all its device memory. NULL-safe. */
+void plan_destroy(imrt_plan* plan);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* imrt_last_error(void);
+
+/* Library version string, e.g. "imrt-gb300 1.0 sm_103a". */
+const char* imrt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMRT_H */

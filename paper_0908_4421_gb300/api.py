@@ -1,0 +1,202 @@
+"""Python binding of the C ABI: a thin ``Plan`` wrapper (argument marshalling only).
+
+Every step of the solve runs in libimrt's CUDA kernels; this module converts
+numpy arrays or torch CUDA tensors into pointers, fills the option structure,
+and turns status codes into exceptions. torch is used only for device buffers
+and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+from . import _lib as L
+
+
+@dataclasses.dataclass
+class Options:
+    """Mirror of imrt_options (defaults = imrt_default_options)."""
+
+    eps: float = 1e-4
+    alpha: float = 2.0
+    lambda0: float = 0.0
+    delta: float = 1e-6
+    max_iter: int = 200
+    max_backtracks: int = 50
+    x_init: int = 0
+    precision: int = L.FP32
+    k_trials: int = 1
+    mode: int = L.MODE_GRAPH
+    profile: int = 0
+    trace: int = 0
+    polish_iter: int = 50
+    timeout_ms: float = 0.0
+    stream: int = 0  # cudaStream_t as an integer; 0 = legacy default stream
+
+    def to_c(self) -> L.imrt_options:
+        o = L.imrt_options()
+        for f in dataclasses.fields(self):
+            setattr(o, f.name, getattr(self, f.name))
+        return o
+
+
+@dataclasses.dataclass
+class Result:
+    status: int
+    stop_reason: int
+    iterations: int
+    backtracks: int
+    passes: int
+    grad_passes: int
+    launches: int
+    polish_iterations: int
+    objective: float
+    initial_objective: float
+    kkt: float
+    rel_change: float
+    lambda0: float
+    ms: float
+    fwd_ms: float
+    bwd_ms: float
+    fwd_launches: int
+    bwd_launches: int
+
+    @classmethod
+    def from_c(cls, r: L.imrt_result) -> "Result":
+        return cls(**{f.name: getattr(r, f.name) for f in dataclasses.fields(cls)})
+
+
+def _ptr(a) -> int:
+    """Data pointer of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    return int(a.ctypes.data)
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+class Plan:
+    """One planning problem resident on the GPU (plan_create / plan_destroy)."""
+
+    def __init__(self, row_ptr, col, val, mask, thresholds, weights, m: Optional[int] = None,
+                 n: Optional[int] = None, options: Optional[Options] = None):
+        lib = L.load()
+        self._lib = lib
+        self.options = options or Options()
+        on_device = _is_torch_cuda(val)
+        if not on_device:
+            row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+            col = np.ascontiguousarray(col, np.int32)
+            val = np.ascontiguousarray(val, np.float32)
+        if not _is_torch_cuda(mask):
+            mask = np.ascontiguousarray(mask, np.uint8)
+        thr = np.ascontiguousarray(thresholds, np.float32)
+        w = np.ascontiguousarray(weights, np.float32)
+        m = int(m if m is not None else row_ptr.shape[0] - 1)
+        nnz = int(col.shape[0])
+        if n is None:
+            raise ValueError("n (number of beamlets) is required")
+        csr = L.imrt_csr(m, int(n), nnz, _ptr(row_ptr), _ptr(col), _ptr(val), 1 if on_device else 0)
+        handle = ctypes.c_void_p()
+        opts = self.options.to_c()
+        L.check(lib.plan_create(ctypes.byref(csr), _ptr(mask), thr.shape[0], _ptr(thr), _ptr(w),
+                                ctypes.byref(opts), ctypes.byref(handle)))
+        self._h = handle
+        self.m, self.n = m, int(n)
+
+    @classmethod
+    def from_case(cls, case, options: Optional[Options] = None, device: bool = False) -> "Plan":
+        """From a phantom.Case; with device=True the inputs go through torch CUDA tensors."""
+        if device:
+            import torch
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            return cls(t(case.row_ptr), t(case.col), t(case.val), t(case.mask), case.thresholds, case.weights,
+                       m=case.m, n=case.n, options=options)
+        return cls(case.row_ptr, case.col, case.val, case.mask, case.thresholds, case.weights, m=case.m,
+                   n=case.n, options=options)
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -------------------------------------------------------------
+    def set_options(self, **changes) -> None:
+        self.options = dataclasses.replace(self.options, **changes)
+        opts = self.options.to_c()
+        L.check(self._lib.plan_set_options(self._h, ctypes.byref(opts)))
+
+    def solve(self, x0=None, raise_on_error: bool = True) -> Result:
+        """plan_solve; x0 (host array or CUDA tensor) is read when x_init = 2."""
+        if x0 is not None and not _is_torch_cuda(x0):
+            x0 = np.ascontiguousarray(x0, np.float32)
+        res = L.imrt_result()
+        st = self._lib.plan_solve(self._h, _ptr(x0), ctypes.byref(res))
+        if raise_on_error and st not in (L.IMRT_OK,):
+            L.check(st)
+        return Result.from_c(res)
+
+    def dose(self, x=None, out=None):
+        """z = D x (m floats) into `out` (numpy or CUDA tensor) or a new numpy array."""
+        if x is not None and not _is_torch_cuda(x):
+            x = np.ascontiguousarray(x, np.float32)
+        if out is None:
+            out = np.empty(self.m, np.float32)
+        L.check(self._lib.plan_dose(self._h, _ptr(x), _ptr(out)))
+        return out
+
+    def eval(self, x=None, z_out=None, g_out=None):
+        """(G, z, g) at x: FP64 objective, dose and gradient."""
+        if x is not None and not _is_torch_cuda(x):
+            x = np.ascontiguousarray(x, np.float32)
+        z_out = np.empty(self.m, np.float32) if z_out is None else z_out
+        g_out = np.empty(self.n, np.float32) if g_out is None else g_out
+        G = ctypes.c_double()
+        L.check(self._lib.plan_eval(self._h, _ptr(x), ctypes.addressof(G), _ptr(z_out), _ptr(g_out)))
+        return G.value, z_out, g_out
+
+    def get_x(self, out=None):
+        out = np.empty(self.n, np.float32) if out is None else out
+        L.check(self._lib.plan_get_x(self._h, _ptr(out)))
+        return out
+
+    def trace(self, iterations: int, with_x: bool = False):
+        """(G[k+1], lambda[k], backtracks[k], xs[k+1, n] or None) of the last solve."""
+        G = np.empty(iterations + 1, np.float64)
+        lam = np.empty(max(iterations, 1), np.float64)
+        bt = np.empty(max(iterations, 1), np.int32)
+        xs = np.empty((iterations + 1, self.n), np.float32) if with_x else None
+        L.check(self._lib.plan_get_trace(self._h, iterations, _ptr(G), _ptr(lam), _ptr(bt), _ptr(xs)))
+        return G, lam[:iterations], bt[:iterations], xs
+
+    def info(self) -> dict:
+        i = L.imrt_plan_info()
+        L.check(self._lib.plan_info(self._h, ctypes.byref(i)))
+        return {f[0]: getattr(i, f[0]) for f in L.imrt_plan_info._fields_}
+
+    def cancel(self) -> None:
+        L.check(self._lib.plan_cancel(self._h))
+
+
+def version() -> str:
+    return L.load().imrt_version().decode()

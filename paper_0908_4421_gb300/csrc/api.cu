@@ -1,0 +1,1110 @@
+// C ABI of libimrt (declared in include/imrt.h): plan construction, the
+// CUDA-graph solve loop, evaluation entry points, and error reporting.
+//
+// The host side only validates, plans layouts (warp partitions, the
+// longest-processing-time schedule of the transposed pass) and launches
+// kernels; every arithmetic step of the method runs on the device.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstddef>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <queue>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/imrt.h"
+#include "imrt_internal.cuh"
+
+using namespace imrt;
+
+namespace {
+
+thread_local std::string g_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) {                                                                          \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);        \
+            return e_ == cudaErrorMemoryAllocation ? IMRT_ENOMEM : IMRT_ECUDA;                            \
+        }                                                                                                 \
+    } while (0)
+
+#define TRY(expr)                                     \
+    do {                                              \
+        imrt_status s_ = (expr);                      \
+        if (s_ != IMRT_OK) return s_;                 \
+    } while (0)
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+size_t elem_bytes(int precision) { return precision == IMRT_FP32 ? 4 : precision == IMRT_FP8E4M3 ? 1 : 2; }
+size_t col_bytes(int precision) { return precision == IMRT_FP32 ? 4 : 2; }
+
+// One voxel-major SELL copy of D at a given storage precision.
+struct SellCopy {
+    int precision = -1;
+    int ge = 4;
+    int64_t* slice_off = nullptr;  // n_slices + 1
+    int32_t* slice_len = nullptr;  // n_slices
+    void* val = nullptr;
+    void* col = nullptr;
+    int64_t entries = 0;
+    std::vector<int64_t> host_cost;  // per slice, for warp partitions
+};
+
+// Forward launch shape for one (copy, k_trials): grid and warp -> slice partition.
+struct FwdShape {
+    int grid = 0;
+    int warps = 0;
+    int32_t* warp_slices = nullptr;
+    size_t smem = 0;
+};
+
+struct SolveGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+};
+
+}  // namespace
+
+struct imrt_plan {
+    int device = 0, sm_count = 0;
+    imrt_options opt{};
+    int32_t m = 0, n = 0, S = 0, n_pad = 0, m_pad = 0, n_slices = 0;
+    int64_t nnz = 0;
+    // voxel-major
+    int32_t* perm = nullptr;
+    uint8_t* mask = nullptr;
+    SellCopy sell32, sellq;
+    float* scale = nullptr;
+    float* inv_scale = nullptr;
+    // beamlet-major
+    int64_t* t_off = nullptr;
+    float* t_val = nullptr;
+    void* t_valq = nullptr;
+    int32_t* t_row = nullptr;
+    int64_t t_entries = 0;
+    int32_t* bwd_rows = nullptr;
+    int32_t* bwd_cta_ptr = nullptr;
+    int bwd_grid = 0;
+    // vectors and state
+    Vecs v{};
+    Terms terms{};
+    Terms* terms_dev = nullptr;
+    DevState* st = nullptr;
+    SolveParams* sp = nullptr;
+    float* x_stage = nullptr;
+    float* z_stage = nullptr;
+    float* r_stage = nullptr;
+    float* g_stage = nullptr;
+    float* zout_stage = nullptr;
+    double* dscratch = nullptr;
+    DevState* st_host = nullptr;     // pinned
+    int32_t* cancel_host = nullptr;  // mapped pinned
+    int32_t* cancel_dev = nullptr;
+    // trace
+    double* tr_G = nullptr;
+    double* tr_lam = nullptr;
+    int32_t* tr_bt = nullptr;
+    float* tr_x = nullptr;
+    int32_t tr_cap = -1;
+    int32_t tr_xcap = -1;
+    int32_t last_iterations = 0;
+    int32_t cur = 0;
+    // caches
+    std::map<std::pair<int, int>, FwdShape> shapes;
+    std::map<std::pair<int, int>, SolveGraph> graphs;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double lambda0_rule = 0.0, x1_scale = 0.0;
+    int64_t device_bytes = 0;
+    std::vector<void*> allocations;
+    int32_t wmax = 0, gmax = 0;
+};
+
+namespace {
+
+cudaStream_t stream_of(const imrt_plan* p) { return static_cast<cudaStream_t>(p->opt.stream); }
+
+template <class T>
+imrt_status dalloc(imrt_plan* p, T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? IMRT_ENOMEM : IMRT_ECUDA;
+    }
+    p->allocations.push_back(ptr);
+    p->device_bytes += (int64_t)(count * sizeof(T));
+    *out = static_cast<T*>(ptr);
+    return IMRT_OK;
+}
+
+imrt_status dalloc_bytes(imrt_plan* p, void** out, size_t bytes) {
+    uint8_t* q = nullptr;
+    TRY(dalloc(p, &q, bytes));
+    *out = q;
+    return IMRT_OK;
+}
+
+// Temporary device buffer freed at scope exit.
+struct Temp {
+    void* ptr = nullptr;
+    ~Temp() {
+        if (ptr) cudaFree(ptr);
+    }
+};
+
+template <class T>
+imrt_status talloc(Temp& t, T** out, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&t.ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("temporary cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? IMRT_ENOMEM : IMRT_ECUDA;
+    }
+    *out = static_cast<T*>(t.ptr);
+    return IMRT_OK;
+}
+
+imrt_status validate_options(const imrt_options* o) {
+    if (!(o->eps > 0.0 && o->eps < 1.0)) return set_error("eps must lie in (0, 1)"), IMRT_EINVAL;
+    if (!(o->alpha > 1.0)) return set_error("alpha must exceed 1"), IMRT_EINVAL;
+    if (!(o->delta >= 0.0)) return set_error("delta must be >= 0"), IMRT_EINVAL;
+    if (o->max_iter < 0 || o->max_backtracks < 0) return set_error("negative iteration limits"), IMRT_EINVAL;
+    if (o->x_init < 0 || o->x_init > 2) return set_error("x_init must be 0, 1 or 2"), IMRT_EINVAL;
+    if (o->precision < IMRT_FP32 || o->precision > IMRT_FP8E4M3) return set_error("unknown precision"), IMRT_EINVAL;
+    if (o->k_trials != 1 && o->k_trials != 2 && o->k_trials != 4 && o->k_trials != 8)
+        return set_error("k_trials must be 1, 2, 4 or 8"), IMRT_EINVAL;
+    if (o->mode != IMRT_MODE_GRAPH && o->mode != IMRT_MODE_HOST) return set_error("unknown mode"), IMRT_EINVAL;
+    if (o->trace < 0 || o->trace > 2) return set_error("trace must be 0, 1 or 2"), IMRT_EINVAL;
+    if (o->polish_iter < 0) return set_error("polish_iter must be >= 0"), IMRT_EINVAL;
+    if (!(o->timeout_ms >= 0.0)) return set_error("timeout_ms must be >= 0"), IMRT_EINVAL;
+    return IMRT_OK;
+}
+
+// Warp partition of the slices of one copy for a given forward grid: contiguous
+// slice ranges of near-equal cost (stored entries plus an epilogue allowance).
+imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, FwdShape* out) {
+    const void* fn = fwd_kernel(c.precision, k_trials);
+    if (!fn) return set_error("no forward kernel for precision %d, k_trials %d", c.precision, k_trials), IMRT_EINVAL;
+    const size_t smem = fwd_smem_bytes(p->n_pad, k_trials, c.precision);
+    int max_smem = 0;
+    CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    if (smem + 4096 > (size_t)max_smem)
+        return set_error("n = %d beamlets with k_trials = %d needs %zu bytes of shared memory (limit %d)", p->n,
+                         k_trials, smem, max_smem),
+               IMRT_EUNSUPPORTED;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFwdThreads, smem));
+    if (per_sm < 1) return set_error("forward kernel does not fit on an SM"), IMRT_EUNSUPPORTED;
+    per_sm = std::min(per_sm, 4);
+    out->grid = p->sm_count * per_sm;
+    out->warps = out->grid * (kFwdThreads / 32);
+    out->smem = smem;
+    const int W = out->warps;
+    std::vector<int32_t> ws(W + 1, 0);
+    const std::vector<int64_t>& cost = c.host_cost;
+    int64_t total = 0;
+    for (int64_t v : cost) total += v;
+    int64_t run = 0;
+    int s = 0;
+    for (int w = 1; w < W; ++w) {
+        const double target = (double)total * w / W;
+        while (s < p->n_slices && (double)(run + cost[s]) <= target) run += cost[s++];
+        ws[w] = s;
+    }
+    ws[W] = p->n_slices;
+    TRY(dalloc(p, &out->warp_slices, W + 1));
+    CK(cudaMemcpy(out->warp_slices, ws.data(), sizeof(int32_t) * (W + 1), cudaMemcpyHostToDevice));
+    return IMRT_OK;
+}
+
+imrt_status get_shape(imrt_plan* p, int precision, int k_trials, FwdShape** out) {
+    auto key = std::make_pair(precision, k_trials);
+    auto it = p->shapes.find(key);
+    if (it == p->shapes.end()) {
+        const SellCopy& c = precision == IMRT_FP32 ? p->sell32 : p->sellq;
+        if (c.precision != precision)
+            return set_error("plan holds no copy of D at precision %d", precision), IMRT_EINVAL;
+        FwdShape sh;
+        TRY(make_shape(p, c, k_trials, &sh));
+        it = p->shapes.emplace(key, sh).first;
+    }
+    *out = &it->second;
+    return IMRT_OK;
+}
+
+FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) {
+    FwdArgs a{};
+    a.slice_off = c.slice_off;
+    a.slice_len = c.slice_len;
+    a.val = c.val;
+    a.col = c.col;
+    a.warp_slices = sh.warp_slices;
+    a.mask = p->mask;
+    a.scale = c.precision == IMRT_FP32 ? nullptr : p->scale;
+    a.terms = p->terms_dev;
+    a.st = p->st;
+    a.sp = p->sp;
+    a.v = p->v;
+    a.m = p->m;
+    a.n = p->n;
+    a.n_pad = p->n_pad;
+    a.m_pad = p->m_pad;
+    a.mode = mode;
+    return a;
+}
+
+BwdArgs bwd_args(imrt_plan* p, int precision, int guard) {
+    BwdArgs a{};
+    a.t_off = p->t_off;
+    a.val = precision == IMRT_FP32 ? (const void*)p->t_val : p->t_valq;
+    a.row = p->t_row;
+    a.cta_rows = p->bwd_rows;
+    a.cta_ptr = p->bwd_cta_ptr;
+    a.scale = precision == IMRT_FP32 ? nullptr : p->scale;
+    a.st = p->st;
+    a.r_fixed = nullptr;
+    a.g = p->v.g;
+    a.m_pad = p->m_pad;
+    a.guard = guard;
+    return a;
+}
+
+const SellCopy& copy_of(const imrt_plan* p, int precision) {
+    return precision == IMRT_FP32 ? p->sell32 : p->sellq;
+}
+
+// Stand-alone evaluation of the forward kernel (no step): z, r (permuted) and per-warp G partials.
+imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, float* r_dst, double* G_out) {
+    FwdShape* sh = nullptr;
+    TRY(get_shape(p, IMRT_FP32, 1, &sh));
+    FwdArgs a = fwd_args(p, p->sell32, *sh, mode);
+    a.x_src = x_src;
+    a.z_dst = z_dst;
+    a.r_dst = r_dst;
+    a.gpart_dst = p->v.gpart;
+    void* args[] = {&a};
+    CK(cudaLaunchKernel(fwd_kernel(IMRT_FP32, 1), dim3(sh->grid), dim3(kFwdThreads), args, sh->smem,
+                        stream_of(p)));
+    if (G_out) CK(launch_g_objective(p->v.gpart, sh->warps, G_out, stream_of(p)));
+    return IMRT_OK;
+}
+
+imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g) {
+    BwdArgs a = bwd_args(p, IMRT_FP32, 0);
+    a.r_fixed = r;
+    a.g = g;
+    void* args[] = {&a};
+    CK(cudaLaunchKernel(bwd_fixed_kernel(IMRT_FP32), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0, stream_of(p)));
+    return IMRT_OK;
+}
+
+// Longest-processing-time assignment of beamlet rows to the transposed kernel's CTAs.
+imrt_status make_bwd_schedule(imrt_plan* p, const std::vector<int64_t>& len) {
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel(IMRT_FP32), kBwdThreads, 0));
+    per_sm = std::max(1, std::min(per_sm, 4));
+    int grid = std::min<int64_t>((int64_t)p->sm_count * per_sm, std::max<int64_t>(1, p->n));
+    std::vector<int32_t> order(p->n);
+    for (int i = 0; i < p->n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return len[a] > len[b]; });
+    using Item = std::pair<int64_t, int>;  // (load, cta), min-heap
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int b = 0; b < grid; ++b) heap.push({0, b});
+    std::vector<std::vector<int32_t>> rows(grid);
+    for (int i : order) {
+        Item it = heap.top();
+        heap.pop();
+        rows[it.second].push_back(i);
+        heap.push({it.first + len[i] + 64, it.second});
+    }
+    std::vector<int32_t> flat, ptr(grid + 1, 0);
+    flat.reserve(p->n);
+    for (int b = 0; b < grid; ++b) {
+        ptr[b] = (int32_t)flat.size();
+        flat.insert(flat.end(), rows[b].begin(), rows[b].end());
+    }
+    ptr[grid] = (int32_t)flat.size();
+    TRY(dalloc(p, &p->bwd_rows, p->n));
+    TRY(dalloc(p, &p->bwd_cta_ptr, grid + 1));
+    CK(cudaMemcpy(p->bwd_rows, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->bwd_cta_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice));
+    p->bwd_grid = grid;
+    return IMRT_OK;
+}
+
+// Builds one SELL copy of D (precision != FP32 uses the per-beamlet inverse scales).
+imrt_status build_sell(imrt_plan* p, SellCopy* c, int precision, const int64_t* row_ptr, const int32_t* col,
+                       const float* val, const int32_t* len, const uint8_t* mask_in, cudaStream_t s) {
+    c->precision = precision;
+    c->ge = fwd_group_entries(precision);
+    TRY(dalloc(p, &c->slice_len, p->n_slices));
+    TRY(dalloc(p, &c->slice_off, p->n_slices + 1));
+    Temp tent;
+    int64_t* entries = nullptr;
+    TRY(talloc(tent, &entries, p->n_slices));
+    CK(launch_slice_sizes(len, p->perm, p->m, p->n_slices, c->ge, c->slice_len, entries, s));
+    CK(launch_scan_i64(entries, c->slice_off, p->n_slices, s));
+    CK(cudaMemcpyAsync(&c->entries, c->slice_off + p->n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> sl(p->n_slices);
+    CK(cudaMemcpyAsync(sl.data(), c->slice_len, sizeof(int32_t) * p->n_slices, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->host_cost.resize(p->n_slices);
+    for (int i = 0; i < p->n_slices; ++i) c->host_cost[i] = (int64_t)sl[i] * kSlice * c->ge + 8 * kSlice;
+    TRY(dalloc_bytes(p, &c->val, (size_t)c->entries * elem_bytes(precision) + 64));
+    TRY(dalloc_bytes(p, &c->col, (size_t)c->entries * col_bytes(precision) + 64));
+    uint8_t* mask_out = precision == IMRT_FP32 ? p->mask : nullptr;
+    Temp tmask;
+    if (!mask_out) TRY(talloc(tmask, &mask_out, p->m_pad));
+    CK(launch_sell_fill(precision, row_ptr, col, val, p->perm, mask_in, p->m, p->m_pad, c->slice_off, c->slice_len,
+                        precision == IMRT_FP32 ? nullptr : p->inv_scale, c->val, c->col, mask_out, s));
+    CK(cudaStreamSynchronize(s));
+    return IMRT_OK;
+}
+
+imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structures, const float* thresholds,
+                       const float* weights) {
+    cudaStream_t s = stream_of(p);
+    const int32_t m = D->m, n = D->n;
+    const int64_t nnz = D->nnz;
+    // --- D on the device ---------------------------------------------------
+    Temp trp, tcol, tval, tmaskin;
+    const int64_t* row_ptr = D->row_ptr;
+    const int32_t* col = D->col_idx;
+    const float* val = D->val;
+    int64_t first = 0, last = 0;
+    if (!D->on_device) {
+        if (D->row_ptr[0] != 0 || D->row_ptr[m] != nnz)
+            return set_error("row_ptr[0] must be 0 and row_ptr[m] must equal nnz"), IMRT_EINVAL;
+        int64_t* drp;
+        int32_t* dcol;
+        float* dval;
+        TRY(talloc(trp, &drp, m + 1));
+        TRY(talloc(tcol, &dcol, nnz));
+        TRY(talloc(tval, &dval, nnz));
+        CK(cudaMemcpyAsync(drp, D->row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
+        if (nnz) {
+            CK(cudaMemcpyAsync(dcol, D->col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(dval, D->val, sizeof(float) * nnz, cudaMemcpyHostToDevice, s));
+        }
+        row_ptr = drp;
+        col = dcol;
+        val = dval;
+    } else {
+        CK(cudaMemcpyAsync(&first, row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&last, row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (first != 0 || last != nnz)
+            return set_error("row_ptr[0] must be 0 and row_ptr[m] must equal nnz"), IMRT_EINVAL;
+    }
+    const uint8_t* mask_in = structures;
+    if (!is_device_ptr(structures)) {
+        uint8_t* dm;
+        TRY(talloc(tmaskin, &dm, m));
+        CK(cudaMemcpyAsync(dm, structures, m, cudaMemcpyHostToDevice, s));
+        mask_in = dm;
+    }
+    // --- validation and row lengths ----------------------------------------
+    Temp tlen, tflags;
+    int32_t* len;
+    int32_t* flags;
+    TRY(talloc(tlen, &len, m));
+    TRY(talloc(tflags, &flags, 1));
+    CK(cudaMemsetAsync(flags, 0, sizeof(int32_t), s));
+    CK(launch_row_check(row_ptr, col, val, m, n, len, flags, s));
+    int32_t hflags = 0;
+    CK(cudaMemcpyAsync(&hflags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hflags) {
+        return set_error("invalid CSR:%s%s%s%s", (hflags & 1) ? " decreasing row_ptr;" : "",
+                         (hflags & 2) ? " column index out of [0, n);" : "",
+                         (hflags & 4) ? " columns not strictly increasing within a row;" : "",
+                         (hflags & 8) ? " non-finite value;" : ""),
+               IMRT_EINVAL;
+    }
+    // --- voxel-major SELL copies --------------------------------------------
+    TRY(dalloc(p, &p->perm, p->m_pad));
+    TRY(dalloc(p, &p->mask, p->m_pad));
+    CK(launch_sigma_sort(len, m, p->m_pad, p->perm, s));
+    TRY(build_sell(p, &p->sell32, IMRT_FP32, row_ptr, col, val, len, mask_in, s));
+    if (p->opt.precision != IMRT_FP32) {
+        Temp tabs;
+        uint32_t* absmax;
+        TRY(talloc(tabs, &absmax, p->n_pad));
+        CK(cudaMemsetAsync(absmax, 0, sizeof(uint32_t) * p->n_pad, s));
+        CK(launch_col_absmax(row_ptr, col, val, m, n, absmax, s));
+        TRY(dalloc(p, &p->scale, p->n_pad));
+        TRY(dalloc(p, &p->inv_scale, p->n_pad));
+        const float qmax = p->opt.precision == IMRT_FP8E4M3 ? 448.0f : 1.0f;
+        CK(launch_scales(absmax, n, p->n_pad, qmax, p->scale, p->inv_scale, s));
+        TRY(build_sell(p, &p->sellq, p->opt.precision, row_ptr, col, val, len, mask_in, s));
+    }
+    // --- beamlet-major copy -------------------------------------------------
+    const int chunk_rows = 512;
+    const int n_chunks = (p->m_pad + chunk_rows - 1) / chunk_rows;
+    Temp tcounts, tcl, tpad;
+    int32_t* counts;
+    int64_t* col_len;
+    int64_t* padded;
+    TRY(talloc(tcounts, &counts, (size_t)n_chunks * n));
+    TRY(talloc(tcl, &col_len, n));
+    TRY(talloc(tpad, &padded, n));
+    TRY(dalloc(p, &p->t_off, n + 1));
+    CK(launch_transpose_plan(row_ptr, col, p->perm, p->m_pad, n, chunk_rows, counts, col_len, padded, p->t_off, s));
+    CK(cudaMemcpyAsync(&p->t_entries, p->t_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> hlen(n);
+    CK(cudaMemcpyAsync(hlen.data(), col_len, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    TRY(dalloc(p, &p->t_val, p->t_entries + 4));
+    TRY(dalloc(p, &p->t_row, p->t_entries + 4));
+    CK(launch_transpose_fill(row_ptr, col, val, p->perm, p->m_pad, n, chunk_rows, counts, col_len, p->t_off,
+                             p->t_val, p->t_row, s));
+    if (p->opt.precision != IMRT_FP32) {
+        TRY(dalloc_bytes(p, &p->t_valq, (size_t)p->t_entries * elem_bytes(p->opt.precision) + 64));
+        CK(launch_t_quantize(p->opt.precision, p->t_off, p->t_val, n, p->inv_scale, p->t_valq, s));
+    }
+    TRY(make_bwd_schedule(p, hlen));
+    // --- structures and term coefficients (Eq. (1): c = w / |V_s|) ----------
+    Temp tcnt;
+    int32_t* scount;
+    TRY(talloc(tcnt, &scount, kMaxStruct));
+    CK(cudaMemsetAsync(scount, 0, sizeof(int32_t) * kMaxStruct, s));
+    CK(launch_mask_counts(p->mask, p->m_pad, scount, s));
+    int32_t hcount[kMaxStruct];
+    CK(cudaMemcpyAsync(hcount, scount, sizeof(hcount), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    Terms& T = p->terms;
+    memset(&T, 0, sizeof(T));
+    T.S = p->S;
+    for (int st = 0; st < p->S; ++st) {
+        for (int k = 0; k < 2; ++k) {
+            const float t = thresholds[2 * st + k];
+            const float w = weights[2 * st + k];
+            const bool present = !std::isnan(t) && w != 0.0f && hcount[st] > 0;
+            if (!present) continue;
+            const double c = (double)w / (double)hcount[st];
+            if (k == 0) {
+                T.has_u |= 1u << st;
+                T.Tu[st] = t;
+                T.cu[st] = (float)c;
+                T.cud[st] = c;
+            } else {
+                T.has_o |= 1u << st;
+                T.To[st] = t;
+                T.co[st] = (float)c;
+                T.cod[st] = c;
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(p->terms_dev, &T, sizeof(Terms), cudaMemcpyHostToDevice, s));
+    // --- x_init = 0 rule: s = T_under / mean over the first under-dose structure of (D 1)_j
+    int s_star = -1;
+    for (int st = 0; st < p->S && s_star < 0; ++st)
+        if ((T.has_u >> st) & 1u) s_star = st;
+    p->x1_scale = 0.0;
+    if (s_star >= 0) {
+        CK(launch_fill(p->x_stage, 1.0f, n, s));
+        TRY(run_eval(p, kFwdEval, p->x_stage, p->z_stage, p->r_stage, nullptr));
+        CK(launch_sum_masked(p->z_stage, p->mask, s_star, p->m, p->dscratch, s));
+        double sum = 0.0;
+        CK(cudaMemcpyAsync(&sum, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double mean = sum / (double)hcount[s_star];
+        if (mean > 0.0) p->x1_scale = (double)T.Tu[s_star] / mean;
+    }
+    // --- lambda0 rule: 8 / L, L = 2 lambda_max(D^T C D), power iteration ------
+    CK(launch_fill(p->x_stage, (float)(1.0 / std::sqrt((double)n)), n, s));
+    double lam = 0.0;
+    for (int it = 0; it < 50; ++it) {
+        TRY(run_eval(p, kFwdPower, p->x_stage, p->z_stage, p->r_stage, nullptr));
+        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage));
+        CK(launch_power_update(p->x_stage, p->g_stage, n, p->dscratch, s));
+    }
+    CK(cudaMemcpyAsync(&lam, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
+    CK(cudaStreamSynchronize(s));
+    p->lambda0_rule = lam > 0.0 ? 8.0 / (2.0 * lam) : 1.0;
+    return IMRT_OK;
+}
+
+imrt_status alloc_vectors(imrt_plan* p) {
+    p->wmax = p->sm_count * 4 * (kFwdThreads / 32);
+    p->gmax = p->sm_count * 4;
+    p->v.n_pad = p->n_pad;
+    p->v.m_pad = p->m_pad;
+    TRY(dalloc(p, &p->v.x, (size_t)kSets * p->n_pad));
+    TRY(dalloc(p, &p->v.z, (size_t)kSets * p->m_pad));
+    TRY(dalloc(p, &p->v.r, (size_t)kSets * p->m_pad));
+    TRY(dalloc(p, &p->v.g, p->n_pad));
+    TRY(dalloc(p, &p->v.gpart, (size_t)kMaxTrials * p->wmax));
+    TRY(dalloc(p, &p->v.dpart, (size_t)kMaxTrials * p->gmax));
+    TRY(dalloc(p, &p->x_stage, p->n_pad));
+    TRY(dalloc(p, &p->g_stage, p->n_pad));
+    TRY(dalloc(p, &p->z_stage, p->m_pad));
+    TRY(dalloc(p, &p->r_stage, p->m_pad));
+    TRY(dalloc(p, &p->zout_stage, std::max(p->m, 1)));
+    TRY(dalloc(p, &p->dscratch, 8));
+    TRY(dalloc(p, &p->terms_dev, 1));
+    TRY(dalloc(p, &p->st, 1));
+    TRY(dalloc(p, &p->sp, 1));
+    cudaStream_t s = stream_of(p);
+    CK(cudaMemsetAsync(p->v.x, 0, sizeof(float) * kSets * p->n_pad, s));
+    CK(cudaMemsetAsync(p->v.g, 0, sizeof(float) * p->n_pad, s));
+    CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
+    CK(cudaMemsetAsync(p->g_stage, 0, sizeof(float) * p->n_pad, s));
+    CK(cudaMemsetAsync(p->st, 0, sizeof(DevState), s));
+    CK(cudaHostAlloc((void**)&p->st_host, sizeof(DevState), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&p->cancel_host, sizeof(int32_t), cudaHostAllocMapped));
+    *p->cancel_host = 0;
+    CK(cudaHostGetDevicePointer((void**)&p->cancel_dev, p->cancel_host, 0));
+    for (auto& e : p->ev) CK(cudaEventCreate(&e));
+    return IMRT_OK;
+}
+
+// --- solve -----------------------------------------------------------------
+
+imrt_status ensure_trace(imrt_plan* p) {
+    const int cap = p->opt.max_iter;
+    if (p->opt.trace >= 1 && p->tr_cap < cap) {
+        TRY(dalloc(p, &p->tr_G, cap + 1));
+        TRY(dalloc(p, &p->tr_lam, std::max(cap, 1)));
+        TRY(dalloc(p, &p->tr_bt, std::max(cap, 1)));
+        p->tr_cap = cap;
+    }
+    if (p->opt.trace >= 2 && p->tr_xcap < cap) {
+        TRY(dalloc(p, &p->tr_x, (size_t)(cap + 1) * p->n));
+        p->tr_xcap = cap;
+    }
+    return IMRT_OK;
+}
+
+SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_init, const float* x0,
+                        unsigned long long cond) {
+    const imrt_options& o = p->opt;
+    SolveParams q{};
+    q.eps = o.eps;
+    q.alpha = o.alpha;
+    q.delta = o.delta;
+    q.lambda0 = o.lambda0 > 0.0 ? o.lambda0 : p->lambda0_rule;
+    q.x1_scale = p->x1_scale;
+    q.max_iter = max_iter;
+    q.max_bt = o.max_backtracks;
+    q.x_init = x_init;
+    q.k_trials = o.k_trials;
+    q.trace = o.trace;
+    q.n = p->n;
+    q.n_pad = p->n_pad;
+    q.m = p->m;
+    q.m_pad = p->m_pad;
+    q.fwd_grid = sh.grid;
+    q.warps = sh.warps;
+    q.timeout_ns = o.timeout_ms > 0.0 ? (unsigned long long)(o.timeout_ms * 1e6) : 0ull;
+    q.tr_G = o.trace >= 1 ? p->tr_G : nullptr;
+    q.tr_lam = o.trace >= 1 ? p->tr_lam : nullptr;
+    q.tr_bt = o.trace >= 1 ? p->tr_bt : nullptr;
+    q.tr_x = o.trace >= 2 ? p->tr_x : nullptr;
+    q.x0 = x0;
+    q.cancel = p->cancel_dev;
+    q.cond = cond;
+    return q;
+}
+
+struct Launch {
+    const void* fn;
+    dim3 grid, block;
+    size_t smem;
+    std::vector<uint8_t> storage;
+    void* arg = nullptr;
+};
+
+template <class A>
+Launch make_launch(const void* fn, int grid, int block, size_t smem, const A& arg) {
+    Launch l;
+    l.fn = fn;
+    l.grid = dim3(grid);
+    l.block = dim3(block);
+    l.smem = smem;
+    l.storage.resize(sizeof(A));
+    memcpy(l.storage.data(), &arg, sizeof(A));
+    return l;
+}
+
+struct InitArgs {
+    DevState* st;
+    const SolveParams* sp;
+    Vecs v;
+};
+
+struct BwdCurArgs {
+    BwdArgs a;
+    const float* r_sets;
+};
+
+// The kernel sequence of one solve phase (precision, k_trials).
+struct PhaseKernels {
+    Launch init, eval, ctl0, bwd, trial, ctl1, finish;
+};
+
+imrt_status phase_kernels(imrt_plan* p, int precision, int k_trials, PhaseKernels* K, FwdShape** shape_out) {
+    FwdShape* sh = nullptr;
+    TRY(get_shape(p, precision, k_trials, &sh));
+    FwdShape* sh1 = nullptr;
+    TRY(get_shape(p, precision, 1, &sh1));
+    (void)sh1;
+    const SellCopy& c = copy_of(p, precision);
+    InitArgs ia{p->st, p->sp, p->v};
+    K->init = make_launch(init_kernel(), 1, kCtlThreads, 0, ia);
+    // The initial evaluation uses the trial launch's grid so that partial counts match.
+    FwdArgs ea = fwd_args(p, c, *sh, kFwdEval);
+    const void* eval_fn = fwd_kernel(precision, 1);
+    const size_t eval_smem = fwd_smem_bytes(p->n_pad, 1, precision);
+    CK(cudaFuncSetAttribute(eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eval_smem));
+    K->eval = make_launch(eval_fn, sh->grid, kFwdThreads, eval_smem, ea);
+    CtlArgs c0{p->st, p->sp, p->v, 0};
+    CtlArgs c1{p->st, p->sp, p->v, 1};
+    K->ctl0 = make_launch(ctl_kernel(0), 1, kCtlThreads, 0, c0);
+    K->ctl1 = make_launch(ctl_kernel(1), 1, kCtlThreads, 0, c1);
+    BwdCurArgs ba{bwd_args(p, precision, 1), p->v.r};
+    K->bwd = make_launch(bwd_kernel(precision), p->bwd_grid, kBwdThreads, 0, ba);
+    FwdArgs ta = fwd_args(p, c, *sh, kFwdTrial);
+    K->trial = make_launch(fwd_kernel(precision, k_trials), sh->grid, kFwdThreads, sh->smem, ta);
+    K->finish = make_launch(finish_kernel(), 1, kCtlThreads, 0, ia);
+    *shape_out = sh;
+    return IMRT_OK;
+}
+
+// Argument pointer array for a Launch whose storage packs the kernel's parameters in order.
+struct ArgPack {
+    std::vector<void*> ptrs;
+};
+
+ArgPack pack_args(Launch& l, const std::vector<size_t>& offsets) {
+    ArgPack a;
+    for (size_t off : offsets) a.ptrs.push_back(l.storage.data() + off);
+    return a;
+}
+
+std::vector<size_t> offsets_for(const Launch& l) {
+    // init / finish: (DevState*, const SolveParams*, Vecs); bwd: (BwdArgs, const float*); others: one struct.
+    if (l.fn == init_kernel() || l.fn == finish_kernel())
+        return {offsetof(InitArgs, st), offsetof(InitArgs, sp), offsetof(InitArgs, v)};
+    for (int prec = 0; prec <= IMRT_FP8E4M3; ++prec)
+        if (l.fn == bwd_kernel(prec)) return {offsetof(BwdCurArgs, a), offsetof(BwdCurArgs, r_sets)};
+    return {0};
+}
+
+imrt_status launch_now(Launch& l, cudaStream_t s) {
+    ArgPack a = pack_args(l, offsets_for(l));
+    CK(cudaLaunchKernel(l.fn, l.grid, l.block, a.ptrs.data(), l.smem, s));
+    return IMRT_OK;
+}
+
+imrt_status add_node(Launch& l, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* out) {
+    ArgPack a = pack_args(l, offsets_for(l));
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(l.fn);
+    kp.gridDim = l.grid;
+    kp.blockDim = l.block;
+    kp.sharedMemBytes = (unsigned)l.smem;
+    kp.kernelParams = a.ptrs.data();
+    kp.extra = nullptr;
+    CK(cudaGraphAddKernelNode(out, g, dep, dep ? 1 : 0, &kp));
+    return IMRT_OK;
+}
+
+// init -> eval -> ctl0 -> while(cond) { bwd -> trial -> ctl1 } -> bwd -> finish
+imrt_status get_graph(imrt_plan* p, int precision, int k_trials, PhaseKernels& K, SolveGraph** out) {
+    auto key = std::make_pair(precision, k_trials);
+    auto it = p->graphs.find(key);
+    if (it != p->graphs.end()) {
+        *out = &it->second;
+        return IMRT_OK;
+    }
+    SolveGraph sg;
+    CK(cudaGraphCreate(&sg.graph, 0));
+    CK(cudaGraphConditionalHandleCreate(&sg.cond, sg.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t n_init, n_eval, n_ctl0, n_loop, n_bwd_final, n_finish;
+    TRY(add_node(K.init, sg.graph, nullptr, &n_init));
+    TRY(add_node(K.eval, sg.graph, &n_init, &n_eval));
+    TRY(add_node(K.ctl0, sg.graph, &n_eval, &n_ctl0));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = sg.cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(cudaGraphAddNode(&n_loop, sg.graph, &n_ctl0, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t b_bwd, b_trial, b_ctl;
+    TRY(add_node(K.bwd, body, nullptr, &b_bwd));
+    TRY(add_node(K.trial, body, &b_bwd, &b_trial));
+    TRY(add_node(K.ctl1, body, &b_trial, &b_ctl));
+    TRY(add_node(K.bwd, sg.graph, &n_loop, &n_bwd_final));
+    TRY(add_node(K.finish, sg.graph, &n_bwd_final, &n_finish));
+    CK(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
+    it = p->graphs.emplace(key, sg).first;
+    *out = &it->second;
+    return IMRT_OK;
+}
+
+// One solve phase on the device. x_init / x0 as in SolveParams.
+imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, const float* x0, imrt_result* res) {
+    cudaStream_t s = stream_of(p);
+    PhaseKernels K;
+    FwdShape* sh = nullptr;
+    TRY(phase_kernels(p, precision, p->opt.k_trials, &K, &sh));
+    const bool graph = p->opt.mode == IMRT_MODE_GRAPH;
+    SolveGraph* sg = nullptr;
+    if (graph) TRY(get_graph(p, precision, p->opt.k_trials, K, &sg));
+    SolveParams q = make_params(p, *sh, max_iter, x_init, x0, graph ? (unsigned long long)sg->cond : 0ull);
+    CK(cudaMemcpyAsync(p->sp, &q, sizeof(q), cudaMemcpyHostToDevice, s));
+    int launches = 0;
+    if (graph) {
+        CK(cudaGraphLaunch(sg->exec, s));
+        CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        launches = 3 + 3 * (p->st_host->passes - 1) + 2;
+    } else {
+        TRY(launch_now(K.init, s));
+        TRY(launch_now(K.eval, s));
+        TRY(launch_now(K.ctl0, s));
+        launches += 3;
+        CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const bool prof = p->opt.profile != 0;
+        while (!p->st_host->done) {
+            if (p->st_host->need_grad) {
+                if (prof) CK(cudaEventRecord(p->ev[2], s));
+                TRY(launch_now(K.bwd, s));
+                if (prof) CK(cudaEventRecord(p->ev[3], s));
+                ++launches;
+            }
+            const bool timed_bwd = prof && p->st_host->need_grad;
+            if (prof) CK(cudaEventRecord(p->ev[0], s));
+            TRY(launch_now(K.trial, s));
+            if (prof) CK(cudaEventRecord(p->ev[1], s));
+            TRY(launch_now(K.ctl1, s));
+            launches += 2;
+            CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (prof) {
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
+                res->fwd_ms += ms;
+                res->fwd_launches += 1;
+                if (timed_bwd) {
+                    CK(cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]));
+                    res->bwd_ms += ms;
+                    res->bwd_launches += 1;
+                }
+            }
+        }
+        TRY(launch_now(K.bwd, s));
+        TRY(launch_now(K.finish, s));
+        launches += 2;
+        CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    const DevState& d = *p->st_host;
+    res->launches += launches;
+    res->passes += d.passes;
+    res->grad_passes += d.grad_passes;
+    p->cur = d.cur;
+    return IMRT_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+
+extern "C" {
+
+void imrt_default_options(imrt_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->eps = 1e-4;
+    o->alpha = 2.0;
+    o->lambda0 = 0.0;
+    o->delta = 1e-6;
+    o->max_iter = 200;
+    o->max_backtracks = 50;
+    o->x_init = 0;
+    o->precision = IMRT_FP32;
+    o->k_trials = 1;
+    o->mode = IMRT_MODE_GRAPH;
+    o->profile = 0;
+    o->trace = 0;
+    o->polish_iter = 50;
+    o->timeout_ms = 0.0;
+    o->stream = nullptr;
+}
+
+const char* imrt_last_error(void) { return g_error.c_str(); }
+
+const char* imrt_version(void) { return "imrt-gb300 1.0 sm_103a"; }
+
+void plan_destroy(imrt_plan* p) {
+    if (!p) return;
+    for (auto& kv : p->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    for (void* a : p->allocations) cudaFree(a);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->cancel_host) cudaFreeHost(p->cancel_host);
+    delete p;
+}
+
+imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_structures, const float* thresholds,
+                        const float* weights, const imrt_options* opt, imrt_plan** out) {
+    g_error.clear();
+    if (!out) return set_error("out is NULL"), IMRT_EINVAL;
+    *out = nullptr;
+    if (!D || !structures || !thresholds || !weights) return set_error("NULL argument"), IMRT_EINVAL;
+    if (D->m < 1 || D->n < 1 || D->nnz < 0) return set_error("need m >= 1, n >= 1, nnz >= 0"), IMRT_EINVAL;
+    if (D->nnz > 0 && (!D->row_ptr || !D->col_idx || !D->val)) return set_error("NULL CSR array"), IMRT_EINVAL;
+    if (!D->row_ptr) return set_error("NULL row_ptr"), IMRT_EINVAL;
+    if (n_structures < 1 || n_structures > kMaxStruct) return set_error("n_structures must be 1..8"), IMRT_EINVAL;
+    if ((int64_t)D->m > (int64_t)INT32_MAX - 1024) return set_error("m too large"), IMRT_EUNSUPPORTED;
+    for (int i = 0; i < 2 * n_structures; ++i)
+        if (!(weights[i] >= 0.0f) || !std::isfinite(weights[i]) || std::isinf(thresholds[i]))
+            return set_error("weights must be finite and >= 0; thresholds finite or NaN"), IMRT_EINVAL;
+    imrt_options o;
+    if (opt) o = *opt;
+    else imrt_default_options(&o);
+    TRY(validate_options(&o));
+    if (o.precision != IMRT_FP32 && D->n > 65536)
+        return set_error("16-bit beamlet indices need n <= 65536"), IMRT_EUNSUPPORTED;
+
+    imrt_plan* p = new imrt_plan();
+    p->opt = o;
+    p->m = D->m;
+    p->n = D->n;
+    p->nnz = D->nnz;
+    p->S = n_structures;
+    p->n_pad = (int32_t)round_up(D->n, 4);
+    p->m_pad = (int32_t)round_up(D->m, kSlice);
+    p->n_slices = p->m_pad / kSlice;
+    imrt_status st = IMRT_OK;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        set_error("no CUDA device: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        delete p;
+        return IMRT_ECUDA;
+    }
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if ((size_t)p->n_pad * 8 + 4096 > (size_t)max_smem) {
+        set_error("n = %d beamlets exceeds the shared-memory staging limit (%d bytes per CTA)", p->n, max_smem);
+        delete p;
+        return IMRT_EUNSUPPORTED;
+    }
+    st = alloc_vectors(p);
+    if (st == IMRT_OK) st = plan_build(p, D, structures, thresholds, weights);
+    if (st != IMRT_OK) {
+        std::string msg = g_error;
+        plan_destroy(p);
+        g_error = msg;
+        return st;
+    }
+    *out = p;
+    return IMRT_OK;
+}
+
+imrt_status plan_set_options(imrt_plan* p, const imrt_options* opt) {
+    g_error.clear();
+    if (!p || !opt) return set_error("NULL argument"), IMRT_EINVAL;
+    TRY(validate_options(opt));
+    if (opt->precision != p->opt.precision && opt->precision != IMRT_FP32 && p->sellq.precision != opt->precision)
+        return set_error("the plan was created without a copy of D at precision %d", opt->precision), IMRT_EINVAL;
+    p->opt = *opt;
+    return IMRT_OK;
+}
+
+imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
+    g_error.clear();
+    if (!p || !res) return set_error("NULL argument"), IMRT_EINVAL;
+    memset(res, 0, sizeof(*res));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = stream_of(p);
+    const imrt_options& o = p->opt;
+    if (o.x_init == 2 && !x0) return set_error("x_init = 2 needs x0"), IMRT_EINVAL;
+    *p->cancel_host = 0;
+    TRY(ensure_trace(p));
+    const float* x0_dev = nullptr;
+    if (o.x_init == 2) {
+        CK(cudaMemcpyAsync(p->x_stage, x0, sizeof(float) * p->n, cudaMemcpyDefault, s));
+        x0_dev = p->x_stage;
+    }
+    const int precision = o.precision;
+    TRY(run_phase(p, precision, o.max_iter, o.x_init, x0_dev, res));
+    DevState d = *p->st_host;
+    res->iterations = d.iter;
+    res->backtracks = d.total_bt;
+    res->initial_objective = d.G0;
+    // Reduced-precision D: polish with the FP32 copy from the reached x (warm start).
+    if (precision != IMRT_FP32 && o.polish_iter > 0 && (d.status == IMRT_OK)) {
+        CK(cudaMemcpyAsync(p->g_stage, p->v.x + (size_t)d.cur * p->n_pad, sizeof(float) * p->n_pad,
+                           cudaMemcpyDeviceToDevice, s));
+        const int trace_saved = p->opt.trace;
+        p->opt.trace = 0;
+        imrt_status ps = run_phase(p, IMRT_FP32, o.polish_iter, 2, p->g_stage, res);
+        p->opt.trace = trace_saved;
+        TRY(ps);
+        d = *p->st_host;
+        res->polish_iterations = d.iter;
+    }
+    res->status = d.status;
+    res->stop_reason = d.stop;
+    res->objective = d.G;
+    res->kkt = d.kkt;
+    res->rel_change = d.rel;
+    res->lambda0 = o.lambda0 > 0.0 ? o.lambda0 : p->lambda0_rule;
+    p->last_iterations = res->iterations;
+    res->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (d.status != IMRT_OK) {
+        const char* what = d.status == IMRT_ELINESEARCH ? "line search exceeded max_backtracks"
+                           : d.status == IMRT_ENUMERIC  ? "non-finite dose or objective"
+                           : d.status == IMRT_ETIMEOUT  ? "timeout"
+                           : d.status == IMRT_ECANCELLED ? "cancelled"
+                           : d.status == IMRT_EINVAL     ? "x0 must be finite and >= 0"
+                                                         : "device error";
+        set_error("solve stopped: %s", what);
+    }
+    return (imrt_status)d.status;
+}
+
+imrt_status plan_dose(imrt_plan* p, const float* x, float* z_out) {
+    g_error.clear();
+    if (!p || !z_out) return set_error("NULL argument"), IMRT_EINVAL;
+    return plan_eval(p, x, nullptr, z_out, nullptr);
+}
+
+imrt_status plan_eval(imrt_plan* p, const float* x, double* G, float* z_out, float* g_out) {
+    g_error.clear();
+    if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    cudaStream_t s = stream_of(p);
+    const float* xs = p->v.x + (size_t)p->cur * p->n_pad;
+    if (x) {
+        CK(cudaMemcpyAsync(p->x_stage, x, sizeof(float) * p->n, cudaMemcpyDefault, s));
+        xs = p->x_stage;
+    }
+    TRY(run_eval(p, kFwdEval, xs, p->z_stage, p->r_stage, G ? p->dscratch : nullptr));
+    if (g_out) {
+        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage));
+        CK(cudaMemcpyAsync(g_out, p->g_stage, sizeof(float) * p->n, cudaMemcpyDefault, s));
+    }
+    if (z_out) {
+        const bool dev = is_device_ptr(z_out);
+        float* dst = dev ? z_out : p->zout_stage;
+        CK(launch_unpermute(p->z_stage, p->perm, p->m, dst, s));
+        if (!dev) CK(cudaMemcpyAsync(z_out, dst, sizeof(float) * p->m, cudaMemcpyDeviceToHost, s));
+    }
+    if (G) CK(cudaMemcpyAsync(G, p->dscratch, sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return IMRT_OK;
+}
+
+imrt_status plan_get_x(imrt_plan* p, float* x_out) {
+    g_error.clear();
+    if (!p || !x_out) return set_error("NULL argument"), IMRT_EINVAL;
+    cudaStream_t s = stream_of(p);
+    CK(cudaMemcpyAsync(x_out, p->v.x + (size_t)p->cur * p->n_pad, sizeof(float) * p->n, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return IMRT_OK;
+}
+
+imrt_status plan_get_trace(imrt_plan* p, int32_t cap, double* G, double* lambda, int32_t* backtracks, float* xs) {
+    g_error.clear();
+    if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    if (p->tr_cap < 0) return set_error("no trace recorded (imrt_options.trace = 0)"), IMRT_EINVAL;
+    const int k = std::min(cap, p->last_iterations);
+    cudaStream_t s = stream_of(p);
+    if (G) CK(cudaMemcpyAsync(G, p->tr_G, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
+    if (lambda && k) CK(cudaMemcpyAsync(lambda, p->tr_lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    if (backtracks && k) CK(cudaMemcpyAsync(backtracks, p->tr_bt, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+    if (xs) {
+        if (p->tr_xcap < 0) return set_error("no x trace recorded (imrt_options.trace < 2)"), IMRT_EINVAL;
+        CK(cudaMemcpyAsync(xs, p->tr_x, sizeof(float) * (size_t)(k + 1) * p->n, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return IMRT_OK;
+}
+
+imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
+    g_error.clear();
+    if (!pc || !info) return set_error("NULL argument"), IMRT_EINVAL;
+    imrt_plan* p = const_cast<imrt_plan*>(pc);
+    memset(info, 0, sizeof(*info));
+    info->m = p->m;
+    info->n = p->n;
+    info->n_structures = p->S;
+    info->n_slices = p->n_slices;
+    info->nnz = p->nnz;
+    const SellCopy& c = copy_of(p, p->opt.precision);
+    info->sell_entries = c.entries;
+    info->t_entries = p->t_entries;
+    const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = (int64_t)col_bytes(p->opt.precision);
+    // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes, mask read)
+    info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 9;
+    info->bwd_bytes = p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4;
+    info->device_bytes = p->device_bytes;
+    FwdShape* sh = nullptr;
+    if (get_shape(p, p->opt.precision, p->opt.k_trials, &sh) == IMRT_OK) {
+        info->fwd_grid = sh->grid;
+    }
+    info->fwd_block = kFwdThreads;
+    info->bwd_grid = p->bwd_grid;
+    info->bwd_block = kBwdThreads;
+    info->precision = p->opt.precision;
+    info->k_trials = p->opt.k_trials;
+    info->lambda0_rule = p->lambda0_rule;
+    info->x1_scale = p->x1_scale;
+    return IMRT_OK;
+}
+
+imrt_status plan_cancel(imrt_plan* p) {
+    if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    *(volatile int32_t*)p->cancel_host = 1;
+    return IMRT_OK;
+}
+
+}  // extern "C"

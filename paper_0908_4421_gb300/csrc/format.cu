@@ -1,0 +1,501 @@
+// Plan set-up kernels: CSR validation, SELL-32-sigma construction of the
+// voxel-major copy, the deterministic beamlet-major transposition, per-beamlet
+// scales of the reduced-precision copies, and small vector utilities.
+//
+// Nothing here runs inside the solve loop. Every kernel is deterministic: the
+// only atomics are integer counts (order-independent) and an integer max.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <math.h>
+
+#include "../../include/imrt.h"
+#include "imrt_internal.cuh"
+
+namespace imrt {
+
+namespace {
+
+inline int blocks_for(int64_t count, int threads) { return (int)((count + threads - 1) / threads); }
+
+// Row lengths and CSR checks: column range, strictly increasing columns, finite values.
+__global__ void k_row_check(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const float* __restrict__ val, int32_t m, int32_t n, int32_t* __restrict__ len,
+                            int32_t* __restrict__ flags) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t a = row_ptr[j], b = row_ptr[j + 1];
+    int f = 0;
+    if (b < a) {
+        f |= 1;
+        len[j] = 0;
+    } else {
+        len[j] = (int32_t)(b - a);
+        int prev = -1;
+        for (int64_t k = a; k < b; ++k) {
+            const int c = col[k];
+            if (c < 0 || c >= n) f |= 2;
+            if (c <= prev) f |= 4;
+            prev = c;
+            if (!isfinite(val[k])) f |= 8;
+        }
+    }
+    if (f) atomicOr(flags, f);
+}
+
+// One CTA per window of kSigma rows: sort by (length desc, row asc); bitonic sort in shared memory.
+__global__ void __launch_bounds__(kSigma / 2) k_sigma_sort(const int32_t* __restrict__ len, int32_t m,
+                                                           int32_t m_pad, int32_t* __restrict__ perm) {
+    __shared__ unsigned long long key[kSigma];
+    const int w0 = blockIdx.x * kSigma;
+    for (int t = threadIdx.x; t < kSigma; t += blockDim.x) {
+        const int j = w0 + t;
+        key[t] = j < m ? ((unsigned long long)(0x7fffffffu - (uint32_t)len[j]) << 32) | (uint32_t)j
+                       : ~0ull;
+    }
+    __syncthreads();
+    for (int size = 2; size <= kSigma; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < kSigma / 2; t += blockDim.x) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const unsigned long long a = key[lo], b = key[hi];
+                if ((a > b) == up) {
+                    key[lo] = b;
+                    key[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < kSigma; t += blockDim.x) {
+        const int p = w0 + t;
+        if (p < m_pad) perm[p] = key[t] == ~0ull ? -1 : (int32_t)(key[t] & 0xffffffffu);
+    }
+}
+
+__global__ void k_slice_sizes(const int32_t* __restrict__ len, const int32_t* __restrict__ perm, int32_t m,
+                              int32_t n_slices, int ge, int32_t* __restrict__ slice_len,
+                              int64_t* __restrict__ slice_entries) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slices) return;
+    int L = 0;
+    for (int l = 0; l < kSlice; ++l) {
+        const int p = s * kSlice + l;
+        if (p < m) {
+            const int j = perm[p];
+            if (j >= 0) L = max(L, len[j]);
+        }
+    }
+    const int groups = (L + ge - 1) / ge;
+    slice_len[s] = groups;
+    slice_entries[s] = (int64_t)groups * kSlice * ge;
+}
+
+// Exclusive scan, single CTA: out[0] = 0, out[i + 1] = in[0] + ... + in[i].
+__global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                                                   int64_t count) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t carry;
+    constexpr int ITEMS = 8;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        out[0] = 0;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < count; base += 1024 * ITEMS) {
+        int64_t local[ITEMS];
+        int64_t s = 0;
+        for (int k = 0; k < ITEMS; ++k) {
+            const int64_t i = base + (int64_t)threadIdx.x * ITEMS + k;
+            local[k] = i < count ? in[i] : 0;
+            s += local[k];
+        }
+        part[threadIdx.x] = s;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int64_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int64_t run = carry + (threadIdx.x ? part[threadIdx.x - 1] : 0);
+        for (int k = 0; k < ITEMS; ++k) {
+            const int64_t i = base + (int64_t)threadIdx.x * ITEMS + k;
+            run += local[k];
+            if (i < count) out[i + 1] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_val(void* dst, int64_t k, float v) {
+    if constexpr (PREC == IMRT_FP32) {
+        static_cast<float*>(dst)[k] = v;
+    } else if constexpr (PREC == IMRT_FP16) {
+        static_cast<__half*>(dst)[k] = __float2half_rn(v);
+    } else if constexpr (PREC == IMRT_BF16) {
+        static_cast<__nv_bfloat16*>(dst)[k] = __float2bfloat16_rn(v);
+    } else {
+        static_cast<__nv_fp8_storage_t*>(dst)[k] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_col(void* dst, int64_t k, int32_t c) {
+    if constexpr (PREC == IMRT_FP32) static_cast<int32_t*>(dst)[k] = c;
+    else static_cast<uint16_t*>(dst)[k] = (uint16_t)c;
+}
+
+// One thread per permuted row: writes the row into its lane of the slice layout.
+template <int PREC, int GE>
+__global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const float* __restrict__ val, const int32_t* __restrict__ perm,
+                            const uint8_t* __restrict__ mask_in, int32_t m, int32_t m_pad,
+                            const int64_t* __restrict__ slice_off, const int32_t* __restrict__ slice_len,
+                            const float* __restrict__ inv_scale, void* sval, void* scol, uint8_t* mask_out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m_pad) return;
+    const int s = p / kSlice, lane = p % kSlice;
+    const int j = p < m ? perm[p] : -1;
+    const int64_t a = j >= 0 ? row_ptr[j] : 0;
+    const int len = j >= 0 ? (int)(row_ptr[j + 1] - a) : 0;
+    const int total = slice_len[s] * GE;
+    const int64_t base = slice_off[s];
+    for (int e = 0; e < total; ++e) {
+        const int64_t dst = base + ((int64_t)(e / GE) * kSlice + lane) * GE + (e % GE);
+        if (e < len) {
+            const int c = col[a + e];
+            const float v = inv_scale ? val[a + e] * inv_scale[c] : val[a + e];
+            store_val<PREC>(sval, dst, v);
+            store_col<PREC>(scol, dst, c);
+        } else {
+            store_val<PREC>(sval, dst, 0.0f);
+            store_col<PREC>(scol, dst, 0);
+        }
+    }
+    mask_out[p] = j >= 0 ? mask_in[j] : (uint8_t)0;
+}
+
+// Transposition, pass 1: per chunk of permuted rows, how many entries each beamlet gets.
+__global__ void k_t_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ perm, int32_t m_pad, int32_t n, int32_t chunk_rows,
+                          int32_t* __restrict__ counts) {
+    extern __shared__ int32_t hist[];
+    for (int c = threadIdx.x; c < n; c += blockDim.x) hist[c] = 0;
+    __syncthreads();
+    const int p0 = blockIdx.x * chunk_rows, p1 = min(m_pad, p0 + chunk_rows);
+    for (int p = p0; p < p1; ++p) {
+        const int j = perm[p];
+        if (j < 0) continue;
+        for (int64_t k = row_ptr[j] + threadIdx.x; k < row_ptr[j + 1]; k += blockDim.x) atomicAdd(&hist[col[k]], 1);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) counts[(size_t)blockIdx.x * n + c] = hist[c];
+}
+
+// Pass 2: per beamlet, exclusive offsets of each chunk inside the beamlet's row; totals.
+__global__ void k_t_colscan(int32_t* __restrict__ counts, int32_t n_chunks, int32_t n, int64_t* __restrict__ col_len,
+                            int64_t* __restrict__ padded) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int64_t run = 0;
+    for (int ch = 0; ch < n_chunks; ++ch) {
+        const int v = counts[(size_t)ch * n + c];
+        counts[(size_t)ch * n + c] = (int32_t)run;
+        run += v;
+    }
+    col_len[c] = run;
+    padded[c] = (run + 3) & ~(int64_t)3;
+}
+
+// Pass 3: scatter. Rows of a chunk are visited in order, so each beamlet row
+// receives voxels in ascending (permuted) index; within one voxel row the
+// columns are distinct, so the per-beamlet cursors need no atomics.
+__global__ void k_t_scatter(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const float* __restrict__ val, const int32_t* __restrict__ perm, int32_t m_pad,
+                            int32_t n, int32_t chunk_rows, const int32_t* __restrict__ counts,
+                            const int64_t* __restrict__ t_off, float* __restrict__ t_val,
+                            int32_t* __restrict__ t_row) {
+    extern __shared__ int32_t cursor[];
+    for (int c = threadIdx.x; c < n; c += blockDim.x) cursor[c] = counts[(size_t)blockIdx.x * n + c];
+    __syncthreads();
+    const int p0 = blockIdx.x * chunk_rows, p1 = min(m_pad, p0 + chunk_rows);
+    for (int p = p0; p < p1; ++p) {
+        const int j = perm[p];
+        if (j >= 0) {
+            for (int64_t k = row_ptr[j] + threadIdx.x; k < row_ptr[j + 1]; k += blockDim.x) {
+                const int c = col[k];
+                const int pos = cursor[c];
+                cursor[c] = pos + 1;
+                const int64_t dst = t_off[c] + pos;
+                t_val[dst] = val[k];
+                t_row[dst] = p;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_t_pad(const int64_t* __restrict__ col_len, const int64_t* __restrict__ t_off, int32_t n,
+                        float* __restrict__ t_val, int32_t* __restrict__ t_row) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    for (int64_t k = t_off[c] + col_len[c]; k < t_off[c + 1]; ++k) {
+        t_val[k] = 0.0f;
+        t_row[k] = 0;
+    }
+}
+
+template <int PREC>
+__global__ void k_t_quantize(const int64_t* __restrict__ t_off, const float* __restrict__ t_val, int32_t n,
+                             const float* __restrict__ inv_scale, void* out) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const float s = inv_scale[i];
+    for (int64_t k = t_off[i] + threadIdx.x; k < t_off[i + 1]; k += blockDim.x) store_val<PREC>(out, k, t_val[k] * s);
+}
+
+__global__ void k_mask_counts(const uint8_t* __restrict__ mask, int32_t m, int32_t* __restrict__ counts) {
+    __shared__ int32_t local[kMaxStruct];
+    if (threadIdx.x < kMaxStruct) local[threadIdx.x] = 0;
+    __syncthreads();
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const uint32_t b = mask[j];
+        for (int s = 0; s < kMaxStruct; ++s)
+            if ((b >> s) & 1u) atomicAdd(&local[s], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxStruct) atomicAdd(&counts[threadIdx.x], local[threadIdx.x]);
+}
+
+__global__ void k_unpermute(const float* __restrict__ zp, const int32_t* __restrict__ perm, int32_t m,
+                            float* __restrict__ z) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const int j = perm[p];
+    if (j >= 0) z[j] = zp[p];
+}
+
+__global__ void k_pad_copy(const float* __restrict__ src, int32_t n, int32_t n_pad, float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pad) dst[i] = i < n ? src[i] : 0.0f;
+}
+
+__global__ void k_fill(float* dst, float v, int32_t count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = v;
+}
+
+__device__ double block_sum_d(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_masked(const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                                                     int32_t bit, int32_t m, double* out) {
+    double s = 0.0;
+    for (int p = threadIdx.x; p < m; p += blockDim.x)
+        if ((mask[p] >> bit) & 1u) s += (double)z[p];
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// Power-iteration update: lambda = v . w, v = w / ||w||.
+__global__ void __launch_bounds__(1024) k_power_update(float* __restrict__ v, const float* __restrict__ w, int32_t n,
+                                                       double* lam) {
+    double vw = 0.0, ww = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        vw += (double)v[i] * (double)w[i];
+        ww += (double)w[i] * (double)w[i];
+    }
+    vw = block_sum_d(vw);
+    ww = block_sum_d(ww);
+    if (threadIdx.x == 0) *lam = vw;
+    if (ww > 0.0) {
+        const float inv = (float)(1.0 / sqrt(ww));
+        for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
+    }
+}
+
+__global__ void k_col_absmax(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                             const float* __restrict__ val, int32_t m, uint32_t* __restrict__ absmax_bits) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    for (int64_t k = row_ptr[j]; k < row_ptr[j + 1]; ++k) atomicMax(&absmax_bits[col[k]], __float_as_uint(fabsf(val[k])));
+}
+
+__global__ void k_scales(const uint32_t* __restrict__ absmax_bits, int32_t n, int32_t n_pad, float qmax,
+                         float* __restrict__ scale, float* __restrict__ inv_scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    const float a = i < n ? __uint_as_float(absmax_bits[i]) : 0.0f;
+    const float s = a > 0.0f ? a / qmax : 1.0f;
+    scale[i] = s;
+    inv_scale[i] = a > 0.0f ? qmax / a : 0.0f;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_doubles(const double* __restrict__ p, int32_t count, double* out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += p[i];
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+}  // namespace
+
+cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
+                             int32_t* len, int32_t* flags, cudaStream_t stream) {
+    k_row_check<<<blocks_for(m, 256), 256, 0, stream>>>(row_ptr, col, val, m, n, len, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_sort(const int32_t* len, int32_t m, int32_t m_pad, int32_t* perm, cudaStream_t stream) {
+    const int windows = (m_pad + kSigma - 1) / kSigma;
+    k_sigma_sort<<<windows, kSigma / 2, 0, stream>>>(len, m, m_pad, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_sizes(const int32_t* len, const int32_t* perm, int32_t m, int32_t n_slices, int ge,
+                               int32_t* slice_len, int64_t* slice_entries, cudaStream_t stream) {
+    k_slice_sizes<<<blocks_for(n_slices, 256), 256, 0, stream>>>(len, perm, m, n_slices, ge, slice_len,
+                                                                 slice_entries);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t stream) {
+    k_scan_i64<<<1, 1024, 0, stream>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_fill(int precision, const int64_t* row_ptr, const int32_t* col, const float* val,
+                             const int32_t* perm, const uint8_t* mask_in, int32_t m, int32_t m_pad,
+                             const int64_t* slice_off, const int32_t* slice_len, const float* inv_scale,
+                             void* sval, void* scol, uint8_t* mask_out, cudaStream_t stream) {
+    const int g = blocks_for(m_pad, 128);
+    switch (precision) {
+        case IMRT_FP32:
+            k_sell_fill<IMRT_FP32, 4><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
+                                                             slice_len, nullptr, sval, scol, mask_out);
+            break;
+        case IMRT_FP16:
+            k_sell_fill<IMRT_FP16, 8><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
+                                                             slice_len, inv_scale, sval, scol, mask_out);
+            break;
+        case IMRT_BF16:
+            k_sell_fill<IMRT_BF16, 8><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
+                                                             slice_len, inv_scale, sval, scol, mask_out);
+            break;
+        case IMRT_FP8E4M3:
+            k_sell_fill<IMRT_FP8E4M3, 16><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad,
+                                                                 slice_off, slice_len, inv_scale, sval, scol,
+                                                                 mask_out);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, const int32_t* perm, int32_t m_pad,
+                                  int32_t n, int32_t chunk_rows, int32_t* counts, int64_t* col_len, int64_t* padded,
+                                  int64_t* t_off, cudaStream_t stream) {
+    const int n_chunks = (m_pad + chunk_rows - 1) / chunk_rows;
+    const size_t smem = (size_t)n * sizeof(int32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_t_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_t_count<<<n_chunks, 256, smem, stream>>>(row_ptr, col, perm, m_pad, n, chunk_rows, counts);
+    k_t_colscan<<<blocks_for(n, 256), 256, 0, stream>>>(counts, n_chunks, n, col_len, padded);
+    k_scan_i64<<<1, 1024, 0, stream>>>(padded, t_off, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* perm,
+                                  int32_t m_pad, int32_t n, int32_t chunk_rows, const int32_t* counts,
+                                  const int64_t* col_len, const int64_t* t_off, float* t_val, int32_t* t_row,
+                                  cudaStream_t stream) {
+    const int n_chunks = (m_pad + chunk_rows - 1) / chunk_rows;
+    const size_t smem = (size_t)n * sizeof(int32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_t_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_t_scatter<<<n_chunks, 256, smem, stream>>>(row_ptr, col, val, perm, m_pad, n, chunk_rows, counts, t_off, t_val,
+                                                 t_row);
+    k_t_pad<<<blocks_for(n, 256), 256, 0, stream>>>(col_len, t_off, n, t_val, t_row);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_quantize(int precision, const int64_t* t_off, const float* t_val, int32_t n,
+                              const float* inv_scale, void* out, cudaStream_t stream) {
+    switch (precision) {
+        case IMRT_FP16: k_t_quantize<IMRT_FP16><<<n, 256, 0, stream>>>(t_off, t_val, n, inv_scale, out); break;
+        case IMRT_BF16: k_t_quantize<IMRT_BF16><<<n, 256, 0, stream>>>(t_off, t_val, n, inv_scale, out); break;
+        case IMRT_FP8E4M3: k_t_quantize<IMRT_FP8E4M3><<<n, 256, 0, stream>>>(t_off, t_val, n, inv_scale, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_counts(const uint8_t* mask, int32_t m, int32_t* counts, cudaStream_t stream) {
+    k_mask_counts<<<min(blocks_for(m, 256), 1024), 256, 0, stream>>>(mask, m, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(const float* zp, const int32_t* perm, int32_t m, float* z, cudaStream_t stream) {
+    k_unpermute<<<blocks_for(m, 256), 256, 0, stream>>>(zp, perm, m, z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* dst, cudaStream_t stream) {
+    k_pad_copy<<<blocks_for(n_pad, 256), 256, 0, stream>>>(src, n, n_pad, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* dst, float v, int32_t count, cudaStream_t stream) {
+    k_fill<<<blocks_for(count, 256), 256, 0, stream>>>(dst, v, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, int32_t m, double* out,
+                              cudaStream_t stream) {
+    k_sum_masked<<<1, 1024, 0, stream>>>(z, mask, bit, m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_update(float* v, const float* w, int32_t n, double* lam, cudaStream_t stream) {
+    k_power_update<<<1, 1024, 0, stream>>>(v, w, n, lam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_absmax(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t,
+                              uint32_t* absmax_bits, cudaStream_t stream) {
+    k_col_absmax<<<blocks_for(m, 256), 256, 0, stream>>>(row_ptr, col, val, m, absmax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scales(const uint32_t* absmax_bits, int32_t n, int32_t n_pad, float qmax, float* scale,
+                          float* inv_scale, cudaStream_t stream) {
+    k_scales<<<blocks_for(n_pad, 256), 256, 0, stream>>>(absmax_bits, n, n_pad, qmax, scale, inv_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g_objective(const double* gpart, int32_t count, double* out, cudaStream_t stream) {
+    k_sum_doubles<<<1, 1024, 0, stream>>>(gpart, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace imrt

@@ -1,0 +1,180 @@
+// Internal declarations shared by the CUDA translation units of libimrt.
+//
+// Layouts (all device-resident, owned by a plan):
+//   Voxel-major copy of D, SELL-32-sigma: voxels are sorted by row length
+//   (descending, ties by index) inside windows of SIGMA rows; the permuted
+//   rows are cut into slices of 32 (one warp, one row per lane). A slice of
+//   L groups stores, for group k and lane l, GE consecutive entries of row
+//   (32 s + l) at entry offset slice_off[s] + (32 k + l) * GE, so one warp-wide
+//   16-byte load per array reads 512 contiguous bytes. Padding entries hold
+//   value 0 and column 0. All per-voxel vectors (z, r, mask) live in this
+//   permuted order; the ABI un-permutes on the way out.
+//   Beamlet-major copy of D: one row per beamlet, voxel indices in the
+//   permuted order (ascending), each row padded to a multiple of 4 entries so
+//   every row starts 16-byte aligned.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace imrt {
+
+constexpr int kSlice = 32;        // SELL chunk height: rows per warp
+constexpr int kSigma = 1024;      // sorting window (rows)
+constexpr int kMaxStruct = 8;
+constexpr int kMaxTrials = 8;     // Armijo step sizes per forward pass
+constexpr int kSets = kMaxTrials + 1;  // x/z/r buffer sets: accepted + trials
+constexpr int kFwdThreads = 512;
+constexpr int kBwdThreads = 512;
+constexpr int kCtlThreads = 256;
+
+// Forward-kernel modes.
+enum FwdMode : int32_t {
+    kFwdEval = 0,   // z, r, G at a given x (no step)
+    kFwdTrial = 1,  // x_t = max(0, x - lambda_q g) for k_trials step sizes, then z, r, G
+    kFwdPower = 2,  // z = D v and u = Cdiag z (power iteration of the step-size rule)
+};
+
+// Per-structure penalty terms (Eq. (1) with per-structure thresholds, c = w / |V_s|).
+struct Terms {
+    int32_t S;
+    uint32_t has_u, has_o;  // bit s: structure s has an under / over term
+    float Tu[kMaxStruct], To[kMaxStruct];
+    float cu[kMaxStruct], co[kMaxStruct];    // FP32 copies for r
+    double cud[kMaxStruct], cod[kMaxStruct]; // FP64 copies for G
+};
+
+// Solver state, device-resident, updated only by the single-CTA controller.
+struct DevState {
+    double G;        // objective at the accepted x
+    double lambda;   // first step size of the next trial batch
+    double rel;      // last relative change
+    double g1_inf;   // ||g(x_1)||_inf
+    double kkt;
+    double G0;       // G(x_1)
+    double lambda_acc;
+    int32_t cur;        // buffer set holding the accepted x / z / r
+    int32_t iter;       // accepted steps
+    int32_t bt;         // rejected trials in the current iteration
+    int32_t total_bt;
+    int32_t passes;     // forward passes (trial batches + the initial evaluation)
+    int32_t grad_passes;
+    int32_t status;     // imrt_status
+    int32_t stop;       // imrt_stop
+    int32_t need_grad;  // the transposed pass must refresh g for the accepted x
+    int32_t done;
+    int32_t g1_done;
+    int32_t launches;
+    unsigned long long t_start;
+};
+
+// Solve parameters, device-resident, written by the host before each solve.
+struct SolveParams {
+    double eps, alpha, delta, lambda0, x1_scale;
+    int32_t max_iter, max_bt, x_init, k_trials, trace, n, n_pad, m, m_pad;
+    int32_t fwd_grid, warps;  // forward launch shape (partials per trial)
+    unsigned long long timeout_ns;
+    double* tr_G;
+    double* tr_lam;
+    int32_t* tr_bt;
+    float* tr_x;
+    const float* x0;
+    const volatile int32_t* cancel;
+    unsigned long long cond;  // cudaGraphConditionalHandle; 0 outside a graph
+};
+
+// Vectors of one plan.
+struct Vecs {
+    float* x;        // kSets * n_pad
+    float* z;        // kSets * m_pad
+    float* r;        // kSets * m_pad
+    float* g;        // n_pad
+    double* gpart;   // kMaxTrials * warps: per-warp objective partials
+    double* dpart;   // kMaxTrials * fwd_grid: per-CTA ||x_t - x||^2 partials
+    int32_t n_pad, m_pad;
+};
+
+struct FwdArgs {
+    const int64_t* slice_off;    // n_slices + 1 (entries)
+    const int32_t* slice_len;    // n_slices (groups)
+    const void* val;
+    const void* col;
+    const int32_t* warp_slices;  // warps + 1
+    const uint8_t* mask;         // m_pad, permuted order
+    const float* scale;          // n_pad per-beamlet value scale, or NULL (FP32)
+    const Terms* terms;
+    DevState* st;
+    const SolveParams* sp;
+    Vecs v;
+    int32_t m, n, n_pad, m_pad;
+    int32_t mode;        // FwdMode
+    const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x
+    float* z_dst;        // kFwdEval / kFwdPower; NULL => accepted set
+    float* r_dst;
+    double* gpart_dst;   // kFwdEval: NULL => v.gpart
+};
+
+struct BwdArgs {
+    const int64_t* t_off;     // n + 1 (entries, padded rows)
+    const void* val;
+    const int32_t* row;       // permuted voxel indices
+    const int32_t* cta_rows;  // beamlet order, grouped by CTA
+    const int32_t* cta_ptr;   // grid + 1
+    const float* scale;       // n_pad or NULL
+    DevState* st;
+    const float* r_fixed;     // NULL => r of the accepted set
+    float* g;
+    int32_t m_pad, guard;     // guard: skip unless st->need_grad
+};
+
+struct CtlArgs {
+    DevState* st;
+    const SolveParams* sp;
+    Vecs v;
+    int32_t phase;  // 0: after the initial evaluation, 1: after a trial batch
+};
+
+// Kernel launchers / function pointers (kernels.cu).
+const void* fwd_kernel(int precision, int k_trials);
+const void* bwd_kernel(int precision);
+const void* bwd_fixed_kernel(int precision);
+const void* ctl_kernel(int phase);
+const void* init_kernel();
+const void* finish_kernel();
+size_t fwd_smem_bytes(int n_pad, int k_trials, int precision);
+int fwd_group_entries(int precision);
+
+// Setup kernels (format.cu), all on `stream`.
+cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
+                             int32_t* len, int32_t* flags, cudaStream_t stream);
+cudaError_t launch_sigma_sort(const int32_t* len, int32_t m, int32_t m_pad, int32_t* perm, cudaStream_t stream);
+cudaError_t launch_slice_sizes(const int32_t* len, const int32_t* perm, int32_t m, int32_t n_slices, int ge,
+                               int32_t* slice_len, int64_t* slice_entries, cudaStream_t stream);
+cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t stream);
+cudaError_t launch_sell_fill(int precision, const int64_t* row_ptr, const int32_t* col, const float* val,
+                             const int32_t* perm, const uint8_t* mask_in, int32_t m, int32_t m_pad,
+                             const int64_t* slice_off, const int32_t* slice_len, const float* inv_scale,
+                             void* sval, void* scol, uint8_t* mask_out, cudaStream_t stream);
+cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, const int32_t* perm, int32_t m_pad,
+                                  int32_t n, int32_t chunk_rows, int32_t* counts, int64_t* col_len, int64_t* padded,
+                                  int64_t* t_off, cudaStream_t stream);
+cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* perm,
+                                  int32_t m_pad, int32_t n, int32_t chunk_rows, const int32_t* counts,
+                                  const int64_t* col_len, const int64_t* t_off, float* t_val, int32_t* t_row,
+                                  cudaStream_t stream);
+cudaError_t launch_t_quantize(int precision, const int64_t* t_off, const float* t_val, int32_t n,
+                              const float* inv_scale, void* out, cudaStream_t stream);
+cudaError_t launch_mask_counts(const uint8_t* mask, int32_t m, int32_t* counts, cudaStream_t stream);
+cudaError_t launch_unpermute(const float* zp, const int32_t* perm, int32_t m, float* z, cudaStream_t stream);
+cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* dst, cudaStream_t stream);
+cudaError_t launch_fill(float* dst, float v, int32_t count, cudaStream_t stream);
+cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, int32_t m, double* out,
+                              cudaStream_t stream);
+cudaError_t launch_power_update(float* v, const float* w, int32_t n, double* lam, cudaStream_t stream);
+cudaError_t launch_col_absmax(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m,
+                              int32_t n, uint32_t* absmax_bits, cudaStream_t stream);
+cudaError_t launch_scales(const uint32_t* absmax_bits, int32_t n, int32_t n_pad, float qmax, float* scale,
+                          float* inv_scale, cudaStream_t stream);
+cudaError_t launch_g_objective(const double* gpart, int32_t count, double* out, cudaStream_t stream);
+
+}  // namespace imrt

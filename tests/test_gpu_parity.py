@@ -1,0 +1,258 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: the kernels accumulate in FP32 and reduce the objective in FP64,
+so the dose z = D x must match the oracle to 1e-5 relative (2-norm over
+voxels), the objective G to 1e-5 relative at a fixed x, and the final
+objective of a full solve to 1e-4 relative (Sec. 3.2 reports a 1e-6 - 1e-5
+CPU/GPU difference in single precision).
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0908_4421_gb300 import Options, Plan, phantom
+from paper_0908_4421_gb300 import _lib as L
+
+pytestmark = pytest.mark.gpu
+
+DOSE_RTOL = 1e-5
+OBJ_RTOL = 1e-5
+FINAL_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0908_4421_gb300 import build as cuda_build
+    cuda_build.build()
+    yield
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+RANDOM_CASES = {
+    "ragged": dict(seed=1, m=1000, n=37, density=0.1, empty_rows=50, long_rows=5),
+    "one_row": dict(seed=2, m=1, n=5, density=0.9),
+    "one_col": dict(seed=3, m=77, n=1, density=0.8, empty_rows=3),
+    "many_slices": dict(seed=4, m=5003, n=130, density=0.05, empty_rows=400, long_rows=2),
+    "n_multiple_of_4": dict(seed=5, m=333, n=64, density=0.2),
+}
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.get()
+
+
+@pytest.mark.parametrize("name", sorted(RANDOM_CASES))
+@pytest.mark.parametrize("device_inputs", [False, True])
+def test_dose_and_eval_random(orc, name, device_inputs):
+    case = phantom.random_case(n_structures=3, **RANDOM_CASES[name])
+    rng = np.random.Generator(np.random.PCG64(7))
+    with Plan.from_case(case, Options(), device=device_inputs) as plan:
+        for trial in range(3):
+            x = rng.uniform(0, 2, case.n).astype(np.float32)
+            G, z, g = plan.eval(x)
+            G_ref, z_ref, r_ref, g_ref = orc.eval(case, x.astype(np.float64))
+            assert rel(z, z_ref) <= DOSE_RTOL
+            assert abs(G - G_ref) <= OBJ_RTOL * max(abs(G_ref), 1e-30)
+            if np.linalg.norm(g_ref) > 0:
+                assert rel(g, g_ref) <= 1e-4
+            z2 = plan.dose(x)
+            np.testing.assert_array_equal(z, z2)
+
+
+def test_empty_matrix(orc):
+    case = phantom.random_case(9, m=40, n=6, density=0.0)
+    assert case.nnz == 0
+    with Plan.from_case(case, Options(lambda0=1.0)) as plan:
+        G, z, g = plan.eval(np.ones(case.n, np.float32))
+        assert np.all(z == 0) and np.all(g == 0)
+        G_ref = orc.eval(case, np.ones(case.n))[0]
+        assert abs(G - G_ref) <= 1e-6 * G_ref
+        res = plan.solve()
+        assert res.status == 0 and res.stop_reason == L.STOP_STATIONARY and res.iterations == 0
+
+
+@pytest.fixture(scope="module")
+def tiny(orc):
+    case = phantom.make_case(phantom.TINY_5MM_5BEAM)
+    return case, orc.lambda0_rule(case)
+
+
+def test_tiny_phantom_eval(orc, tiny):
+    case, _ = tiny
+    with Plan.from_case(case) as plan:
+        x1 = orc.initial_point(case).astype(np.float32)
+        G, z, g = plan.eval(x1)
+        G_ref, z_ref, _, g_ref = orc.eval(case, x1.astype(np.float64))
+        assert rel(z, z_ref) <= DOSE_RTOL
+        assert abs(G - G_ref) <= OBJ_RTOL * G_ref
+        assert rel(g, g_ref) <= 1e-4
+        info = plan.info()
+        assert (info["m"], info["n"], info["nnz"]) == (case.m, case.n, case.nnz)
+        # the step-size rule and the x_1 scale, against the oracle's FP64 versions
+        assert abs(info["lambda0_rule"] - orc.lambda0_rule(case)) <= 1e-3 * orc.lambda0_rule(case)
+        assert abs(info["x1_scale"] - float(x1[0])) <= 1e-5 * float(x1[0])
+
+
+def _solve_pair(orc, case, lam0, **kw):
+    max_iter = kw.pop("max_iter", 200)
+    delta = kw.pop("delta", 1e-6)
+    ref = orc.solve(case, lambda0=lam0, max_iter=max_iter, delta=delta, trace=True, trace_x=True)
+    opts = Options(lambda0=lam0, max_iter=max_iter, delta=delta, trace=2, **kw)
+    with Plan.from_case(case, opts) as plan:
+        res = plan.solve()
+        G, lam, bt, xs = plan.trace(res.iterations, with_x=True)
+        z_final = plan.dose()
+        x_final = plan.get_x()
+    return ref, res, G, lam, bt, xs, z_final, x_final
+
+
+@pytest.mark.parametrize("mode", [L.MODE_GRAPH, L.MODE_HOST])
+def test_tiny_phantom_solve_parity(orc, tiny, mode):
+    """Per iteration: dose of the GPU iterate within 1e-5 of the oracle's, until the first
+    disagreement in the accepted step; final objective within 1e-4."""
+    case, lam0 = tiny
+    ref, res, G, lam, bt, xs, z_final, x_final = _solve_pair(orc, case, lam0, mode=mode)
+    assert res.status == 0
+    assert abs(res.objective - ref.objective) <= FINAL_RTOL * ref.objective
+    assert abs(res.initial_objective - ref.initial_objective) <= OBJ_RTOL * ref.initial_objective
+    k_common = min(res.iterations, ref.iterations)
+    same_path = 0
+    for k in range(k_common + 1):
+        if k > 0 and (bt[k - 1] != ref.backtrack_trace[k - 1]):
+            break
+        z_gpu = orc.dose(case, xs[k].astype(np.float64))
+        z_orc = orc.dose(case, ref.xs[k])
+        assert rel(z_gpu, z_orc) <= DOSE_RTOL, k
+        assert abs(G[k] - ref.G[k]) <= FINAL_RTOL * ref.G[k]
+        same_path = k
+    assert same_path >= min(20, k_common)
+    # the kernel's own dose of the final iterate
+    assert rel(z_final, orc.dose(case, x_final.astype(np.float64))) <= DOSE_RTOL
+    assert np.all(xs >= 0)
+    assert np.all(np.diff(G) < 0)
+
+
+def test_graph_and_host_modes_agree_bitwise(tiny):
+    case, lam0 = tiny
+    out = []
+    for mode in (L.MODE_GRAPH, L.MODE_HOST):
+        with Plan.from_case(case, Options(lambda0=lam0, max_iter=60, trace=1, mode=mode)) as plan:
+            res = plan.solve()
+            out.append((res.iterations, res.objective, plan.get_x(), plan.trace(res.iterations)[0]))
+    assert out[0][0] == out[1][0]
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_array_equal(out[0][3], out[1][3])
+
+
+@pytest.mark.parametrize("k_trials", [2, 4, 8])
+def test_k_trials_same_trajectory(tiny, k_trials):
+    """Evaluating k step sizes per pass over D takes exactly the sequential Armijo decisions."""
+    case, lam0 = tiny
+    big = 16 * lam0  # forces backtracking so batches matter
+    runs = []
+    for kt in (1, k_trials):
+        with Plan.from_case(case, Options(lambda0=big, max_iter=40, trace=1, k_trials=kt)) as plan:
+            res = plan.solve()
+            G, lam, bt, _ = plan.trace(res.iterations)
+            runs.append((res, G, lam, bt))
+    (r1, G1, l1, b1), (rk, Gk, lk, bk) = runs
+    assert r1.iterations == rk.iterations and r1.backtracks == rk.backtracks
+    np.testing.assert_array_equal(b1, bk)
+    np.testing.assert_array_equal(l1, lk)
+    np.testing.assert_allclose(Gk, G1, rtol=1e-12)
+    assert rk.passes < r1.passes
+
+
+def test_backtracking_parity(orc, tiny):
+    case, lam0 = tiny
+    ref, res, G, lam, bt, xs, _, _ = _solve_pair(orc, case, 64 * lam0, max_iter=30)
+    assert ref.backtracks > 0
+    k = min(res.iterations, ref.iterations)
+    np.testing.assert_array_equal(bt[:10], ref.backtrack_trace[:10])
+    assert abs(res.objective - ref.objective) <= FINAL_RTOL * ref.objective
+
+
+def test_warm_start_and_zero_start(orc, tiny):
+    case, lam0 = tiny
+    x0 = (orc.initial_point(case) * 0.5).astype(np.float32)
+    for x_init, given in ((2, x0), (1, None)):
+        ref = orc.solve(case, lambda0=lam0, max_iter=25, x_init=x_init, x0=given)
+        with Plan.from_case(case, Options(lambda0=lam0, max_iter=25, x_init=x_init)) as plan:
+            res = plan.solve(x0=given)
+        assert res.iterations == ref.iterations
+        assert abs(res.objective - ref.objective) <= FINAL_RTOL * ref.objective
+
+
+def test_error_paths(tiny):
+    case, lam0 = tiny
+    # negative x0
+    with Plan.from_case(case, Options(lambda0=lam0, x_init=2)) as plan:
+        x0 = np.ones(case.n, np.float32)
+        x0[3] = -1.0
+        res = plan.solve(x0=x0, raise_on_error=False)
+        assert res.status == L.IMRT_EINVAL
+    # line search cap
+    with Plan.from_case(case, Options(lambda0=1e9, max_backtracks=0)) as plan:
+        res = plan.solve(raise_on_error=False)
+        assert res.status == L.IMRT_ELINESEARCH and res.iterations == 0
+    # timeout (device clock)
+    with Plan.from_case(case, Options(lambda0=lam0, timeout_ms=1e-6, max_iter=10000, delta=0.0)) as plan:
+        res = plan.solve(raise_on_error=False)
+        assert res.status == L.IMRT_ETIMEOUT
+    # invalid CSR: column out of range, then unsorted columns
+    bad = phantom.random_case(1, m=50, n=8, density=0.3)
+    col = bad.col.copy()
+    col[0] = 99
+    with pytest.raises(L.ImrtError) as e:
+        Plan(bad.row_ptr, col, bad.val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n)
+    assert e.value.status == L.IMRT_EINVAL
+    col = bad.col.copy()
+    k = int(np.argmax(np.diff(bad.row_ptr) >= 2))
+    a = bad.row_ptr[k]
+    col[a], col[a + 1] = col[a + 1], col[a]
+    with pytest.raises(L.ImrtError):
+        Plan(bad.row_ptr, col, bad.val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n)
+    val = bad.val.copy()
+    val[1] = np.nan
+    with pytest.raises(L.ImrtError):
+        Plan(bad.row_ptr, bad.col, val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n)
+
+
+def test_cancel_from_another_thread(tiny):
+    case, lam0 = tiny
+    with Plan.from_case(case, Options(lambda0=lam0, max_iter=1_000_000, delta=0.0, max_backtracks=60)) as plan:
+        out = {}
+        t = threading.Thread(target=lambda: out.setdefault("r", plan.solve(raise_on_error=False)))
+        t.start()
+        import time
+        time.sleep(0.2)
+        plan.cancel()
+        t.join(timeout=60)
+        assert not t.is_alive()
+        assert out["r"].status == L.IMRT_ECANCELLED
+
+
+@pytest.mark.parametrize("prec,tol", [(L.FP16, 2e-3), (L.BF16, 1e-2), (L.FP8E4M3, 8e-2)])
+def test_reduced_precision_dose_and_polish(orc, tiny, prec, tol):
+    """Reduced-precision D: per-beamlet scaled values, FP32 accumulation; the FP32 polish restores G."""
+    case, lam0 = tiny
+    with Plan.from_case(case, Options(lambda0=lam0, precision=prec, max_iter=200, polish_iter=200)) as plan:
+        res = plan.solve()
+        x = plan.get_x()
+        z = plan.dose(x)  # always the FP32 copy
+    assert res.status == 0
+    ref = orc.solve(case, lambda0=lam0, max_iter=200)
+    assert rel(z, orc.dose(case, x.astype(np.float64))) <= DOSE_RTOL
+    assert res.objective <= ref.objective * (1 + 1e-3)
