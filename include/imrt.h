@@ -100,7 +100,7 @@ typedef struct {
     int32_t mode;           /* imrt_mode; default IMRT_MODE_GRAPH */
     int32_t profile;        /* 1: time every forward and transposed-product launch with CUDA events */
     int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
-    int32_t polish_iter;    /* reduced precision: FP32-D iterations after the first stop; default 50 */
+    int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy; default 20 */
     int32_t reserved;
     double timeout_ms;      /* 0: none; else the device loop stops with IMRT_ETIMEOUT */
     void* stream;           /* cudaStream_t */
@@ -177,12 +177,14 @@ imrt_status plan_set_options(imrt_plan* plan, const imrt_options* opt);
  */
 imrt_status plan_solve(imrt_plan* plan, const float* x0, imrt_result* res);
 
-/* z = D x (Sec. 2.1). x: n (host or device), NULL => the plan's current x. z_out: m (host or device). */
+/* z = D x (Sec. 2.1) with the FP32 copy of D. x: n (host or device), NULL => the plan's current x.
+   z_out: m (host or device). */
 imrt_status plan_dose(imrt_plan* plan, const float* x, float* z_out);
 
 /*
- * One evaluation at x (Eq. (1)-(4)): G in FP64 (host pointer), and optionally
- * z (m) and g = grad G = D^T r (n), host or device pointers, NULL to skip.
+ * One evaluation at x (Eq. (1)-(4)) with the copy of D the options' precision
+ * selects: G in FP64 (host pointer), and optionally z (m) and g = grad G =
+ * D^T r (n), host or device pointers, NULL to skip.
  * x: n (host or device), NULL => the plan's current x.
  */
 imrt_status plan_eval(imrt_plan* plan, const float* x, double* G, float* z_out, float* g_out);

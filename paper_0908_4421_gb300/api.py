@@ -32,7 +32,7 @@ class Options:
     mode: int = L.MODE_GRAPH
     profile: int = 0
     trace: int = 0
-    polish_iter: int = 50
+    polish_iter: int = 20
     timeout_ms: float = 0.0
     stream: int = 0  # cudaStream_t as an integer; 0 = legacy default stream
 

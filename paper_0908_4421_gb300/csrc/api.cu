@@ -78,12 +78,14 @@ struct SellCopy {
     std::vector<int64_t> host_cost;  // per slice, for warp partitions
 };
 
-// Forward launch shape for one (copy, k_trials): grid and warp -> slice partition.
+// Forward launch shape for one (copy, k_trials): grid, work units and their warp partition.
 struct FwdShape {
     int grid = 0;
     int warps = 0;
-    int32_t* warp_slices = nullptr;
+    int n_splits = 0;
+    int gstride = 0;
     size_t smem = 0;
+    FwdUnits units{};
 };
 
 struct SolveGraph {
@@ -108,11 +110,16 @@ struct imrt_plan {
     // beamlet-major
     int64_t* t_off = nullptr;
     float* t_val = nullptr;
-    void* t_valq = nullptr;
+    void* t_valq = nullptr;            // reduced-precision beamlet-major values
+    uint16_t* t_lo = nullptr;          // their 16-bit voxel offsets
+    int64_t* t_seg = nullptr;          // n * H + 1 segment starts
+    int32_t t_H = 0;
+    int64_t tq_entries = 0;
     int32_t* t_row = nullptr;
     int64_t t_entries = 0;
-    int32_t* bwd_rows = nullptr;
-    int32_t* bwd_cta_ptr = nullptr;
+    int32_t* bwd_order = nullptr;     // beamlet rows, longest first
+    int32_t* bwd_next = nullptr;      // schedule counter
+    int32_t* bwd_ticket = nullptr;
     int bwd_grid = 0;
     // vectors and state
     Vecs v{};
@@ -213,8 +220,9 @@ imrt_status validate_options(const imrt_options* o) {
     return IMRT_OK;
 }
 
-// Warp partition of the slices of one copy for a given forward grid: contiguous
-// slice ranges of near-equal cost (stored entries plus an epilogue allowance).
+// Work units of one copy for a given forward grid: slices whose cost exceeds half a warp's
+// share are cut into near-equal pieces (ranges of groups); units are then dealt to warps in
+// contiguous runs of near-equal cost (stored entries plus an epilogue allowance per slice).
 imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, FwdShape* out) {
     const void* fn = fwd_kernel(c.precision, k_trials);
     if (!fn) return set_error("no forward kernel for precision %d, k_trials %d", c.precision, k_trials), IMRT_EINVAL;
@@ -234,20 +242,72 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, FwdShape* 
     out->warps = out->grid * (kFwdThreads / 32);
     out->smem = smem;
     const int W = out->warps;
-    std::vector<int32_t> ws(W + 1, 0);
-    const std::vector<int64_t>& cost = c.host_cost;
+    const int64_t group_entries = (int64_t)kSlice * c.ge;
+    const int64_t epi = 8 * kSlice;
     int64_t total = 0;
-    for (int64_t v : cost) total += v;
-    int64_t run = 0;
-    int s = 0;
-    for (int w = 1; w < W; ++w) {
-        const double target = (double)total * w / W;
-        while (s < p->n_slices && (double)(run + cost[s]) <= target) run += cost[s++];
-        ws[w] = s;
+    for (int s = 0; s < p->n_slices; ++s) total += c.host_cost[s];
+    const double budget = (double)total / W;
+    const int64_t piece_groups = std::max<int64_t>(4, (int64_t)(budget / group_entries));
+    std::vector<int32_t> us, ug0, ug1, usplit, upiece, spieces, sbase;
+    std::vector<int64_t> ucost;
+    int32_t parts = 0;
+    for (int s = 0; s < p->n_slices; ++s) {
+        const int64_t L = (c.host_cost[s] - epi) / group_entries;
+        if (L <= piece_groups) {
+            us.push_back(s), ug0.push_back(0), ug1.push_back((int32_t)L), usplit.push_back(-1), upiece.push_back(0);
+            ucost.push_back(c.host_cost[s]);
+            continue;
+        }
+        const int P = (int)((L + piece_groups - 1) / piece_groups);
+        const int sid = (int)spieces.size();
+        spieces.push_back(P);
+        sbase.push_back(parts);
+        parts += P;
+        for (int k = 0; k < P; ++k) {
+            const int32_t g0 = (int32_t)(L * k / P), g1 = (int32_t)(L * (k + 1) / P);
+            us.push_back(s), ug0.push_back(g0), ug1.push_back(g1), usplit.push_back(sid), upiece.push_back(k);
+            ucost.push_back((int64_t)(g1 - g0) * group_entries + (k == P - 1 ? epi : 0));
+        }
     }
-    ws[W] = p->n_slices;
-    TRY(dalloc(p, &out->warp_slices, W + 1));
-    CK(cudaMemcpy(out->warp_slices, ws.data(), sizeof(int32_t) * (W + 1), cudaMemcpyHostToDevice));
+    const int n_units = (int)us.size();
+    // longest first for the dynamic schedule (the order does not change any result)
+    std::vector<int32_t> ord(n_units);
+    for (int i = 0; i < n_units; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return ucost[x] > ucost[y]; });
+    auto permute = [&](std::vector<int32_t>& v) {
+        std::vector<int32_t> t(v.size());
+        for (int i = 0; i < n_units; ++i) t[i] = v[ord[i]];
+        v.swap(t);
+    };
+    permute(us), permute(ug0), permute(ug1), permute(usplit), permute(upiece);
+    out->n_splits = (int)spieces.size();
+    out->gstride = p->n_slices;
+    FwdUnits& U = out->units;
+    U.n_units = n_units;
+    U.n_splits = out->n_splits;
+    U.gstride = out->gstride;
+    auto upload = [&](const std::vector<int32_t>& h, const int32_t** dst) -> imrt_status {
+        int32_t* d = nullptr;
+        TRY(dalloc(p, &d, std::max<size_t>(h.size(), 1)));
+        if (!h.empty()) CK(cudaMemcpy(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice));
+        *dst = d;
+        return IMRT_OK;
+    };
+    TRY(upload(us, &U.unit_slice));
+    TRY(upload(ug0, &U.unit_g0));
+    TRY(upload(ug1, &U.unit_g1));
+    TRY(upload(usplit, &U.unit_split));
+    TRY(upload(upiece, &U.unit_piece));
+    TRY(upload(spieces, &U.split_pieces));
+    TRY(upload(sbase, &U.split_base));
+    TRY(dalloc(p, &U.partials, (size_t)std::max(parts, 1) * kSlice * k_trials));
+    TRY(dalloc(p, &U.counters, std::max(out->n_splits, 1)));
+    CK(cudaMemset(U.counters, 0, sizeof(int32_t) * std::max(out->n_splits, 1)));
+    TRY(dalloc(p, &U.gpart, (size_t)k_trials * out->gstride));
+    TRY(dalloc(p, &U.ticket, 1));
+    TRY(dalloc(p, &U.next_unit, 1));
+    CK(cudaMemset(U.ticket, 0, sizeof(int32_t)));
+    CK(cudaMemset(U.next_unit, 0, sizeof(int32_t)));
     return IMRT_OK;
 }
 
@@ -272,7 +332,7 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.slice_len = c.slice_len;
     a.val = c.val;
     a.col = c.col;
-    a.warp_slices = sh.warp_slices;
+    a.u = sh.units;
     a.mask = p->mask;
     a.scale = c.precision == IMRT_FP32 ? nullptr : p->scale;
     a.terms = p->terms_dev;
@@ -292,8 +352,13 @@ BwdArgs bwd_args(imrt_plan* p, int precision, int guard) {
     a.t_off = p->t_off;
     a.val = precision == IMRT_FP32 ? (const void*)p->t_val : p->t_valq;
     a.row = p->t_row;
-    a.cta_rows = p->bwd_rows;
-    a.cta_ptr = p->bwd_cta_ptr;
+    a.order = p->bwd_order;
+    a.next_row = p->bwd_next;
+    a.ticket = p->bwd_ticket;
+    a.n = p->n;
+    a.seg = p->t_seg;
+    a.lo = p->t_lo;
+    a.H = p->t_H;
     a.scale = precision == IMRT_FP32 ? nullptr : p->scale;
     a.st = p->st;
     a.r_fixed = nullptr;
@@ -307,61 +372,47 @@ const SellCopy& copy_of(const imrt_plan* p, int precision) {
     return precision == IMRT_FP32 ? p->sell32 : p->sellq;
 }
 
-// Stand-alone evaluation of the forward kernel (no step): z, r (permuted) and per-warp G partials.
-imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, float* r_dst, double* G_out) {
+// Stand-alone evaluation of the forward kernel (no step) with the copy of D at `precision`:
+// z, r (permuted) and the objective partials (summed into *G_out when given).
+imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, float* r_dst, double* G_out,
+                     int precision = IMRT_FP32) {
     FwdShape* sh = nullptr;
-    TRY(get_shape(p, IMRT_FP32, 1, &sh));
-    FwdArgs a = fwd_args(p, p->sell32, *sh, mode);
+    TRY(get_shape(p, precision, 1, &sh));
+    FwdArgs a = fwd_args(p, copy_of(p, precision), *sh, mode);
     a.x_src = x_src;
     a.z_dst = z_dst;
     a.r_dst = r_dst;
-    a.gpart_dst = p->v.gpart;
     void* args[] = {&a};
-    CK(cudaLaunchKernel(fwd_kernel(IMRT_FP32, 1), dim3(sh->grid), dim3(kFwdThreads), args, sh->smem,
+    CK(cudaLaunchKernel(fwd_kernel(precision, 1), dim3(sh->grid), dim3(kFwdThreads), args, sh->smem,
                         stream_of(p)));
-    if (G_out) CK(launch_g_objective(p->v.gpart, sh->warps, G_out, stream_of(p)));
+    if (G_out) CK(launch_g_objective(sh->units.gpart, sh->gstride, G_out, stream_of(p)));
     return IMRT_OK;
 }
 
-imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g) {
-    BwdArgs a = bwd_args(p, IMRT_FP32, 0);
+imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision = IMRT_FP32) {
+    BwdArgs a = bwd_args(p, precision, 0);
     a.r_fixed = r;
     a.g = g;
     void* args[] = {&a};
-    CK(cudaLaunchKernel(bwd_fixed_kernel(IMRT_FP32), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0, stream_of(p)));
+    CK(cudaLaunchKernel(bwd_fixed_kernel(precision), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0, stream_of(p)));
     return IMRT_OK;
 }
 
-// Longest-processing-time assignment of beamlet rows to the transposed kernel's CTAs.
+// Transposed-pass schedule: a persistent grid whose CTAs take beamlet rows longest first.
 imrt_status make_bwd_schedule(imrt_plan* p, const std::vector<int64_t>& len) {
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel(IMRT_FP32), kBwdThreads, 0));
     per_sm = std::max(1, std::min(per_sm, 4));
-    int grid = std::min<int64_t>((int64_t)p->sm_count * per_sm, std::max<int64_t>(1, p->n));
+    const int grid = (int)std::min<int64_t>((int64_t)p->sm_count * per_sm, std::max<int64_t>(1, p->n));
     std::vector<int32_t> order(p->n);
     for (int i = 0; i < p->n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return len[a] > len[b]; });
-    using Item = std::pair<int64_t, int>;  // (load, cta), min-heap
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
-    for (int b = 0; b < grid; ++b) heap.push({0, b});
-    std::vector<std::vector<int32_t>> rows(grid);
-    for (int i : order) {
-        Item it = heap.top();
-        heap.pop();
-        rows[it.second].push_back(i);
-        heap.push({it.first + len[i] + 64, it.second});
-    }
-    std::vector<int32_t> flat, ptr(grid + 1, 0);
-    flat.reserve(p->n);
-    for (int b = 0; b < grid; ++b) {
-        ptr[b] = (int32_t)flat.size();
-        flat.insert(flat.end(), rows[b].begin(), rows[b].end());
-    }
-    ptr[grid] = (int32_t)flat.size();
-    TRY(dalloc(p, &p->bwd_rows, p->n));
-    TRY(dalloc(p, &p->bwd_cta_ptr, grid + 1));
-    CK(cudaMemcpy(p->bwd_rows, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p->bwd_cta_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice));
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return len[x] > len[y]; });
+    TRY(dalloc(p, &p->bwd_order, p->n));
+    TRY(dalloc(p, &p->bwd_next, 1));
+    TRY(dalloc(p, &p->bwd_ticket, 1));
+    CK(cudaMemcpy(p->bwd_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(p->bwd_next, 0, sizeof(int32_t)));
+    CK(cudaMemset(p->bwd_ticket, 0, sizeof(int32_t)));
     p->bwd_grid = grid;
     return IMRT_OK;
 }
@@ -392,6 +443,25 @@ imrt_status build_sell(imrt_plan* p, SellCopy* c, int precision, const int64_t* 
     CK(launch_sell_fill(precision, row_ptr, col, val, p->perm, mask_in, p->m, p->m_pad, c->slice_off, c->slice_len,
                         precision == IMRT_FP32 ? nullptr : p->inv_scale, c->val, c->col, mask_out, s));
     CK(cudaStreamSynchronize(s));
+    return IMRT_OK;
+}
+
+// Step-size rule lambda0 = 8 / L, L = 2 lambda_max(D^T C D), C = diag(sum of the voxel's
+// term coefficients): 50 power iterations from the all-ones vector (computed once per plan).
+imrt_status ensure_lambda0_rule(imrt_plan* p) {
+    if (p->lambda0_rule > 0.0) return IMRT_OK;
+    cudaStream_t s = stream_of(p);
+    CK(launch_fill(p->x_stage, (float)(1.0 / std::sqrt((double)p->n)), p->n, s));
+    for (int it = 0; it < 50; ++it) {
+        TRY(run_eval(p, kFwdPower, p->x_stage, p->z_stage, p->r_stage, nullptr));
+        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage));
+        CK(launch_power_update(p->x_stage, p->g_stage, p->n, p->dscratch, s));
+    }
+    double lam = 0.0;
+    CK(cudaMemcpyAsync(&lam, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
+    CK(cudaStreamSynchronize(s));
+    p->lambda0_rule = lam > 0.0 ? 8.0 / (2.0 * lam) : 1.0;
     return IMRT_OK;
 }
 
@@ -493,8 +563,22 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     CK(launch_transpose_fill(row_ptr, col, val, p->perm, p->m_pad, n, chunk_rows, counts, col_len, p->t_off,
                              p->t_val, p->t_row, s));
     if (p->opt.precision != IMRT_FP32) {
-        TRY(dalloc_bytes(p, &p->t_valq, (size_t)p->t_entries * elem_bytes(p->opt.precision) + 64));
-        CK(launch_t_quantize(p->opt.precision, p->t_off, p->t_val, n, p->inv_scale, p->t_valq, s));
+        const int H = (int)((p->m_pad + 65535) / 65536);
+        if (H > 16) return set_error("reduced precision supports at most 1048576 voxels"), IMRT_EUNSUPPORTED;
+        p->t_H = H;
+        Temp tsl;
+        int64_t* seg_len;
+        TRY(talloc(tsl, &seg_len, (size_t)n * H));
+        TRY(dalloc(p, &p->t_seg, (size_t)n * H + 1));
+        CK(launch_tq_count(p->t_off, p->t_row, col_len, n, H, seg_len, s));
+        CK(launch_scan_i64(seg_len, p->t_seg, (int64_t)n * H, s));
+        CK(cudaMemcpyAsync(&p->tq_entries, p->t_seg + (size_t)n * H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        TRY(dalloc_bytes(p, &p->t_valq, (size_t)p->tq_entries * elem_bytes(p->opt.precision) + 64));
+        TRY(dalloc(p, &p->t_lo, (size_t)p->tq_entries + 32));
+        CK(launch_tq_fill(p->opt.precision, p->t_off, p->t_row, p->t_val, col_len, n, H, p->t_seg, p->inv_scale,
+                          p->t_valq, p->t_lo, s));
+        CK(cudaStreamSynchronize(s));
     }
     TRY(make_bwd_schedule(p, hlen));
     // --- structures and term coefficients (Eq. (1): c = w / |V_s|) ----------
@@ -545,18 +629,8 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
         const double mean = sum / (double)hcount[s_star];
         if (mean > 0.0) p->x1_scale = (double)T.Tu[s_star] / mean;
     }
-    // --- lambda0 rule: 8 / L, L = 2 lambda_max(D^T C D), power iteration ------
-    CK(launch_fill(p->x_stage, (float)(1.0 / std::sqrt((double)n)), n, s));
-    double lam = 0.0;
-    for (int it = 0; it < 50; ++it) {
-        TRY(run_eval(p, kFwdPower, p->x_stage, p->z_stage, p->r_stage, nullptr));
-        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage));
-        CK(launch_power_update(p->x_stage, p->g_stage, n, p->dscratch, s));
-    }
-    CK(cudaMemcpyAsync(&lam, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
+    if (p->opt.lambda0 <= 0.0) TRY(ensure_lambda0_rule(p));
     CK(cudaStreamSynchronize(s));
-    p->lambda0_rule = lam > 0.0 ? 8.0 / (2.0 * lam) : 1.0;
     return IMRT_OK;
 }
 
@@ -569,7 +643,6 @@ imrt_status alloc_vectors(imrt_plan* p) {
     TRY(dalloc(p, &p->v.z, (size_t)kSets * p->m_pad));
     TRY(dalloc(p, &p->v.r, (size_t)kSets * p->m_pad));
     TRY(dalloc(p, &p->v.g, p->n_pad));
-    TRY(dalloc(p, &p->v.gpart, (size_t)kMaxTrials * p->wmax));
     TRY(dalloc(p, &p->v.dpart, (size_t)kMaxTrials * p->gmax));
     TRY(dalloc(p, &p->x_stage, p->n_pad));
     TRY(dalloc(p, &p->g_stage, p->n_pad));
@@ -630,7 +703,8 @@ SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_in
     q.m = p->m;
     q.m_pad = p->m_pad;
     q.fwd_grid = sh.grid;
-    q.warps = sh.warps;
+    q.gstride = sh.gstride;
+    q.gpart = sh.units.gpart;
     q.timeout_ns = o.timeout_ms > 0.0 ? (unsigned long long)(o.timeout_ms * 1e6) : 0ull;
     q.tr_G = o.trace >= 1 ? p->tr_G : nullptr;
     q.tr_lam = o.trace >= 1 ? p->tr_lam : nullptr;
@@ -675,7 +749,7 @@ struct BwdCurArgs {
 
 // The kernel sequence of one solve phase (precision, k_trials).
 struct PhaseKernels {
-    Launch init, eval, ctl0, bwd, trial, ctl1, finish;
+    Launch init, eval, bwd, trial, finish;
 };
 
 imrt_status phase_kernels(imrt_plan* p, int precision, int k_trials, PhaseKernels* K, FwdShape** shape_out) {
@@ -689,17 +763,15 @@ imrt_status phase_kernels(imrt_plan* p, int precision, int k_trials, PhaseKernel
     K->init = make_launch(init_kernel(), 1, kCtlThreads, 0, ia);
     // The initial evaluation uses the trial launch's grid so that partial counts match.
     FwdArgs ea = fwd_args(p, c, *sh, kFwdEval);
+    ea.control = 1;
     const void* eval_fn = fwd_kernel(precision, 1);
     const size_t eval_smem = fwd_smem_bytes(p->n_pad, 1, precision);
     CK(cudaFuncSetAttribute(eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eval_smem));
     K->eval = make_launch(eval_fn, sh->grid, kFwdThreads, eval_smem, ea);
-    CtlArgs c0{p->st, p->sp, p->v, 0};
-    CtlArgs c1{p->st, p->sp, p->v, 1};
-    K->ctl0 = make_launch(ctl_kernel(0), 1, kCtlThreads, 0, c0);
-    K->ctl1 = make_launch(ctl_kernel(1), 1, kCtlThreads, 0, c1);
     BwdCurArgs ba{bwd_args(p, precision, 1), p->v.r};
     K->bwd = make_launch(bwd_kernel(precision), p->bwd_grid, kBwdThreads, 0, ba);
     FwdArgs ta = fwd_args(p, c, *sh, kFwdTrial);
+    ta.control = 1;
     K->trial = make_launch(fwd_kernel(precision, k_trials), sh->grid, kFwdThreads, sh->smem, ta);
     K->finish = make_launch(finish_kernel(), 1, kCtlThreads, 0, ia);
     *shape_out = sh;
@@ -745,7 +817,8 @@ imrt_status add_node(Launch& l, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNo
     return IMRT_OK;
 }
 
-// init -> eval -> ctl0 -> while(cond) { bwd -> trial -> ctl1 } -> bwd -> finish
+// init -> eval -> while(cond) { bwd -> trial } -> bwd -> finish (the controller runs in the
+// last CTA of eval and trial)
 imrt_status get_graph(imrt_plan* p, int precision, int k_trials, PhaseKernels& K, SolveGraph** out) {
     auto key = std::make_pair(precision, k_trials);
     auto it = p->graphs.find(key);
@@ -756,21 +829,19 @@ imrt_status get_graph(imrt_plan* p, int precision, int k_trials, PhaseKernels& K
     SolveGraph sg;
     CK(cudaGraphCreate(&sg.graph, 0));
     CK(cudaGraphConditionalHandleCreate(&sg.cond, sg.graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNode_t n_init, n_eval, n_ctl0, n_loop, n_bwd_final, n_finish;
+    cudaGraphNode_t n_init, n_eval, n_loop, n_bwd_final, n_finish;
     TRY(add_node(K.init, sg.graph, nullptr, &n_init));
     TRY(add_node(K.eval, sg.graph, &n_init, &n_eval));
-    TRY(add_node(K.ctl0, sg.graph, &n_eval, &n_ctl0));
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = sg.cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    CK(cudaGraphAddNode(&n_loop, sg.graph, &n_ctl0, nullptr, 1, &cp));
+    CK(cudaGraphAddNode(&n_loop, sg.graph, &n_eval, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t b_bwd, b_trial, b_ctl;
+    cudaGraphNode_t b_bwd, b_trial;
     TRY(add_node(K.bwd, body, nullptr, &b_bwd));
     TRY(add_node(K.trial, body, &b_bwd, &b_trial));
-    TRY(add_node(K.ctl1, body, &b_trial, &b_ctl));
     TRY(add_node(K.bwd, sg.graph, &n_loop, &n_bwd_final));
     TRY(add_node(K.finish, sg.graph, &n_bwd_final, &n_finish));
     CK(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
@@ -795,12 +866,11 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
         CK(cudaGraphLaunch(sg->exec, s));
         CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        launches = 3 + 3 * (p->st_host->passes - 1) + 2;
+        launches = 2 + 2 * (p->st_host->passes - 1) + 2;
     } else {
         TRY(launch_now(K.init, s));
         TRY(launch_now(K.eval, s));
-        TRY(launch_now(K.ctl0, s));
-        launches += 3;
+        launches += 2;
         CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const bool prof = p->opt.profile != 0;
@@ -815,8 +885,7 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
             if (prof) CK(cudaEventRecord(p->ev[0], s));
             TRY(launch_now(K.trial, s));
             if (prof) CK(cudaEventRecord(p->ev[1], s));
-            TRY(launch_now(K.ctl1, s));
-            launches += 2;
+            launches += 1;
             CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (prof) {
@@ -847,6 +916,8 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
 
 }  // namespace
 
+void imrt::set_last_error_message(const char* msg) { g_error = msg ? msg : ""; }
+
 // =============================================================================
 // C ABI
 // =============================================================================
@@ -868,7 +939,7 @@ void imrt_default_options(imrt_options* o) {
     o->mode = IMRT_MODE_GRAPH;
     o->profile = 0;
     o->trace = 0;
-    o->polish_iter = 50;
+    o->polish_iter = 20;
     o->timeout_ms = 0.0;
     o->stream = nullptr;
 }
@@ -969,24 +1040,27 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     if (o.x_init == 2 && !x0) return set_error("x_init = 2 needs x0"), IMRT_EINVAL;
     *p->cancel_host = 0;
     TRY(ensure_trace(p));
+    if (o.lambda0 <= 0.0) TRY(ensure_lambda0_rule(p));
     const float* x0_dev = nullptr;
     if (o.x_init == 2) {
         CK(cudaMemcpyAsync(p->x_stage, x0, sizeof(float) * p->n, cudaMemcpyDefault, s));
         x0_dev = p->x_stage;
     }
     const int precision = o.precision;
-    TRY(run_phase(p, precision, o.max_iter, o.x_init, x0_dev, res));
+    const bool polish = precision != IMRT_FP32 && o.polish_iter > 0;
+    const int first_iter = polish ? std::max(0, o.max_iter - std::min(o.polish_iter, o.max_iter)) : o.max_iter;
+    TRY(run_phase(p, precision, first_iter, o.x_init, x0_dev, res));
     DevState d = *p->st_host;
     res->iterations = d.iter;
     res->backtracks = d.total_bt;
     res->initial_objective = d.G0;
     // Reduced-precision D: polish with the FP32 copy from the reached x (warm start).
-    if (precision != IMRT_FP32 && o.polish_iter > 0 && (d.status == IMRT_OK)) {
+    if (polish && d.status == IMRT_OK) {
         CK(cudaMemcpyAsync(p->g_stage, p->v.x + (size_t)d.cur * p->n_pad, sizeof(float) * p->n_pad,
                            cudaMemcpyDeviceToDevice, s));
         const int trace_saved = p->opt.trace;
         p->opt.trace = 0;
-        imrt_status ps = run_phase(p, IMRT_FP32, o.polish_iter, 2, p->g_stage, res);
+        imrt_status ps = run_phase(p, IMRT_FP32, std::min(o.polish_iter, o.max_iter), 2, p->g_stage, res);
         p->opt.trace = trace_saved;
         TRY(ps);
         d = *p->st_host;
@@ -1015,7 +1089,11 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
 imrt_status plan_dose(imrt_plan* p, const float* x, float* z_out) {
     g_error.clear();
     if (!p || !z_out) return set_error("NULL argument"), IMRT_EINVAL;
-    return plan_eval(p, x, nullptr, z_out, nullptr);
+    const int saved = p->opt.precision;
+    p->opt.precision = IMRT_FP32;  // the dose always comes from the FP32 copy
+    const imrt_status st = plan_eval(p, x, nullptr, z_out, nullptr);
+    p->opt.precision = saved;
+    return st;
 }
 
 imrt_status plan_eval(imrt_plan* p, const float* x, double* G, float* z_out, float* g_out) {
@@ -1027,9 +1105,9 @@ imrt_status plan_eval(imrt_plan* p, const float* x, double* G, float* z_out, flo
         CK(cudaMemcpyAsync(p->x_stage, x, sizeof(float) * p->n, cudaMemcpyDefault, s));
         xs = p->x_stage;
     }
-    TRY(run_eval(p, kFwdEval, xs, p->z_stage, p->r_stage, G ? p->dscratch : nullptr));
+    TRY(run_eval(p, kFwdEval, xs, p->z_stage, p->r_stage, G ? p->dscratch : nullptr, p->opt.precision));
     if (g_out) {
-        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage));
+        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage, p->opt.precision));
         CK(cudaMemcpyAsync(g_out, p->g_stage, sizeof(float) * p->n, cudaMemcpyDefault, s));
     }
     if (z_out) {
@@ -1081,11 +1159,14 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     info->nnz = p->nnz;
     const SellCopy& c = copy_of(p, p->opt.precision);
     info->sell_entries = c.entries;
-    info->t_entries = p->t_entries;
+    info->t_entries = p->opt.precision == IMRT_FP32 ? p->t_entries : p->tq_entries;
     const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = (int64_t)col_bytes(p->opt.precision);
     // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes, mask read)
     info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 9;
-    info->bwd_bytes = p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4;
+    info->bwd_bytes = p->opt.precision == IMRT_FP32
+                          ? p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4
+                          : p->nnz * (vb + 2) + ((int64_t)p->n * p->t_H + 1) * 8 + (int64_t)p->m * 4 +
+                                (int64_t)p->n * 4;
     info->device_bytes = p->device_bytes;
     FwdShape* sh = nullptr;
     if (get_shape(p, p->opt.precision, p->opt.k_trials, &sh) == IMRT_OK) {
@@ -1096,6 +1177,7 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     info->bwd_block = kBwdThreads;
     info->precision = p->opt.precision;
     info->k_trials = p->opt.k_trials;
+    if (ensure_lambda0_rule(p) != IMRT_OK) return IMRT_ECUDA;
     info->lambda0_rule = p->lambda0_rule;
     info->x1_scale = p->x1_scale;
     return IMRT_OK;

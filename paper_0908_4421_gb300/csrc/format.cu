@@ -251,13 +251,56 @@ __global__ void k_t_pad(const int64_t* __restrict__ col_len, const int64_t* __re
     }
 }
 
+// Reduced-precision beamlet-major copy with 16-bit voxel indices: row i is cut into
+// segments h = voxel >> 16 (the row is sorted, so each segment is one contiguous run,
+// found by binary search); each segment is padded to a multiple of 8 entries.
+__device__ __forceinline__ int64_t lower_bound_row(const int32_t* __restrict__ row, int64_t a, int64_t b, int32_t v) {
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (row[mid] < v) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
+__global__ void k_tq_count(const int64_t* __restrict__ t_off, const int32_t* __restrict__ t_row,
+                           const int64_t* __restrict__ col_len, int32_t n, int32_t H, int64_t* __restrict__ seg_len) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t a = t_off[i], b = a + col_len[i];
+    int64_t prev = a;
+    for (int h = 0; h < H; ++h) {
+        const int64_t e = h + 1 < H ? lower_bound_row(t_row, a, b, (h + 1) << 16) : b;
+        const int64_t len = e - prev;
+        seg_len[(int64_t)i * H + h] = (len + 7) & ~(int64_t)7;
+        prev = e;
+    }
+}
+
 template <int PREC>
-__global__ void k_t_quantize(const int64_t* __restrict__ t_off, const float* __restrict__ t_val, int32_t n,
-                             const float* __restrict__ inv_scale, void* out) {
+__global__ void k_tq_fill(const int64_t* __restrict__ t_off, const int32_t* __restrict__ t_row,
+                          const float* __restrict__ t_val, const int64_t* __restrict__ col_len, int32_t n, int32_t H,
+                          const int64_t* __restrict__ seg, const float* __restrict__ inv_scale, void* q_val,
+                          uint16_t* __restrict__ q_lo) {
     const int i = blockIdx.x;
     if (i >= n) return;
+    const int64_t a = t_off[i], b = a + col_len[i];
     const float s = inv_scale[i];
-    for (int64_t k = t_off[i] + threadIdx.x; k < t_off[i + 1]; k += blockDim.x) store_val<PREC>(out, k, t_val[k] * s);
+    for (int h = 0; h < H; ++h) {
+        const int64_t lo_b = lower_bound_row(t_row, a, b, h << 16);
+        const int64_t hi_b = h + 1 < H ? lower_bound_row(t_row, a, b, (h + 1) << 16) : b;
+        const int64_t dst0 = seg[(int64_t)i * H + h], dst1 = seg[(int64_t)i * H + h + 1];
+        for (int64_t k = dst0 + threadIdx.x; k < dst1; k += blockDim.x) {
+            const int64_t src = lo_b + (k - dst0);
+            if (src < hi_b) {
+                store_val<PREC>(q_val, k, t_val[src] * s);
+                q_lo[k] = (uint16_t)(t_row[src] & 0xffff);
+            } else {
+                store_val<PREC>(q_val, k, 0.0f);
+                q_lo[k] = 0;
+            }
+        }
+    }
 }
 
 __global__ void k_mask_counts(const uint8_t* __restrict__ mask, int32_t m, int32_t* __restrict__ counts) {
@@ -439,13 +482,28 @@ cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_quantize(int precision, const int64_t* t_off, const float* t_val, int32_t n,
-                              const float* inv_scale, void* out, cudaStream_t stream) {
+cudaError_t launch_tq_count(const int64_t* t_off, const int32_t* t_row, const int64_t* col_len, int32_t n, int32_t H,
+                            int64_t* seg_len, cudaStream_t stream) {
+    k_tq_count<<<blocks_for(n, 128), 128, 0, stream>>>(t_off, t_row, col_len, n, H, seg_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tq_fill(int precision, const int64_t* t_off, const int32_t* t_row, const float* t_val,
+                           const int64_t* col_len, int32_t n, int32_t H, const int64_t* seg, const float* inv_scale,
+                           void* q_val, uint16_t* q_lo, cudaStream_t stream) {
     switch (precision) {
-        case IMRT_FP16: k_t_quantize<IMRT_FP16><<<n, 256, 0, stream>>>(t_off, t_val, n, inv_scale, out); break;
-        case IMRT_BF16: k_t_quantize<IMRT_BF16><<<n, 256, 0, stream>>>(t_off, t_val, n, inv_scale, out); break;
-        case IMRT_FP8E4M3: k_t_quantize<IMRT_FP8E4M3><<<n, 256, 0, stream>>>(t_off, t_val, n, inv_scale, out); break;
-        default: return cudaErrorInvalidValue;
+        case IMRT_FP16:
+            k_tq_fill<IMRT_FP16><<<n, 256, 0, stream>>>(t_off, t_row, t_val, col_len, n, H, seg, inv_scale, q_val, q_lo);
+            break;
+        case IMRT_BF16:
+            k_tq_fill<IMRT_BF16><<<n, 256, 0, stream>>>(t_off, t_row, t_val, col_len, n, H, seg, inv_scale, q_val, q_lo);
+            break;
+        case IMRT_FP8E4M3:
+            k_tq_fill<IMRT_FP8E4M3><<<n, 256, 0, stream>>>(t_off, t_row, t_val, col_len, n, H, seg, inv_scale, q_val,
+                                                          q_lo);
+            break;
+        default:
+            return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

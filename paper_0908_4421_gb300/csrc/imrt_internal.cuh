@@ -72,7 +72,8 @@ struct DevState {
 struct SolveParams {
     double eps, alpha, delta, lambda0, x1_scale;
     int32_t max_iter, max_bt, x_init, k_trials, trace, n, n_pad, m, m_pad;
-    int32_t fwd_grid, warps;  // forward launch shape (partials per trial)
+    int32_t fwd_grid, gstride;  // forward grid; objective partials per trial
+    const double* gpart;        // objective partials of the forward shape in use
     unsigned long long timeout_ns;
     double* tr_G;
     double* tr_lam;
@@ -89,9 +90,30 @@ struct Vecs {
     float* z;        // kSets * m_pad
     float* r;        // kSets * m_pad
     float* g;        // n_pad
-    double* gpart;   // kMaxTrials * warps: per-warp objective partials
     double* dpart;   // kMaxTrials * fwd_grid: per-CTA ||x_t - x||^2 partials
     int32_t n_pad, m_pad;
+};
+
+// Forward work units: a whole slice, or one piece (a range of groups) of a
+// heavy slice. Warps take units dynamically, longest first, from an integer
+// counter. Pieces of a split slice write partial row sums; the last piece to
+// finish (integer arrival counter) adds them in piece order and runs the
+// epilogue. Every slice writes its own objective partial, so results do not
+// depend on which warp ran which unit.
+struct FwdUnits {
+    const int32_t* unit_slice;   // n_units, longest first
+    const int32_t* unit_g0;      // first group
+    const int32_t* unit_g1;      // one past the last group
+    const int32_t* unit_split;   // split id, or -1 for a whole slice
+    const int32_t* unit_piece;   // piece index within its split
+    const int32_t* split_pieces; // n_splits
+    const int32_t* split_base;   // n_splits: first partial row block of the split
+    float* partials;             // (sum of pieces) * 32 * k_trials
+    int32_t* counters;           // n_splits arrival counters, left at 0
+    double* gpart;               // k_trials * gstride objective partials, one per slice
+    int32_t* next_unit;          // dynamic schedule counter, reset by the last CTA
+    int32_t* ticket;             // CTAs finished in the current launch
+    int32_t n_units, n_splits, gstride;
 };
 
 struct FwdArgs {
@@ -99,7 +121,7 @@ struct FwdArgs {
     const int32_t* slice_len;    // n_slices (groups)
     const void* val;
     const void* col;
-    const int32_t* warp_slices;  // warps + 1
+    FwdUnits u;
     const uint8_t* mask;         // m_pad, permuted order
     const float* scale;          // n_pad per-beamlet value scale, or NULL (FP32)
     const Terms* terms;
@@ -108,18 +130,24 @@ struct FwdArgs {
     Vecs v;
     int32_t m, n, n_pad, m_pad;
     int32_t mode;        // FwdMode
+    int32_t control;     // 1: the last CTA runs the Armijo controller (inside a solve)
     const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x
     float* z_dst;        // kFwdEval / kFwdPower; NULL => accepted set
     float* r_dst;
-    double* gpart_dst;   // kFwdEval: NULL => v.gpart
 };
 
 struct BwdArgs {
     const int64_t* t_off;     // n + 1 (entries, padded rows)
     const void* val;
     const int32_t* row;       // permuted voxel indices
-    const int32_t* cta_rows;  // beamlet order, grouped by CTA
-    const int32_t* cta_ptr;   // grid + 1
+    const int32_t* order;     // beamlet rows, longest first (dynamic schedule)
+    int32_t* next_row;        // schedule counter, reset by the last CTA
+    int32_t* ticket;          // CTAs finished in the current launch
+    int32_t n;
+    // reduced precision: 16-bit voxel indices in segments of 65536 voxels
+    const int64_t* seg;       // n * H + 1 entry offsets (row i, segment h at i * H + h)
+    const uint16_t* lo;       // voxel index & 0xffff
+    int32_t H;
     const float* scale;       // n_pad or NULL
     DevState* st;
     const float* r_fixed;     // NULL => r of the accepted set
@@ -127,18 +155,13 @@ struct BwdArgs {
     int32_t m_pad, guard;     // guard: skip unless st->need_grad
 };
 
-struct CtlArgs {
-    DevState* st;
-    const SolveParams* sp;
-    Vecs v;
-    int32_t phase;  // 0: after the initial evaluation, 1: after a trial batch
-};
+// Sets the message imrt_last_error() returns on this thread (api.cu).
+void set_last_error_message(const char* msg);
 
 // Kernel launchers / function pointers (kernels.cu).
 const void* fwd_kernel(int precision, int k_trials);
 const void* bwd_kernel(int precision);
 const void* bwd_fixed_kernel(int precision);
-const void* ctl_kernel(int phase);
 const void* init_kernel();
 const void* finish_kernel();
 size_t fwd_smem_bytes(int n_pad, int k_trials, int precision);
@@ -162,8 +185,11 @@ cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, co
                                   int32_t m_pad, int32_t n, int32_t chunk_rows, const int32_t* counts,
                                   const int64_t* col_len, const int64_t* t_off, float* t_val, int32_t* t_row,
                                   cudaStream_t stream);
-cudaError_t launch_t_quantize(int precision, const int64_t* t_off, const float* t_val, int32_t n,
-                              const float* inv_scale, void* out, cudaStream_t stream);
+cudaError_t launch_tq_count(const int64_t* t_off, const int32_t* t_row, const int64_t* col_len, int32_t n, int32_t H,
+                            int64_t* seg_len, cudaStream_t stream);
+cudaError_t launch_tq_fill(int precision, const int64_t* t_off, const int32_t* t_row, const float* t_val,
+                           const int64_t* col_len, int32_t n, int32_t H, const int64_t* seg, const float* inv_scale,
+                           void* q_val, uint16_t* q_lo, cudaStream_t stream);
 cudaError_t launch_mask_counts(const uint8_t* mask, int32_t m, int32_t* counts, cudaStream_t stream);
 cudaError_t launch_unpermute(const float* zp, const int32_t* perm, int32_t m, float* z, cudaStream_t stream);
 cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* dst, cudaStream_t stream);

@@ -12,9 +12,10 @@
 //   k_transposed Sec. 2.3 "gradient calculation": g = D^T r (Eq. (3)-(4)) over
 //                the beamlet-major copy, one CTA per beamlet row at a time,
 //                deterministic shuffle + shared-memory reduction, no atomics.
-//   k_control    Sec. 2.2 steps 3-5 and Eq. (5): single-CTA FP64 reduction of
-//                the partials, the Armijo acceptance test, lambda / alpha, the
-//                stop test, and the CUDA-graph loop condition.
+//   controller   Sec. 2.2 steps 3-5 and Eq. (5), run by the last CTA of each
+//                forward launch inside a solve: FP64 reduction of the partials
+//                in a fixed order, the Armijo acceptance test, lambda / alpha,
+//                the stop test, and the CUDA-graph loop condition.
 //   k_init / k_finish  x_1 and the KKT residual.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -119,14 +120,15 @@ __device__ __forceinline__ float2 e4m3x2f(uint16_t w) {
 }
 
 // One row (one lane) of a slice: acc[q] = sum over the row's entries in storage order.
+// Groups [g0, g1) of one slice; lane = row within the slice.
 template <class F, int KT>
 __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, const void* __restrict__ col,
-                                              int64_t off, int L, int lane, const float* __restrict__ xs,
+                                              int64_t off, int g0, int L, int lane, const float* __restrict__ xs,
                                               float (&acc)[KT]) {
     if constexpr (F::GE == 4) {  // FP32 values, int32 columns
         const float4* vp = reinterpret_cast<const float4*>(static_cast<const float*>(val) + off) + lane;
         const int4* cp = reinterpret_cast<const int4*>(static_cast<const int32_t*>(col) + off) + lane;
-        int k = 0;
+        int k = g0;
         for (; k + 2 <= L; k += 2) {
             const float4 v0 = ld_stream(vp + (size_t)k * 32);
             const int4 c0 = ld_stream(cp + (size_t)k * 32);
@@ -152,9 +154,7 @@ __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, cons
     } else if constexpr (F::GE == 8) {  // 16-bit values, 16-bit columns
         const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + off) + lane;
         const uint4* cp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + lane;
-        for (int k = 0; k < L; ++k) {
-            const uint4 vw = ld_stream(vp + (size_t)k * 32);
-            const uint4 cw = ld_stream(cp + (size_t)k * 32);
+        auto group = [&](const uint4& vw, const uint4& cw) {
             const uint32_t vv[4] = {vw.x, vw.y, vw.z, vw.w};
             const uint32_t cc[4] = {cw.x, cw.y, cw.z, cw.w};
 #pragma unroll
@@ -163,11 +163,21 @@ __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, cons
                 fma_entry<KT>(f.x, (int)(cc[h] & 0xffffu), xs, acc);
                 fma_entry<KT>(f.y, (int)(cc[h] >> 16), xs, acc);
             }
+        };
+        int k = g0;
+        for (; k + 2 <= L; k += 2) {
+            const uint4 v0 = ld_stream(vp + (size_t)k * 32);
+            const uint4 c0 = ld_stream(cp + (size_t)k * 32);
+            const uint4 v1 = ld_stream(vp + (size_t)(k + 1) * 32);
+            const uint4 c1 = ld_stream(cp + (size_t)(k + 1) * 32);
+            group(v0, c0);
+            group(v1, c1);
         }
+        if (k < L) group(ld_stream(vp + (size_t)k * 32), ld_stream(cp + (size_t)k * 32));
     } else {  // FP8 e4m3 values (16 per 16 bytes), 16-bit columns
         const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(val) + off) + lane;
         const uint4* cp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + 2 * lane;
-        for (int k = 0; k < L; ++k) {
+        for (int k = g0; k < L; ++k) {
             const uint4 vw = ld_stream(vp + (size_t)k * 32);
             const uint4 c0 = ld_stream(cp + (size_t)k * 64);
             const uint4 c1 = ld_stream(cp + (size_t)k * 64 + 1);
@@ -198,14 +208,207 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ---------------------------------------------------------------------------
+// Deterministic single-CTA reductions.
+// ---------------------------------------------------------------------------
+__device__ float block_absmax(const float* __restrict__ p, int count, float* sh) {
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    float s = 0.0f;
+    for (int i = tid; i < count; i += blockDim.x) s = fmaxf(s, fabsf(__ldcg(p + i)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, o));
+    __syncthreads();
+    if (lane == 0) sh[wib] = s;
+    __syncthreads();
+    float t = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmaxf(t, sh[k]);
+    __syncthreads();
+    return t;
+}
+
+// Copies a POD struct between global and shared memory with all threads of the CTA.
+template <class T>
+__device__ __forceinline__ void cta_copy_in(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(dst)[i] = __ldcg(reinterpret_cast<const uint32_t*>(src) + i);
+}
+template <class T>
+__device__ __forceinline__ void cta_copy_out(T* dst, const T* src) {
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
+}
+
+__device__ __forceinline__ void finish_loop(DevState& S, const SolveParams& P, int status, int stop) {
+    S.status = status;
+    S.stop = stop;
+    S.done = 1;
+    if (P.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
+}
+
+// Armijo controller (Sec. 2.2 steps 3-5, Eq. (5)); phase 0 follows the initial evaluation.
+// Runs on every thread of one CTA after all partials of the launch are visible. The state and
+// parameters are staged in shared memory so the decision is one short sequential section.
+__device__ void control_step(int phase, DevState* st, const SolveParams* sp, const Vecs& v, int grid) {
+    __shared__ DevState S;
+    __shared__ SolveParams P;
+    __shared__ double red[32][2 * kMaxTrials];
+    __shared__ double sums[2 * kMaxTrials];
+    __shared__ float shf[32];
+    __shared__ int acc_set;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
+    cta_copy_in(&S, st);
+    cta_copy_in(&P, sp);
+    __syncthreads();
+    const int KT = phase == 0 ? 1 : P.k_trials;
+    const int W = P.gstride;
+    // all objective and step-length sums of the launch, fixed order per thread and per warp
+    for (int q = 0; q < KT; ++q) {
+        const double* g = P.gpart + (size_t)q * W;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int i = tid;
+        for (; i + 3 * (int)blockDim.x < W; i += 4 * blockDim.x) {
+            s0 += __ldcg(g + i);
+            s1 += __ldcg(g + i + blockDim.x);
+            s2 += __ldcg(g + i + 2 * blockDim.x);
+            s3 += __ldcg(g + i + 3 * blockDim.x);
+        }
+        for (; i < W; i += blockDim.x) s0 += __ldcg(g + i);
+        const double t = warp_sum((s0 + s1) + (s2 + s3));
+        if (lane == 0) red[wib][q] = t;
+        if (phase == 1) {
+            double d = 0.0;
+            for (int k = tid; k < grid; k += blockDim.x) d += __ldcg(v.dpart + (size_t)q * grid + k);
+            d = warp_sum(d);
+            if (lane == 0) red[wib][kMaxTrials + q] = d;
+        }
+    }
+    float ginf = 0.0f;
+    const bool want_g1 = phase == 1 && !S.g1_done;
+    if (want_g1) {
+        for (int i = tid; i < P.n; i += blockDim.x) ginf = fmaxf(ginf, fabsf(__ldcg(v.g + i)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ginf = fmaxf(ginf, __shfl_xor_sync(0xffffffffu, ginf, o));
+        if (lane == 0) shf[wib] = ginf;
+    }
+    __syncthreads();
+    if (tid < 2 * kMaxTrials) {
+        const int q = tid % kMaxTrials;
+        double t = 0.0;
+        if (q < KT && (tid < kMaxTrials || phase == 1))
+            for (int k = 0; k < nw; ++k) t += red[k][tid];
+        sums[tid] = t;
+    }
+    if (want_g1 && tid == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < nw; ++k) t = fmaxf(t, shf[k]);
+        shf[0] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        acc_set = -1;
+        if (phase == 0) {
+            const double G0 = sums[0];
+            S.G = G0;
+            S.G0 = G0;
+            S.passes = 1;
+            S.need_grad = 1;
+            if (P.tr_G) P.tr_G[0] = G0;
+            if (S.status != 0) finish_loop(S, P, S.status, 0);
+            else if (!isfinite(G0)) finish_loop(S, P, IMRT_ENUMERIC, 0);
+            else if (P.max_iter <= 0) finish_loop(S, P, 0, IMRT_STOP_MAXITER);
+            else if (G0 == 0.0) finish_loop(S, P, 0, IMRT_STOP_EXACT);
+        } else if (!S.done) {
+            S.need_grad = 0;
+            S.passes += 1;
+            if (!S.g1_done) {
+                S.g1_inf = shf[0];
+                S.g1_done = 1;
+            }
+            const double G = S.G;
+            double lam = S.lambda;
+            const int bt = S.bt;
+            int status = S.status, stop = 0, accepted = -1;
+            for (int q = 0; q < KT && status == 0; ++q) {
+                if (bt + q > P.max_bt) {
+                    status = IMRT_ELINESEARCH;
+                    break;
+                }
+                const double d2 = sums[kMaxTrials + q], Gt = sums[q];
+                if (d2 == 0.0) {
+                    stop = IMRT_STOP_STATIONARY;
+                    break;
+                }
+                if (!isfinite(Gt)) {
+                    status = IMRT_ENUMERIC;
+                    break;
+                }
+                if (Gt < G - (P.eps / lam) * d2) {  // Eq. (5), strict
+                    accepted = q;
+                    break;
+                }
+                lam = lam / P.alpha;  // step 4
+            }
+            if (accepted >= 0) {
+                const double Gt = sums[accepted];
+                const int set = (S.cur + 1 + accepted) % kSets;
+                const double rel = Gt > 0.0 ? fabs(Gt - G) / Gt : 0.0;
+                const int k = S.iter;
+                if (P.tr_lam) P.tr_lam[k] = lam;
+                if (P.tr_bt) P.tr_bt[k] = bt + accepted;
+                if (P.tr_G) P.tr_G[k + 1] = Gt;
+                S.total_bt += bt + accepted;
+                S.cur = set;
+                S.G = Gt;
+                S.rel = rel;
+                S.iter = k + 1;
+                S.lambda_acc = lam;
+                S.lambda = P.lambda0;  // step 2 of the next iteration
+                S.bt = 0;
+                S.need_grad = 1;
+                acc_set = set;
+                if (Gt == 0.0) stop = IMRT_STOP_EXACT;
+                else if (rel < P.delta) stop = IMRT_STOP_REL;  // step 5
+                else if (S.iter >= P.max_iter) stop = IMRT_STOP_MAXITER;
+            } else if (status == 0 && stop == 0) {
+                if (bt + KT - 1 >= P.max_bt) {
+                    status = IMRT_ELINESEARCH;
+                } else {
+                    S.bt = bt + KT;
+                    S.lambda = lam;
+                }
+            }
+            if (status == IMRT_ELINESEARCH) S.total_bt += P.max_bt;
+            if (status == 0 && stop == 0) {
+                if (P.timeout_ns && global_timer_ns() - S.t_start > P.timeout_ns) status = IMRT_ETIMEOUT;
+                else if (P.cancel && *P.cancel) status = IMRT_ECANCELLED;
+            }
+            if (status != 0 || stop != 0) finish_loop(S, P, status, stop);
+        }
+    }
+    __syncthreads();
+    cta_copy_out(st, &S);
+    if (P.trace >= 2 && P.tr_x) {
+        if (phase == 0) {
+            for (int i = tid; i < P.n; i += blockDim.x) P.tr_x[i] = __ldcg(v.x + i);
+        } else if (acc_set >= 0) {
+            const int k = S.iter;
+            for (int i = tid; i < P.n; i += blockDim.x)
+                P.tr_x[(size_t)k * P.n + i] = __ldcg(v.x + (size_t)acc_set * P.n_pad + i);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Forward pass (fused step + dose + penalty + objective partials).
 // ---------------------------------------------------------------------------
+#ifndef IMRT_FWD_MINB1
+#define IMRT_FWD_MINB1 3
+#endif
 template <class F, int KT>
-__global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, KT == 1 ? IMRT_FWD_MINB1 : (KT == 2 ? 2 : 1)) k_forward(const FwdArgs a) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ Terms T;
-    constexpr int WPB = kFwdThreads / 32;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int n_pad = a.n_pad;
     DevState* st = a.st;
@@ -242,10 +445,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdArgs a) {
             bulk_g2s(xs, xsrc, bytes, &bar);
         }
     }
-    if (!mbar_wait_bounded(&bar, 0)) {
-        if (tid == 0) atomicExch(&st->status, (int)IMRT_ECUDA);
-        return;
-    }
+    // A bounded wait: on expiry the CTA flags a device error, skips its work, and still
+    // reports to the ticket so the controller runs and ends the solve.
+    const bool failed = __syncthreads_or(!mbar_wait_bounded(&bar, 0)) != 0;
+    if (failed && tid == 0) atomicExch(&st->status, (int)IMRT_ECUDA);
 
     float lamf[KT];
     {
@@ -296,10 +499,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdArgs a) {
         }
     }
 
-    // Rows: this warp's contiguous range of slices.
-    const int W = gridDim.x * WPB;
-    const int w = blockIdx.x * WPB + wib;
-    const int s0 = a.warp_slices[w], s1 = a.warp_slices[w + 1];
+    // Rows: work units taken dynamically (longest first) from the schedule counter.
+    const FwdUnits& U = a.u;
     float* zq[KT];
     float* rq[KT];
 #pragma unroll
@@ -313,41 +514,88 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdArgs a) {
             rq[q] = a.r_dst ? a.r_dst : a.v.r + (size_t)st->cur * a.m_pad;
         }
     }
-    double gacc[KT];
-#pragma unroll
-    for (int q = 0; q < KT; ++q) gacc[q] = 0.0;
-
-    for (int s = s0; s < s1; ++s) {
+    int u = U.n_units;
+    if (!failed) {
+        if (lane == 0) u = atomicAdd(U.next_unit, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+    }
+    while (u < U.n_units) {
+        int u_next = 0;
+        if (lane == 0) u_next = atomicAdd(U.next_unit, 1);  // latency overlaps this unit
+        const int s = U.unit_slice[u];
+        const int sid = U.unit_split[u];
+        const int piece = U.unit_piece[u];
         const int64_t off = a.slice_off[s];
-        const int L = a.slice_len[s];
         float acc[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-        slice_row_dot<F, KT>(a.val, a.col, off, L, lane, xs, acc);
-        const int p = s * kSlice + lane;
-        if (p < a.m) {
-            const uint32_t bits = a.mask[p];
-            if (mode == kFwdPower) {
-                zq[0][p] = acc[0];
-                rq[0][p] = cdiag(bits, T) * acc[0];
-            } else {
+        slice_row_dot<F, KT>(a.val, a.col, off, U.unit_g0[u], U.unit_g1[u], lane, xs, acc);
+        bool finish = true;
+        if (sid >= 0) {
+            // piece of a split slice: publish the partial row sums; the last piece finishes the rows
+            float* part = U.partials + ((size_t)(U.split_base[sid] + piece) * kSlice + lane) * KT;
 #pragma unroll
-                for (int q = 0; q < KT; ++q) {
-                    double Fj;
-                    float rj;
-                    penalty(acc[q], bits, T, Fj, rj);
-                    zq[q][p] = acc[q];
-                    rq[q][p] = rj;
-                    gacc[q] += Fj;
+            for (int q = 0; q < KT; ++q) part[q] = acc[q];
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(&U.counters[sid], 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            const int P = U.split_pieces[sid];
+            finish = (old == P - 1);
+            if (finish) {
+                __threadfence();
+                const float* base = U.partials + (size_t)U.split_base[sid] * kSlice * KT;
+#pragma unroll
+                for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+                for (int k = 0; k < P; ++k) {
+#pragma unroll
+                    for (int q = 0; q < KT; ++q) acc[q] += __ldcg(base + ((size_t)k * kSlice + lane) * KT + q);
                 }
+                if (lane == 0) U.counters[sid] = 0;
             }
         }
-    }
-    double* gp = a.gpart_dst ? a.gpart_dst : a.v.gpart;
+        if (finish) {
+            const int p = s * kSlice + lane;
+            double Fq[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        const double s = warp_sum(gacc[q]);
-        if (lane == 0) gp[(size_t)q * W + w] = s;
+            for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+            if (p < a.m) {
+                const uint32_t bits = a.mask[p];
+                if (mode == kFwdPower) {
+                    zq[0][p] = acc[0];
+                    rq[0][p] = cdiag(bits, T) * acc[0];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < KT; ++q) {
+                        float rj;
+                        penalty(acc[q], bits, T, Fq[q], rj);
+                        zq[q][p] = acc[q];
+                        rq[q][p] = rj;
+                    }
+                }
+            }
+            // objective share of this slice (one partial per slice: scheduling-independent)
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                const double g = warp_sum(Fq[q]);
+                if (lane == 0) U.gpart[(size_t)q * U.gstride + s] = g;
+            }
+        }
+        u = __shfl_sync(0xffffffffu, u_next, 0);
+    }
+    // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (a.control) control_step(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, gridDim.x);
+    if (tid == 0) {
+        *U.next_unit = 0;
+        *U.ticket = 0;
     }
 }
 
@@ -356,29 +604,26 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdArgs a) {
 // ---------------------------------------------------------------------------
 template <int PREC>
 __device__ __forceinline__ float4 load_tval(const void* val, int64_t off, int k) {
-    if constexpr (PREC == IMRT_FP32) {
-        return ld_stream(reinterpret_cast<const float4*>(static_cast<const float*>(val) + off) + k);
-    } else if constexpr (PREC == IMRT_FP16 || PREC == IMRT_BF16) {
-        const uint2 w = __ldg(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(val) + off) + k);
-        const float2 a = PREC == IMRT_FP16 ? h2f(w.x) : b2f(w.x);
-        const float2 b = PREC == IMRT_FP16 ? h2f(w.y) : b2f(w.y);
-        return make_float4(a.x, a.y, b.x, b.y);
-    } else {
-        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(val) + off) + k);
-        const float2 a = e4m3x2f((uint16_t)(w & 0xffffu));
-        const float2 b = e4m3x2f((uint16_t)(w >> 16));
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
+    static_assert(PREC == IMRT_FP32, "the FP32 beamlet-major copy");
+    return ld_stream(reinterpret_cast<const float4*>(static_cast<const float*>(val) + off) + k);
 }
 
-// g_i = sum over row i of the beamlet-major copy of D_ij r_j, for this CTA's rows.
+// g_i = sum over row i of the beamlet-major copy of D_ij r_j. CTAs take rows dynamically,
+// longest first; a row is always reduced by one CTA in a fixed order, so g does not
+// depend on the schedule. The last CTA to finish resets the schedule counter.
 template <int PREC>
-__device__ __forceinline__ void transposed_rows(const BwdArgs& a, const float* __restrict__ r) {
+__device__ __forceinline__ bool transposed_rows(const BwdArgs& a, const float* __restrict__ r) {
     __shared__ float red[kBwdThreads / 32];
+    __shared__ int next_idx[2];
+    __shared__ int is_last;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    const int b = blockIdx.x;
-    for (int idx = a.cta_ptr[b]; idx < a.cta_ptr[b + 1]; ++idx) {
-        const int i = a.cta_rows[idx];
+    if (tid == 0) next_idx[0] = atomicAdd(a.next_row, 1);
+    __syncthreads();
+    int buf = 0;
+    int idx = next_idx[0];
+    while (idx < a.n) {
+        if (tid == 0) next_idx[buf ^ 1] = atomicAdd(a.next_row, 1);  // latency overlaps this row
+        const int i = a.order[idx];
         const int64_t off = a.t_off[i];
         const int L = (int)((a.t_off[i + 1] - off) >> 2);
         const int4* rp = reinterpret_cast<const int4*>(a.row + off);
@@ -415,7 +660,117 @@ __device__ __forceinline__ void transposed_rows(const BwdArgs& a, const float* _
             if (lane == 0) a.g[i] = a.scale ? t * a.scale[i] : t;
         }
         __syncthreads();
+        buf ^= 1;
+        idx = next_idx[buf];
     }
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (is_last && tid == 0) {
+        *a.next_row = 0;
+        *a.ticket = 0;
+    }
+    return is_last;
+}
+
+// Reduced-precision rows: groups of 8 entries, 16-bit voxel offsets inside segments of 65536
+// voxels; the row's segment boundaries are staged in shared memory.
+template <int PREC>
+__device__ __forceinline__ void load_q8(const void* val, int64_t e, float (&v)[8]) {
+    if constexpr (PREC == IMRT_FP8E4M3) {
+        const uint2 w = ld_stream_u2(reinterpret_cast<const uint2*>(static_cast<const uint8_t*>(val) + e));
+        const uint32_t ww[2] = {w.x, w.y};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 lo = e4m3x2f((uint16_t)(ww[h] & 0xffffu));
+            const float2 hi = e4m3x2f((uint16_t)(ww[h] >> 16));
+            v[4 * h + 0] = lo.x;
+            v[4 * h + 1] = lo.y;
+            v[4 * h + 2] = hi.x;
+            v[4 * h + 3] = hi.y;
+        }
+    } else {
+        const uint4 w = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + e));
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 f = PREC == IMRT_FP16 ? h2f(ww[h]) : b2f(ww[h]);
+            v[2 * h] = f.x;
+            v[2 * h + 1] = f.y;
+        }
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float* __restrict__ r) {
+    __shared__ float red[kBwdThreads / 32];
+    __shared__ int next_idx[2];
+    __shared__ int64_t sb[2][17];
+    __shared__ int is_last;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const int H = a.H;
+    if (tid == 0) next_idx[0] = atomicAdd(a.next_row, 1);
+    __syncthreads();
+    int buf = 0;
+    int idx = next_idx[0];
+    if (idx < a.n && tid <= H) sb[0][tid] = a.seg[(int64_t)a.order[idx] * H + tid];
+    __syncthreads();
+    while (idx < a.n) {
+        if (tid == 0) next_idx[buf ^ 1] = atomicAdd(a.next_row, 1);
+        const int i = a.order[idx];
+        const int64_t* b = sb[buf];
+        const int64_t r0 = b[0];
+        const int G = (int)((b[H] - r0) >> 3);
+        float acc0 = 0.0f, acc1 = 0.0f;
+        auto group = [&](int k, float& acc) {
+            const int64_t e = r0 + 8 * (int64_t)k;
+            int h = 0;
+            while (h + 1 < H && e >= b[h + 1]) ++h;
+            const float* rb = r + ((size_t)h << 16);
+            float v[8];
+            load_q8<PREC>(a.val, e, v);
+            const uint4 lw = ld_stream(reinterpret_cast<const uint4*>(a.lo + e));
+            const uint32_t l4[4] = {lw.x, lw.y, lw.z, lw.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                acc = fmaf(v[2 * t], __ldg(rb + (l4[t] & 0xffffu)), acc);
+                acc = fmaf(v[2 * t + 1], __ldg(rb + (l4[t] >> 16)), acc);
+            }
+        };
+        int k = tid;
+        for (; k + kBwdThreads < G; k += 2 * kBwdThreads) {
+            group(k, acc0);
+            group(k + kBwdThreads, acc1);
+        }
+        if (k < G) group(k, acc0);
+        const float acc = warp_sum(acc0 + acc1);
+        if (lane == 0) red[wib] = acc;
+        __syncthreads();  // next_idx[buf ^ 1] is visible after this barrier
+        const int nidx = next_idx[buf ^ 1];
+        if (nidx < a.n && tid <= H) sb[buf ^ 1][tid] = a.seg[(int64_t)a.order[nidx] * H + tid];
+        if (wib == 0) {
+            float t = lane < kBwdThreads / 32 ? red[lane] : 0.0f;
+            t = warp_sum(t);
+            if (lane == 0) a.g[i] = t * a.scale[i];
+        }
+        __syncthreads();
+        buf ^= 1;
+        idx = nidx;
+    }
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (is_last && tid == 0) {
+        *a.next_row = 0;
+        *a.ticket = 0;
+    }
+    return is_last;
+}
+
+template <int PREC>
+__device__ __forceinline__ bool transposed_any(const BwdArgs& a, const float* __restrict__ r) {
+    if constexpr (PREC == IMRT_FP32) return transposed_rows<PREC>(a, r);
+    else return transposed_rows_q<PREC>(a, r);
 }
 
 // Inside the solve: r of the accepted set, skipped when g is already current.
@@ -423,53 +778,14 @@ template <int PREC>
 __global__ void __launch_bounds__(kBwdThreads) k_transposed_cur(const BwdArgs a, const float* __restrict__ r_sets) {
     DevState* st = a.st;
     if (a.guard && !st->need_grad) return;
-    transposed_rows<PREC>(a, r_sets + (size_t)st->cur * a.m_pad);
-    if (a.guard && blockIdx.x == 0 && threadIdx.x == 0) st->grad_passes += 1;
+    const bool last = transposed_any<PREC>(a, r_sets + (size_t)st->cur * a.m_pad);
+    if (a.guard && last && threadIdx.x == 0) st->grad_passes += 1;
 }
 
 // Outside the solve: r given explicitly.
 template <int PREC>
 __global__ void __launch_bounds__(kBwdThreads) k_transposed(const BwdArgs a) {
-    transposed_rows<PREC>(a, a.r_fixed);
-}
-
-// ---------------------------------------------------------------------------
-// Deterministic single-CTA reductions.
-// ---------------------------------------------------------------------------
-__device__ double block_sum(const double* __restrict__ p, int count, double* sh) {
-    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    double s = 0.0;
-    for (int i = tid; i < count; i += blockDim.x) s += p[i];
-    s = warp_sum(s);
-    __syncthreads();
-    if (lane == 0) sh[wib] = s;
-    __syncthreads();
-    double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
-    __syncthreads();
-    return t;
-}
-
-__device__ float block_absmax(const float* __restrict__ p, int count, float* sh) {
-    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    float s = 0.0f;
-    for (int i = tid; i < count; i += blockDim.x) s = fmaxf(s, fabsf(p[i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, o));
-    __syncthreads();
-    if (lane == 0) sh[wib] = s;
-    __syncthreads();
-    float t = 0.0f;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmaxf(t, sh[k]);
-    __syncthreads();
-    return t;
-}
-
-__device__ __forceinline__ void finish_loop(DevState* st, const SolveParams* sp, int status, int stop) {
-    st->status = status;
-    st->stop = stop;
-    st->done = 1;
-    if (sp->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)sp->cond, 0u);
+    transposed_any<PREC>(a, a.r_fixed);
 }
 
 // x_1 (Initialization of Sec. 2.2) and the solver state.
@@ -511,120 +827,6 @@ __global__ void __launch_bounds__(kCtlThreads) k_init(DevState* st, const SolveP
         st->g1_done = 0;
         st->launches = 0;
         st->t_start = global_timer_ns();
-    }
-}
-
-// Armijo controller (Sec. 2.2 steps 3-5, Eq. (5)); phase 0 follows the initial evaluation.
-__global__ void __launch_bounds__(kCtlThreads) k_control(const CtlArgs a) {
-    __shared__ double sh[kCtlThreads / 32];
-    __shared__ float shf[kCtlThreads / 32];
-    __shared__ double Gq[kMaxTrials], Dq[kMaxTrials];
-    __shared__ int acc_set;
-    DevState* st = a.st;
-    const SolveParams* sp = a.sp;
-    const int W = sp->warps, grid = sp->fwd_grid;
-    if (a.phase == 0) {
-        const double G0 = block_sum(a.v.gpart, W, sh);
-        if (threadIdx.x == 0) {
-            st->G = G0;
-            st->G0 = G0;
-            st->passes = 1;
-            st->need_grad = 1;
-            if (sp->tr_G) sp->tr_G[0] = G0;
-            if (st->status != 0) finish_loop(st, sp, st->status, 0);
-            else if (!isfinite(G0)) finish_loop(st, sp, IMRT_ENUMERIC, 0);
-            else if (sp->max_iter <= 0) finish_loop(st, sp, 0, IMRT_STOP_MAXITER);
-            else if (G0 == 0.0) finish_loop(st, sp, 0, IMRT_STOP_EXACT);
-        }
-        if (sp->trace >= 2 && sp->tr_x)
-            for (int i = threadIdx.x; i < sp->n; i += blockDim.x) sp->tr_x[i] = a.v.x[i];
-        return;
-    }
-    if (st->done) return;
-    const int KT = sp->k_trials;
-    for (int q = 0; q < KT; ++q) {
-        const double gsum = block_sum(a.v.gpart + (size_t)q * W, W, sh);
-        const double dsum = block_sum(a.v.dpart + (size_t)q * grid, grid, sh);
-        if (threadIdx.x == 0) {
-            Gq[q] = gsum;
-            Dq[q] = dsum;
-        }
-    }
-    float ginf = 0.0f;
-    if (!st->g1_done) ginf = block_absmax(a.v.g, sp->n, shf);
-    if (threadIdx.x == 0) {
-        acc_set = -1;
-        st->need_grad = 0;
-        st->passes += 1;
-        if (!st->g1_done) {
-            st->g1_inf = ginf;
-            st->g1_done = 1;
-        }
-        const double G = st->G;
-        double lam = st->lambda;
-        const int bt = st->bt;
-        int status = 0, stop = 0, accepted = -1;
-        for (int q = 0; q < KT; ++q) {
-            if (bt + q > sp->max_bt) {
-                status = IMRT_ELINESEARCH;
-                break;
-            }
-            const double d2 = Dq[q], Gt = Gq[q];
-            if (d2 == 0.0) {
-                stop = IMRT_STOP_STATIONARY;
-                break;
-            }
-            if (!isfinite(Gt)) {
-                status = IMRT_ENUMERIC;
-                break;
-            }
-            if (Gt < G - (sp->eps / lam) * d2) {
-                accepted = q;
-                break;
-            }
-            lam = lam / sp->alpha;
-        }
-        if (accepted >= 0) {
-            const double Gt = Gq[accepted];
-            const int set = (st->cur + 1 + accepted) % kSets;
-            const double rel = Gt > 0.0 ? fabs(Gt - G) / Gt : 0.0;
-            const int k = st->iter;
-            if (sp->tr_lam) sp->tr_lam[k] = lam;
-            if (sp->tr_bt) sp->tr_bt[k] = bt + accepted;
-            if (sp->tr_G) sp->tr_G[k + 1] = Gt;
-            st->total_bt += bt + accepted;
-            st->cur = set;
-            st->G = Gt;
-            st->rel = rel;
-            st->iter = k + 1;
-            st->lambda_acc = lam;
-            st->lambda = sp->lambda0;
-            st->bt = 0;
-            st->need_grad = 1;
-            acc_set = set;
-            if (Gt == 0.0) stop = IMRT_STOP_EXACT;
-            else if (rel < sp->delta) stop = IMRT_STOP_REL;
-            else if (st->iter >= sp->max_iter) stop = IMRT_STOP_MAXITER;
-        } else if (status == 0 && stop == 0) {
-            if (bt + KT - 1 >= sp->max_bt) {
-                status = IMRT_ELINESEARCH;
-            } else {
-                st->bt = bt + KT;
-                st->lambda = lam;
-            }
-        }
-        if (status == IMRT_ELINESEARCH) st->total_bt += sp->max_bt;
-        if (status == 0 && stop == 0) {
-            if (sp->timeout_ns && global_timer_ns() - st->t_start > sp->timeout_ns) status = IMRT_ETIMEOUT;
-            else if (sp->cancel && *sp->cancel) status = IMRT_ECANCELLED;
-        }
-        if (status != 0 || stop != 0) finish_loop(st, sp, status, stop);
-    }
-    __syncthreads();
-    if (acc_set >= 0 && sp->trace >= 2 && sp->tr_x) {
-        const int k = st->iter;
-        for (int i = threadIdx.x; i < sp->n; i += blockDim.x)
-            sp->tr_x[(size_t)k * sp->n + i] = a.v.x[(size_t)acc_set * sp->n_pad + i];
     }
 }
 
@@ -697,7 +899,6 @@ const void* bwd_fixed_kernel(int precision) {
     }
 }
 
-const void* ctl_kernel(int) { return (const void*)k_control; }
 const void* init_kernel() { return (const void*)k_init; }
 const void* finish_kernel() { return (const void*)k_finish; }
 

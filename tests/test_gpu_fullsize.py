@@ -1,0 +1,65 @@
+"""Parity at the benchmark's full size (192x160x96 voxels at 2.5 mm, 9 beams, 2.5 mm beamlets:
+~61M nonzeros), in the launch configurations bench.py times."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0908_4421_gb300 import Options, Plan, phantom
+
+pytestmark = pytest.mark.gpu
+
+WORKLOAD = "prostate-192x160x96-2.5mm-9beam-2.5mm-beamlets"
+
+
+@pytest.fixture(scope="module")
+def big():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0908_4421_gb300 import build as cuda_build
+    cuda_build.build()
+    case = phantom.make_case(phantom.WORKLOADS[WORKLOAD])
+    return case
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_full_size_eval(big):
+    case = big
+    orc = oracle.get()
+    threads = os.cpu_count() or 1
+    x1 = orc.initial_point(case).astype(np.float32)
+    with Plan.from_case(case, device=True) as plan:
+        G, z, g = plan.eval(x1)
+        info = plan.info()
+    G_ref, z_ref, _, g_ref = orc.eval(case, x1.astype(np.float64), threads=threads)
+    assert info["nnz"] == case.nnz and case.nnz > 50_000_000
+    assert rel(z, z_ref) <= 1e-5
+    assert abs(G - G_ref) <= 1e-5 * G_ref
+    assert rel(g, g_ref) <= 1e-4
+    # every voxel row, elementwise: |z - z_ref| <= 1e-5 |z_ref| + 1e-6 max|z|
+    assert np.all(np.abs(z - z_ref) <= 1e-5 * np.abs(z_ref) + 1e-6 * np.abs(z_ref).max())
+
+
+@pytest.mark.parametrize("k_trials", [1, 4])
+def test_full_size_iterations(big, k_trials):
+    case = big
+    orc = oracle.get()
+    threads = os.cpu_count() or 1
+    with Plan.from_case(case, Options(max_iter=4, trace=2, k_trials=k_trials), device=True) as plan:
+        lam0 = plan.info()["lambda0_rule"]
+        res = plan.solve()
+        G, lam, bt, xs = plan.trace(res.iterations, with_x=True)
+    ref = orc.solve(case, lambda0=lam0, max_iter=4, threads=threads, trace=True, trace_x=True)
+    assert res.iterations == ref.iterations == 4
+    np.testing.assert_array_equal(bt, ref.backtrack_trace)
+    for k in range(res.iterations + 1):
+        assert rel(orc.dose(case, xs[k].astype(np.float64), threads=threads),
+                   orc.dose(case, ref.xs[k], threads=threads)) <= 1e-5
+        assert abs(G[k] - ref.G[k]) <= 1e-5 * ref.G[k]
