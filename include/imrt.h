@@ -211,6 +211,34 @@ imrt_status plan_info(const imrt_plan* plan, imrt_plan_info* info);
  */
 imrt_status plan_cancel(imrt_plan* plan);
 
+/*
+ * Dose and objective at x straight from a device CSR, without allocating any
+ * memory. The paper has no counterpart: this entry point serves callers that
+ * cannot allocate device memory when they evaluate a plan, such as code that is
+ * capturing a stream into a CUDA graph (cudaMalloc is not allowed during a
+ * global-mode capture), treatment-delivery controllers whose device memory is
+ * reserved once at start-up, or host frameworks that own every allocation. It
+ * calls no cudaMalloc, cudaFree or allocating library routine; its scratch is a
+ * file-scope device array of about 129 KiB that every GPU loading the library
+ * holds until the process exits.
+ *   D           voxel-major CSR, device pointers (D->on_device must be 1);
+ *               m <= 16,777,216 voxels, else IMRT_EUNSUPPORTED.
+ *   structures  m bytes, device: bit s set => voxel in structure s.
+ *   n_structures, thresholds, weights: as for plan_create (host arrays).
+ *   x           n beamlet intensities, device.
+ *   z_out       m floats, device, in the caller's row order; NULL to skip.
+ *   G_out       the FP64 objective, host.
+ *   stream      cudaStream_t; the call returns after its work finished.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call clears the parts of the scratch that must start at zero. All calls
+ * on one device share the scratch: calls whose work overlaps on the GPU (other
+ * streams or host threads) race and must be serialised by the caller.
+ */
+imrt_status imrt_eval_csr_noalloc(const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
+                                  const float* thresholds, const float* weights, const float* x, float* z_out,
+                                  double* G_out, void* stream);
+
 /* Frees the plan and all its device memory. NULL-safe. */
 void plan_destroy(imrt_plan* plan);
 
