@@ -194,11 +194,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(phantom.WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
-    ap.add_argument("--k-trials", type=int, default=0, help="0: pick the fastest of 1, 2, 4")
+    ap.add_argument("--k-trials", type=int, default=0, help="0: pick the faster of 1, 2")
+    ap.add_argument("--variant", type=int, default=-1, help="forward kernel: 0 warp streaming, 1 bulk-copy, -1 tune")
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision forms")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -231,22 +233,25 @@ def main():
     lam0 = info["lambda0_rule"]
 
     # k_trials: evaluated step sizes per pass over D (identical results, fewer passes)
-    candidates = [args.k_trials] if args.k_trials else [1, 2, 4]
-    best_kt, best_t = candidates[0], float("inf")
+    # tuning: forward kernel variant and k_trials (identical results; only speed differs)
+    kts = [args.k_trials] if args.k_trials else [1, 2]
+    variants = [args.variant] if args.variant >= 0 else [0, 1]
+    candidates = [(v, kt) for v in variants for kt in kts]
+    best_kt, best_variant, best_t = kts[0], variants[0], float("inf")
     tuned = {}
     if len(candidates) > 1:
-        for kt in candidates:
-            plan.set_options(k_trials=kt)
+        for v, kt in candidates:
+            plan.set_options(k_trials=kt, kernel_variant=v)
             plan.solve()
             ts = []
             for _ in range(3):
                 t0 = time.perf_counter()
                 plan.solve()
                 ts.append(time.perf_counter() - t0)
-            tuned[kt] = statistics.median(ts)
-            if tuned[kt] < best_t:
-                best_kt, best_t = kt, tuned[kt]
-    plan.set_options(k_trials=best_kt)
+            tuned[f"v{v}k{kt}"] = statistics.median(ts)
+            if tuned[f"v{v}k{kt}"] < best_t:
+                best_kt, best_variant, best_t = kt, v, tuned[f"v{v}k{kt}"]
+    plan.set_options(k_trials=best_kt, kernel_variant=best_variant)
     info = plan.info()
 
     for _ in range(args.warmup):
@@ -307,7 +312,7 @@ def main():
     h2d = h_rp.nbytes + h_col.nbytes + h_val.nbytes + h_mask.nbytes
     d2h = x_out.nbytes + z_out.nbytes
     e2e_opts = Options(max_iter=args.max_iter, delta=1e-6, precision=prec, k_trials=best_kt,
-                       stream=stream.cuda_stream)
+                       kernel_variant=best_variant, stream=stream.cuda_stream)
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         barrier()
@@ -330,6 +335,54 @@ def main():
                          f"({det['seconds_timed']} s), per-iteration time scaled to the GPU's "
                          f"{res.iterations} iterations plus set-up"}
 
+    # the reduced-precision forms (FP16 / BF16 / FP8-e4m3 storage, FP32 accumulation, FP64
+    # objective and Armijo test, FP32 polish): time-to-plan, bandwidth, errors vs the FP64 oracle
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        import oracle
+        orc = oracle.get()
+        ref = orc.solve(case, lambda0=lam0, max_iter=args.max_iter, delta=1e-6, threads=os.cpu_count() or 1,
+                        trace=False)
+        z_ref = orc.dose(case, ref.x, threads=os.cpu_count() or 1)
+
+        def errors(x):
+            z = plan.dose(x)
+            G = orc.eval(case, x.astype(np.float64), gradient=False, threads=os.cpu_count() or 1)[0]
+            return {"objective_rel_err": (G - ref.objective) / ref.objective,
+                    "dose_rel_err": float(np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref)),
+                    "x_rel_err": float(np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x))}
+
+        forms = {"oracle_fp64": {"objective": ref.objective, "iterations": ref.iterations},
+                 "fp32": {"time_to_plan_s": step_s, "objective": res.objective, **errors(plan.get_x())}}
+        for name in ("fp16", "bf16", "fp8"):
+            with torch.cuda.stream(stream):
+                fp = Plan.from_case(case, Options(max_iter=args.max_iter, delta=1e-6, precision=PRECISIONS[name],
+                                                  k_trials=best_kt, kernel_variant=best_variant,
+                                                  lambda0=lam0, stream=stream.cuda_stream), device=True)
+            for _ in range(2):
+                fp.solve()
+            ts = []
+            for _ in range(5):
+                ev0.record(stream)
+                r_ = fp.solve()
+                ev1.record(stream)
+                ev1.synchronize()
+                ts.append(ev0.elapsed_time(ev1) / 1e3)
+            x_ = fp.get_x()
+            fp.set_options(mode=L.MODE_HOST, profile=1)
+            rp = fp.solve()
+            fi = fp.info()
+            fp.close()
+            f_s = rp.fwd_ms / max(rp.fwd_launches, 1) / 1e3
+            b_s = rp.bwd_ms / max(rp.bwd_launches, 1) / 1e3
+            forms[name] = {"time_to_plan_s": statistics.mean(ts), "speedup_vs_fp32": step_s / statistics.mean(ts),
+                           "iterations": r_.iterations, "polish_iterations": r_.polish_iterations,
+                           "objective": r_.objective,
+                           "k_forward_gbs": fi["fwd_bytes"] / f_s / 1e9 if f_s > 0 else None,
+                           "k_transposed_gbs": fi["bwd_bytes"] / b_s / 1e9 if b_s > 0 else None,
+                           "bytes_per_pass": {"forward": fi["fwd_bytes"], "transposed": fi["bwd_bytes"]},
+                           **errors(x_)}
+
     traffic = profiled_traffic(dominant, args.workload)
     lat = sorted(times)
     line = {
@@ -339,7 +392,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "m": case.m, "n": case.n, "nnz": case.nnz,
                    "precision": args.precision, "k_trials": best_kt,
-                   "k_trials_tuned_s": {str(k): round(v, 5) for k, v in tuned.items()}, "max_iter": args.max_iter, "delta": 1e-6,
+                   "kernel_variant": best_variant,
+                   "tuned_s": {k: round(v, 5) for k, v in tuned.items()}, "max_iter": args.max_iter, "delta": 1e-6,
                    "lambda0": f"rule 8/L = {lam0:.6g}",
                    "l2": f"inputs larger than L2: D held twice, {(info['sell_entries'] + info['t_entries']) * 8 / 1e9:.2f} GB > 129 MB",
                    "parallelism": f"replicas x{world}"},
@@ -356,6 +410,7 @@ def main():
         "grad_passes": res.grad_passes, "objective": res.objective, "stop_reason": res.stop_reason,
         "latency_p50_s": lat[len(lat) // 2], "latency_p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
         "cpu_baseline": cpu,
+        "forms": forms,
         "e2e": None if e2e_s is None else {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "includes": "plan_create from pinned host CSR (copy, layouts, step-size rule), plan_solve, "
                             "plan_get_x and plan_dose to host"},

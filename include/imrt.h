@@ -101,7 +101,7 @@ typedef struct {
     int32_t profile;        /* 1: time every forward and transposed-product launch with CUDA events */
     int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
     int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy; default 20 */
-    int32_t reserved;
+    int32_t kernel_variant; /* forward pass: 0 warp streaming (default), 1 bulk-copy (TMA) pipeline */
     double timeout_ms;      /* 0: none; else the device loop stops with IMRT_ETIMEOUT */
     void* stream;           /* cudaStream_t */
 } imrt_options;
@@ -168,6 +168,20 @@ imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_
 imrt_status plan_set_options(imrt_plan* plan, const imrt_options* opt);
 
 /*
+ * Adds Eq. (1)'s per-voxel terms as printed, around a per-voxel dose T_j (the
+ * original plan's dose, Sec. 2.1): every voxel gets w_over * max(0, z_j - T_j)^2,
+ * every voxel of V_T also w_under * max(0, T_j - z_j)^2, each divided by m and
+ * |V_T| when normalise is 1. They add to the per-structure terms (give those
+ * zero weights for the paper's model alone). With no under-dose structure the
+ * x_init = 0 rule uses s = sum_VT T_j / sum_VT (D 1)_j.
+ *   dose    m floats (host or device), caller's row order; NULL removes the terms.
+ *   target  m bytes (host or device): nonzero => voxel in V_T; NULL => V_T empty.
+ * Errors: IMRT_EINVAL (non-finite dose, negative weights).
+ */
+imrt_status plan_set_voxel_targets(imrt_plan* plan, const float* dose, const uint8_t* target, float w_under,
+                                   float w_over, int32_t normalise);
+
+/*
  * Runs the projected-gradient Armijo loop (Sec. 2.2, steps 1-5) from x_1.
  *   x0   n beamlet intensities (host or device), read only when x_init = 2;
  *        must be >= 0. May be NULL otherwise.
@@ -177,7 +191,23 @@ imrt_status plan_set_options(imrt_plan* plan, const imrt_options* opt);
  */
 imrt_status plan_solve(imrt_plan* plan, const float* x0, imrt_result* res);
 
-/* z = D x (Sec. 2.1) with the FP32 copy of D. x: n (host or device), NULL => the plan's current x.
+/*
+ * Solves several plans (Sec. 2.2, steps 1-5, each plan independently) in one
+ * CUDA-graph launch: every plan's solve is one branch of the graph, so plans of
+ * different sizes run concurrently and finish independently; each keeps its own
+ * options (precision, k_trials, x_init, max_iter, ...), and reduced-precision
+ * plans get their FP32 polish in a second launch.
+ *   plans    count distinct plan handles.
+ *   x0s      NULL, or count pointers read for plans with x_init = 2.
+ *   results  count results (host).
+ *   stream   cudaStream_t of the launch; the call returns when all solves ended.
+ * Returns IMRT_OK when every solve succeeded, else the first failing status
+ * (each result carries its own).
+ */
+imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float* const* x0s, imrt_result* results,
+                             void* stream);
+
+/* z = D x (Sec. 2.1) with the FP32 copy of D./* z = D x (Sec. 2.1) with the FP32 copy of D. x: n (host or device), NULL => the plan's current x.
    z_out: m (host or device). */
 imrt_status plan_dose(imrt_plan* plan, const float* x, float* z_out);
 

@@ -44,7 +44,9 @@ class _Problem(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
                 ("mask", ctypes.c_void_p), ("n_structures", ctypes.c_int32),
-                ("thresholds", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+                ("thresholds", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("vt", ctypes.c_void_p), ("vt_target", ctypes.c_void_p),
+                ("vt_wu", ctypes.c_double), ("vt_wo", ctypes.c_double), ("vt_normalise", ctypes.c_int32)]
 
 
 class _Params(ctypes.Structure):
@@ -90,9 +92,18 @@ class Oracle:
                     mask=np.ascontiguousarray(case.mask, np.uint8),
                     thr=np.ascontiguousarray(case.thresholds, np.float32),
                     w=np.ascontiguousarray(case.weights, np.float32))
+        vt = getattr(case, "voxel_targets", None)
+        vt_ptr = vt_tg = None
+        wu = wo = 0.0
+        norm = 0
+        if vt is not None:
+            keep["vt"] = np.ascontiguousarray(vt.dose, np.float32)
+            keep["vtg"] = np.ascontiguousarray(vt.target, np.uint8)
+            vt_ptr, vt_tg = keep["vt"].ctypes.data, keep["vtg"].ctypes.data
+            wu, wo, norm = float(vt.w_under), float(vt.w_over), int(vt.normalise)
         p = _Problem(case.m, case.n, keep["row_ptr"].ctypes.data, keep["col"].ctypes.data,
                      keep["val"].ctypes.data, keep["mask"].ctypes.data, case.n_structures,
-                     keep["thr"].ctypes.data, keep["w"].ctypes.data)
+                     keep["thr"].ctypes.data, keep["w"].ctypes.data, vt_ptr, vt_tg, wu, wo, norm)
         return p, keep
 
     def eval(self, case, x, gradient: bool = True, threads: int = 0):

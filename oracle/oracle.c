@@ -24,6 +24,11 @@
  *       G(x_t) < G(x_k) - (eps/lambda) * ||x_t - x_k||^2, and the relative
  *       change stop test |G_new - G_old| / G_new < delta.
  *
+ * Per-voxel targets (Eq. (1) as printed, T_j = the original plan's dose): when
+ * the problem carries vt, every voxel gets an over-dose term w_o max(0, z - T_j)^2
+ * and every voxel of V_T an under-dose term w_u max(0, T_j - z)^2 (divided by m
+ * and |V_T| when vt_normalise is set), added to the per-structure terms.
+ *
  * Readings where the paper is silent (each restated in the design notes):
  *   - The initial point (x_init = 0) is s * 1 with s = T_under / mean over the
  *     first under-dose structure of (D 1)_j; x_init = 1 is zeros, 2 is given.
@@ -59,6 +64,11 @@ typedef struct {
     int32_t n_structures;
     const float* thresholds; /* [S][2] (under, over); NaN => no such term */
     const float* weights;    /* [S][2] */
+    /* Eq. (1) with a per-voxel dose T_j (the original plan's dose): NULL => none */
+    const float* vt;         /* m */
+    const uint8_t* vt_target; /* m: 1 => voxel in V_T (under-dose term) */
+    double vt_wu, vt_wo;     /* weights of the under / over terms */
+    int32_t vt_normalise;    /* 1: divide by |V_T| and m */
 } orc_problem;
 
 typedef struct {
@@ -103,6 +113,18 @@ void orc_term_coeffs(const orc_problem* P, double* T, double* c) {
     }
 }
 
+/* Coefficients of the per-voxel terms of Eq. (1): under-dose on V_T, over-dose on all voxels. */
+void orc_vt_coeffs(const orc_problem* P, double* cu, double* co) {
+    *cu = 0.0;
+    *co = 0.0;
+    if (!P->vt) return;
+    int64_t nt = 0;
+    for (int32_t j = 0; j < P->m; ++j)
+        if (P->vt_target && P->vt_target[j]) ++nt;
+    *cu = (nt > 0 && P->vt_target) ? P->vt_wu / (P->vt_normalise ? (double)nt : 1.0) : 0.0;
+    *co = P->m > 0 ? P->vt_wo / (P->vt_normalise ? (double)P->m : 1.0) : 0.0;
+}
+
 /* z = D x over the voxel-major rows (Sec. 2.1: z_j = sum_i D_ij x_i). */
 void orc_dose(const orc_problem* P, const double* x, double* z) {
 #pragma omp parallel for schedule(static)
@@ -120,8 +142,27 @@ void orc_dose(const orc_problem* P, const double* x, double* z) {
  */
 double orc_objective(const orc_problem* P, const double* T, const double* c, const double* z, double* r) {
     double G = 0.0;
+    double vcu, vco;
+    orc_vt_coeffs(P, &vcu, &vco);
     for (int32_t j = 0; j < P->m; ++j) {
         double F = 0.0, d = 0.0;
+        if (P->vt) {
+            const double t = (double)P->vt[j];
+            if (vco != 0.0) {
+                double e = z[j] - t;
+                if (e > 0.0) {
+                    F += vco * e * e;
+                    d += 2.0 * vco * e;
+                }
+            }
+            if (vcu != 0.0 && P->vt_target[j]) {
+                double e = t - z[j];
+                if (e > 0.0) {
+                    F += vcu * e * e;
+                    d -= 2.0 * vcu * e;
+                }
+            }
+        }
         for (int32_t s = 0; s < P->n_structures; ++s) {
             if (!((P->mask[j] >> s) & 1u)) continue;
             if (c[2 * s] != 0.0) {
@@ -187,6 +228,26 @@ void orc_initial_x(const orc_problem* P, const double* T, const double* c, int32
     int32_t s_star = -1;
     for (int32_t s = 0; s < P->n_structures && s_star < 0; ++s)
         if (c[2 * s] != 0.0) s_star = s;
+    double vcu, vco;
+    orc_vt_coeffs(P, &vcu, &vco);
+    if (s_star < 0 && vcu != 0.0) {
+        /* voxel targets only: s = sum over V_T of T_j / sum over V_T of (D 1)_j */
+        double* ones = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        double* z = (double*)malloc(sizeof(double) * (size_t)(P->m > 0 ? P->m : 1));
+        for (int32_t i = 0; i < n; ++i) ones[i] = 1.0;
+        orc_dose(P, ones, z);
+        double st = 0.0, sz = 0.0;
+        for (int32_t j = 0; j < P->m; ++j)
+            if (P->vt_target[j]) {
+                st += (double)P->vt[j];
+                sz += z[j];
+            }
+        if (sz > 0.0)
+            for (int32_t i = 0; i < n; ++i) x[i] = st / sz;
+        free(ones);
+        free(z);
+        return;
+    }
     if (s_star < 0) return;
     double* ones = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double* z = (double*)malloc(sizeof(double) * (size_t)(P->m > 0 ? P->m : 1));
@@ -219,12 +280,15 @@ double orc_lambda0_rule(const orc_problem* P, const int64_t* tptr, const int32_t
     double* u = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     for (int32_t i = 0; i < n; ++i) v[i] = 1.0 / sqrt((double)n);
     double lam = 0.0;
+    double vcu, vco;
+    orc_vt_coeffs(P, &vcu, &vco);
     for (int32_t it = 0; it < iters; ++it) {
         orc_dose(P, v, u);
         for (int32_t j = 0; j < m; ++j) {
             double cj = 0.0;
             for (int32_t s = 0; s < P->n_structures; ++s)
                 if ((P->mask[j] >> s) & 1u) cj += c[2 * s] + c[2 * s + 1];
+            if (P->vt) cj += vco + (P->vt_target[j] ? vcu : 0.0);
             u[j] *= cj;
         }
         orc_gradient(n, tptr, trow, tval, u, w);

@@ -24,7 +24,7 @@ MODE_GRAPH, MODE_HOST = 0, 1
 # Every symbol include/imrt.h declares.
 EXPORTS = ("imrt_default_options", "plan_create", "plan_set_options", "plan_solve", "plan_dose", "plan_eval",
            "plan_get_x", "plan_get_trace", "plan_info", "plan_cancel", "plan_destroy", "imrt_last_error",
-           "imrt_version", "imrt_eval_csr_noalloc")
+           "imrt_version", "imrt_eval_csr_noalloc", "plan_solve_batch", "plan_set_voxel_targets")
 
 
 class imrt_csr(ctypes.Structure):
@@ -38,7 +38,7 @@ class imrt_options(ctypes.Structure):
                 ("delta", ctypes.c_double), ("max_iter", ctypes.c_int32), ("max_backtracks", ctypes.c_int32),
                 ("x_init", ctypes.c_int32), ("precision", ctypes.c_int32), ("k_trials", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("profile", ctypes.c_int32), ("trace", ctypes.c_int32),
-                ("polish_iter", ctypes.c_int32), ("reserved", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
+                ("polish_iter", ctypes.c_int32), ("kernel_variant", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -83,6 +83,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.plan_set_options.argtypes = [vp, P(imrt_options)]
     lib.plan_solve.restype = ctypes.c_int
     lib.plan_solve.argtypes = [vp, vp, P(imrt_result)]
+    lib.plan_set_voxel_targets.restype = ctypes.c_int
+    lib.plan_set_voxel_targets.argtypes = [vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_int32]
+    lib.plan_solve_batch.restype = ctypes.c_int
+    lib.plan_solve_batch.argtypes = [vp, ctypes.c_int32, vp, vp, vp]
     lib.plan_dose.restype = ctypes.c_int
     lib.plan_dose.argtypes = [vp, vp, vp]
     lib.plan_eval.restype = ctypes.c_int

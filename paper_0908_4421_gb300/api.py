@@ -33,6 +33,7 @@ class Options:
     profile: int = 0
     trace: int = 0
     polish_iter: int = 20
+    kernel_variant: int = 0  # forward pass: 0 warp streaming, 1 bulk-copy (TMA) pipeline
     timeout_ms: float = 0.0
     stream: int = 0  # cudaStream_t as an integer; 0 = legacy default stream
 
@@ -113,14 +114,20 @@ class Plan:
 
     @classmethod
     def from_case(cls, case, options: Optional[Options] = None, device: bool = False) -> "Plan":
-        """From a phantom.Case; with device=True the inputs go through torch CUDA tensors."""
+        """From a phantom.Case (with its voxel targets, if any); with device=True the inputs go
+        through torch CUDA tensors."""
         if device:
             import torch
             t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-            return cls(t(case.row_ptr), t(case.col), t(case.val), t(case.mask), case.thresholds, case.weights,
+            plan = cls(t(case.row_ptr), t(case.col), t(case.val), t(case.mask), case.thresholds, case.weights,
                        m=case.m, n=case.n, options=options)
-        return cls(case.row_ptr, case.col, case.val, case.mask, case.thresholds, case.weights, m=case.m,
-                   n=case.n, options=options)
+        else:
+            plan = cls(case.row_ptr, case.col, case.val, case.mask, case.thresholds, case.weights, m=case.m,
+                       n=case.n, options=options)
+        vt = getattr(case, "voxel_targets", None)
+        if vt is not None:
+            plan.set_voxel_targets(vt.dose, vt.target, vt.w_under, vt.w_over, vt.normalise)
+        return plan
 
     # -- lifetime ----------------------------------------------------------
     def close(self):
@@ -146,10 +153,22 @@ class Plan:
         opts = self.options.to_c()
         L.check(self._lib.plan_set_options(self._h, ctypes.byref(opts)))
 
+    def set_voxel_targets(self, dose=None, target=None, w_under: float = 1.0, w_over: float = 1.0,
+                          normalise: bool = False) -> None:
+        """plan_set_voxel_targets: Eq. (1)'s per-voxel terms around `dose` (None removes them)."""
+        if dose is not None and not _is_torch_cuda(dose):
+            dose = np.ascontiguousarray(dose, np.float32)
+        if target is not None and not _is_torch_cuda(target):
+            target = np.ascontiguousarray(target, np.uint8)
+        L.check(self._lib.plan_set_voxel_targets(self._h, _ptr(dose), _ptr(target), float(w_under), float(w_over),
+                                                  1 if normalise else 0))
+
     def solve(self, x0=None, raise_on_error: bool = True) -> Result:
         """plan_solve; x0 (host array or CUDA tensor) is read when x_init = 2."""
         if x0 is not None and not _is_torch_cuda(x0):
             x0 = np.ascontiguousarray(x0, np.float32)
+        if x0 is not None and int(x0.shape[0]) != self.n:
+            raise ValueError(f"x0 has {x0.shape[0]} entries, the plan has {self.n} beamlets")
         res = L.imrt_result()
         st = self._lib.plan_solve(self._h, _ptr(x0), ctypes.byref(res))
         if raise_on_error and st not in (L.IMRT_OK,):
@@ -200,3 +219,25 @@ class Plan:
 
 def version() -> str:
     return L.load().imrt_version().decode()
+
+
+def solve_batch(plans, x0s=None, stream: int = 0, raise_on_error: bool = True):
+    """plan_solve_batch: all plans in one CUDA-graph launch (one branch per plan)."""
+    lib = L.load()
+    n = len(plans)
+    handles = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    keep = []
+    x0p = None
+    if x0s is not None:
+        ptrs = []
+        for x in x0s:
+            if x is not None and not _is_torch_cuda(x):
+                x = np.ascontiguousarray(x, np.float32)
+            keep.append(x)
+            ptrs.append(_ptr(x))
+        x0p = (ctypes.c_void_p * n)(*ptrs)
+    res = (L.imrt_result * n)()
+    st = lib.plan_solve_batch(handles, n, x0p, res, stream)
+    if raise_on_error and st != L.IMRT_OK:
+        L.check(st)
+    return [Result.from_c(r) for r in res]

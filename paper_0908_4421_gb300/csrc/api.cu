@@ -13,8 +13,10 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <queue>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -40,6 +42,7 @@ void set_error(const char* fmt, ...) {
     do {                                                                                                  \
         cudaError_t e_ = (call);                                                                          \
         if (e_ != cudaSuccess) {                                                                          \
+            cudaGetLastError(); /* do not leave the error behind for the next launch check */           \
             set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);        \
             return e_ == cudaErrorMemoryAllocation ? IMRT_ENOMEM : IMRT_ECUDA;                            \
         }                                                                                                 \
@@ -80,11 +83,17 @@ struct SellCopy {
 
 // Forward launch shape for one (copy, k_trials): grid, work units and their warp partition.
 struct FwdShape {
+    int variant = 0;          // 0: warp streaming, 1: bulk-copy pipeline
+    const void* fn = nullptr;   // k_trials instance
+    const void* fn1 = nullptr;  // single-trial instance (evaluations)
     int grid = 0;
+    int block = 0;
     int warps = 0;
     int n_splits = 0;
     int gstride = 0;
+    int stages = 0;
     size_t smem = 0;
+    size_t smem1 = 0;
     FwdUnits units{};
 };
 
@@ -95,6 +104,45 @@ struct SolveGraph {
 };
 
 }  // namespace
+
+// Small mapped pinned blocks (state read-back and cancel flag) are recycled through a
+// process-wide pool: freeing pinned memory synchronises the device, which would stall
+// plans running on other streams.
+struct PinnedBlock {
+    DevState state;
+    int32_t cancel;
+    int32_t pad[15];
+};
+
+namespace {
+std::mutex g_pinned_mu;
+std::vector<PinnedBlock*> g_pinned_free;
+}  // namespace
+
+imrt_status pinned_acquire(PinnedBlock** out) {
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            *out = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return IMRT_OK;
+        }
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaHostAlloc(&p, sizeof(PinnedBlock), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaHostAlloc failed: %s", cudaGetErrorString(e));
+        return IMRT_ENOMEM;
+    }
+    *out = static_cast<PinnedBlock*>(p);
+    return IMRT_OK;
+}
+
+void pinned_release(PinnedBlock* b) {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.push_back(b);
+}
 
 struct imrt_plan {
     int device = 0, sm_count = 0;
@@ -121,6 +169,11 @@ struct imrt_plan {
     int32_t* bwd_next = nullptr;      // schedule counter
     int32_t* bwd_ticket = nullptr;
     int bwd_grid = 0;
+    // per-voxel targets (Eq. (1) as printed), permuted order; NULL when unset
+    float* vt_p = nullptr;
+    uint8_t* vtm_p = nullptr;
+    bool vt_on = false;
+    int32_t s_star = -1;  // first structure with an under-dose term (x_init = 0 rule)
     // vectors and state
     Vecs v{};
     Terms terms{};
@@ -133,6 +186,7 @@ struct imrt_plan {
     float* g_stage = nullptr;
     float* zout_stage = nullptr;
     double* dscratch = nullptr;
+    struct PinnedBlock* pinned = nullptr;  // from the process-wide pool
     DevState* st_host = nullptr;     // pinned
     int32_t* cancel_host = nullptr;  // mapped pinned
     int32_t* cancel_dev = nullptr;
@@ -146,8 +200,8 @@ struct imrt_plan {
     int32_t last_iterations = 0;
     int32_t cur = 0;
     // caches
-    std::map<std::pair<int, int>, FwdShape> shapes;
-    std::map<std::pair<int, int>, SolveGraph> graphs;
+    std::map<std::tuple<int, int, int>, FwdShape> shapes;
+    std::map<std::tuple<int, int, int>, SolveGraph> graphs;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double lambda0_rule = 0.0, x1_scale = 0.0;
     int64_t device_bytes = 0;
@@ -164,10 +218,12 @@ imrt_status dalloc(imrt_plan* p, T** out, size_t count) {
     *out = nullptr;
     if (count == 0) count = 1;
     void* ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+    // stream-ordered: plan creation and destruction never synchronise the whole device,
+    // so plans on other streams keep running (the serving loop relies on this)
+    cudaError_t e = cudaMallocAsync(&ptr, count * sizeof(T), stream_of(p));
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        set_error("cudaMallocAsync of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? IMRT_ENOMEM : IMRT_ECUDA;
     }
     p->allocations.push_back(ptr);
@@ -183,18 +239,22 @@ imrt_status dalloc_bytes(imrt_plan* p, void** out, size_t bytes) {
     return IMRT_OK;
 }
 
-// Temporary device buffer freed at scope exit.
+// Temporary device buffer freed (stream-ordered) at scope exit.
 struct Temp {
     void* ptr = nullptr;
+    cudaStream_t stream = nullptr;
     ~Temp() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) cudaFreeAsync(ptr, stream);
     }
 };
+
+thread_local cudaStream_t g_temp_stream = nullptr;  // the stream of the plan being built
 
 template <class T>
 imrt_status talloc(Temp& t, T** out, size_t count) {
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&t.ptr, count * sizeof(T));
+    t.stream = g_temp_stream;
+    cudaError_t e = cudaMallocAsync(&t.ptr, count * sizeof(T), t.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("temporary cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
@@ -216,6 +276,7 @@ imrt_status validate_options(const imrt_options* o) {
     if (o->mode != IMRT_MODE_GRAPH && o->mode != IMRT_MODE_HOST) return set_error("unknown mode"), IMRT_EINVAL;
     if (o->trace < 0 || o->trace > 2) return set_error("trace must be 0, 1 or 2"), IMRT_EINVAL;
     if (o->polish_iter < 0) return set_error("polish_iter must be >= 0"), IMRT_EINVAL;
+    if (o->kernel_variant < 0 || o->kernel_variant > 1) return set_error("kernel_variant must be 0 or 1"), IMRT_EINVAL;
     if (!(o->timeout_ms >= 0.0)) return set_error("timeout_ms must be >= 0"), IMRT_EINVAL;
     return IMRT_OK;
 }
@@ -223,31 +284,83 @@ imrt_status validate_options(const imrt_options* o) {
 // Work units of one copy for a given forward grid: slices whose cost exceeds half a warp's
 // share are cut into near-equal pieces (ranges of groups); units are then dealt to warps in
 // contiguous runs of near-equal cost (stored entries plus an epilogue allowance per slice).
-imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, FwdShape* out) {
-    const void* fn = fwd_kernel(c.precision, k_trials);
-    if (!fn) return set_error("no forward kernel for precision %d, k_trials %d", c.precision, k_trials), IMRT_EINVAL;
-    const size_t smem = fwd_smem_bytes(p->n_pad, k_trials, c.precision);
+imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int variant, FwdShape* out) {
     int max_smem = 0;
     CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    if (smem + 4096 > (size_t)max_smem)
-        return set_error("n = %d beamlets with k_trials = %d needs %zu bytes of shared memory (limit %d)", p->n,
-                         k_trials, smem, max_smem),
-               IMRT_EUNSUPPORTED;
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFwdThreads, smem));
-    if (per_sm < 1) return set_error("forward kernel does not fit on an SM"), IMRT_EUNSUPPORTED;
-    per_sm = std::min(per_sm, 4);
-    out->grid = p->sm_count * per_sm;
-    out->warps = out->grid * (kFwdThreads / 32);
-    out->smem = smem;
+    out->variant = variant;
+    if (variant == 1) {
+        out->fn = fwd_tma_kernel(c.precision, k_trials);
+        out->fn1 = fwd_tma_kernel(c.precision, 1);
+        if (!out->fn) return set_error("no forward kernel for k_trials %d", k_trials), IMRT_EINVAL;
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, out->fn));
+        const size_t sb = (size_t)fwd_tma_stage_bytes(c.precision);
+        const size_t xs = ((size_t)p->n_pad * k_trials * 4 + 127) & ~(size_t)127;
+        const size_t xs1 = ((size_t)p->n_pad * 4 + 127) & ~(size_t)127;
+        const size_t avail = (size_t)max_smem - fa.sharedSizeBytes - 1024;
+        const int ns_max = (int)std::min<size_t>(kTmaMaxStages, avail > xs ? (avail - xs) / sb : 0);
+        // consumer warps and ring stages per consumer: prefer two stages each
+#ifndef IMRT_TMA_RING
+#define IMRT_TMA_RING 2
+#endif
+        const int nc = std::max(1, std::min(kTmaMaxConsumers, ns_max / IMRT_TMA_RING));
+        const int r = nc > 0 ? ns_max / nc : 0;
+        if (r < 1 || (size_t)(nc * r) * sb < 2 * xs1)
+            return set_error("n = %d beamlets with k_trials = %d leaves too little shared memory for the "
+                             "bulk-copy ring", p->n, k_trials),
+                   IMRT_EUNSUPPORTED;
+        out->stages = r;
+        out->smem = xs + (size_t)nc * r * sb;
+        out->smem1 = xs1 + (size_t)nc * r * sb;
+        out->block = 32 * (1 + nc);
+        out->grid = p->sm_count;
+        out->warps = out->grid * nc;
+        // the attribute is per kernel function, shared by every plan: always the device maximum
+        CK(cudaFuncSetAttribute(out->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem - (int)fa.sharedSizeBytes));
+        cudaFuncAttributes fa1;
+        CK(cudaFuncGetAttributes(&fa1, out->fn1));
+        CK(cudaFuncSetAttribute(out->fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem - (int)fa1.sharedSizeBytes));
+    } else {
+        out->fn = fwd_kernel(c.precision, k_trials);
+        out->fn1 = fwd_kernel(c.precision, 1);
+        if (!out->fn) return set_error("no forward kernel for k_trials %d", k_trials), IMRT_EINVAL;
+        const size_t smem = fwd_smem_bytes(p->n_pad, k_trials, c.precision);
+        if (smem + 4096 > (size_t)max_smem)
+            return set_error("n = %d beamlets with k_trials = %d needs %zu bytes of shared memory (limit %d)", p->n,
+                             k_trials, smem, max_smem),
+                   IMRT_EUNSUPPORTED;
+        // the attribute is per kernel function, shared by every plan: always the device maximum
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, out->fn));
+        CK(cudaFuncSetAttribute(out->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem - (int)fa.sharedSizeBytes));
+        cudaFuncAttributes fa1;
+        CK(cudaFuncGetAttributes(&fa1, out->fn1));
+        CK(cudaFuncSetAttribute(out->fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem - (int)fa1.sharedSizeBytes));
+        const size_t smem1 = fwd_smem_bytes(p->n_pad, 1, c.precision);
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, out->fn, kFwdThreads, smem));
+        if (per_sm < 1) return set_error("forward kernel does not fit on an SM"), IMRT_EUNSUPPORTED;
+        per_sm = std::min(per_sm, 4);
+        out->grid = p->sm_count * per_sm;
+        out->block = kFwdThreads;
+        out->warps = out->grid * (kFwdThreads / 32);
+        out->smem = smem;
+        out->smem1 = smem1;
+        out->stages = 0;
+    }
     const int W = out->warps;
     const int64_t group_entries = (int64_t)kSlice * c.ge;
     const int64_t epi = 8 * kSlice;
     int64_t total = 0;
     for (int s = 0; s < p->n_slices; ++s) total += c.host_cost[s];
     const double budget = (double)total / W;
-    const int64_t piece_groups = std::max<int64_t>(4, (int64_t)(budget / group_entries));
+    // the bulk-copy kernel streams whole slices (its producer cuts them into stage-sized pieces)
+    const int64_t piece_groups =
+        variant == 1 ? INT64_MAX / 4 : std::max<int64_t>(4, (int64_t)(budget / group_entries));
     std::vector<int32_t> us, ug0, ug1, usplit, upiece, spieces, sbase;
     std::vector<int64_t> ucost;
     int32_t parts = 0;
@@ -289,7 +402,8 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, FwdShape* 
     auto upload = [&](const std::vector<int32_t>& h, const int32_t** dst) -> imrt_status {
         int32_t* d = nullptr;
         TRY(dalloc(p, &d, std::max<size_t>(h.size(), 1)));
-        if (!h.empty()) CK(cudaMemcpy(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice));
+        if (!h.empty())
+            CK(cudaMemcpyAsync(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, stream_of(p)));
         *dst = d;
         return IMRT_OK;
     };
@@ -302,24 +416,26 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, FwdShape* 
     TRY(upload(sbase, &U.split_base));
     TRY(dalloc(p, &U.partials, (size_t)std::max(parts, 1) * kSlice * k_trials));
     TRY(dalloc(p, &U.counters, std::max(out->n_splits, 1)));
-    CK(cudaMemset(U.counters, 0, sizeof(int32_t) * std::max(out->n_splits, 1)));
+    CK(cudaMemsetAsync(U.counters, 0, sizeof(int32_t) * std::max(out->n_splits, 1), stream_of(p)));
     TRY(dalloc(p, &U.gpart, (size_t)k_trials * out->gstride));
     TRY(dalloc(p, &U.ticket, 1));
     TRY(dalloc(p, &U.next_unit, 1));
-    CK(cudaMemset(U.ticket, 0, sizeof(int32_t)));
-    CK(cudaMemset(U.next_unit, 0, sizeof(int32_t)));
+    CK(cudaMemsetAsync(U.ticket, 0, sizeof(int32_t), stream_of(p)));
+    CK(cudaMemsetAsync(U.next_unit, 0, sizeof(int32_t), stream_of(p)));
+    CK(cudaStreamSynchronize(stream_of(p)));  // the host vectors above go out of scope
     return IMRT_OK;
 }
 
 imrt_status get_shape(imrt_plan* p, int precision, int k_trials, FwdShape** out) {
-    auto key = std::make_pair(precision, k_trials);
+    const int variant = p->opt.kernel_variant;
+    auto key = std::make_tuple(precision, k_trials, variant);
     auto it = p->shapes.find(key);
     if (it == p->shapes.end()) {
         const SellCopy& c = precision == IMRT_FP32 ? p->sell32 : p->sellq;
         if (c.precision != precision)
             return set_error("plan holds no copy of D at precision %d", precision), IMRT_EINVAL;
         FwdShape sh;
-        TRY(make_shape(p, c, k_trials, &sh));
+        TRY(make_shape(p, c, k_trials, variant, &sh));
         it = p->shapes.emplace(key, sh).first;
     }
     *out = &it->second;
@@ -333,8 +449,11 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.val = c.val;
     a.col = c.col;
     a.u = sh.units;
+    a.stages = sh.stages;
     a.mask = p->mask;
     a.scale = c.precision == IMRT_FP32 ? nullptr : p->scale;
+    a.vt = p->vt_on ? p->vt_p : nullptr;
+    a.vtm = p->vt_on ? p->vtm_p : nullptr;
     a.terms = p->terms_dev;
     a.st = p->st;
     a.sp = p->sp;
@@ -383,8 +502,7 @@ imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, f
     a.z_dst = z_dst;
     a.r_dst = r_dst;
     void* args[] = {&a};
-    CK(cudaLaunchKernel(fwd_kernel(precision, 1), dim3(sh->grid), dim3(kFwdThreads), args, sh->smem,
-                        stream_of(p)));
+    CK(cudaLaunchKernel(sh->fn1, dim3(sh->grid), dim3(sh->block), args, sh->smem1, stream_of(p)));
     if (G_out) CK(launch_g_objective(sh->units.gpart, sh->gstride, G_out, stream_of(p)));
     return IMRT_OK;
 }
@@ -410,9 +528,11 @@ imrt_status make_bwd_schedule(imrt_plan* p, const std::vector<int64_t>& len) {
     TRY(dalloc(p, &p->bwd_order, p->n));
     TRY(dalloc(p, &p->bwd_next, 1));
     TRY(dalloc(p, &p->bwd_ticket, 1));
-    CK(cudaMemcpy(p->bwd_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemset(p->bwd_next, 0, sizeof(int32_t)));
-    CK(cudaMemset(p->bwd_ticket, 0, sizeof(int32_t)));
+    CK(cudaMemcpyAsync(p->bwd_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+                       stream_of(p)));
+    CK(cudaMemsetAsync(p->bwd_next, 0, sizeof(int32_t), stream_of(p)));
+    CK(cudaMemsetAsync(p->bwd_ticket, 0, sizeof(int32_t), stream_of(p)));
+    CK(cudaStreamSynchronize(stream_of(p)));
     p->bwd_grid = grid;
     return IMRT_OK;
 }
@@ -468,6 +588,7 @@ imrt_status ensure_lambda0_rule(imrt_plan* p) {
 imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structures, const float* thresholds,
                        const float* weights) {
     cudaStream_t s = stream_of(p);
+    g_temp_stream = s;
     const int32_t m = D->m, n = D->n;
     const int64_t nnz = D->nnz;
     // --- D on the device ---------------------------------------------------
@@ -618,6 +739,7 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     int s_star = -1;
     for (int st = 0; st < p->S && s_star < 0; ++st)
         if ((T.has_u >> st) & 1u) s_star = st;
+    p->s_star = s_star;
     p->x1_scale = 0.0;
     if (s_star >= 0) {
         CK(launch_fill(p->x_stage, 1.0f, n, s));
@@ -659,8 +781,9 @@ imrt_status alloc_vectors(imrt_plan* p) {
     CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
     CK(cudaMemsetAsync(p->g_stage, 0, sizeof(float) * p->n_pad, s));
     CK(cudaMemsetAsync(p->st, 0, sizeof(DevState), s));
-    CK(cudaHostAlloc((void**)&p->st_host, sizeof(DevState), cudaHostAllocDefault));
-    CK(cudaHostAlloc((void**)&p->cancel_host, sizeof(int32_t), cudaHostAllocMapped));
+    TRY(pinned_acquire(&p->pinned));
+    p->st_host = &p->pinned->state;
+    p->cancel_host = &p->pinned->cancel;
     *p->cancel_host = 0;
     CK(cudaHostGetDevicePointer((void**)&p->cancel_dev, p->cancel_host, 0));
     for (auto& e : p->ev) CK(cudaEventCreate(&e));
@@ -761,18 +884,15 @@ imrt_status phase_kernels(imrt_plan* p, int precision, int k_trials, PhaseKernel
     const SellCopy& c = copy_of(p, precision);
     InitArgs ia{p->st, p->sp, p->v};
     K->init = make_launch(init_kernel(), 1, kCtlThreads, 0, ia);
-    // The initial evaluation uses the trial launch's grid so that partial counts match.
+    // The initial evaluation uses the trial launch's grid and work units.
     FwdArgs ea = fwd_args(p, c, *sh, kFwdEval);
     ea.control = 1;
-    const void* eval_fn = fwd_kernel(precision, 1);
-    const size_t eval_smem = fwd_smem_bytes(p->n_pad, 1, precision);
-    CK(cudaFuncSetAttribute(eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eval_smem));
-    K->eval = make_launch(eval_fn, sh->grid, kFwdThreads, eval_smem, ea);
+    K->eval = make_launch(sh->fn1, sh->grid, sh->block, sh->smem1, ea);
     BwdCurArgs ba{bwd_args(p, precision, 1), p->v.r};
     K->bwd = make_launch(bwd_kernel(precision), p->bwd_grid, kBwdThreads, 0, ba);
     FwdArgs ta = fwd_args(p, c, *sh, kFwdTrial);
     ta.control = 1;
-    K->trial = make_launch(fwd_kernel(precision, k_trials), sh->grid, kFwdThreads, sh->smem, ta);
+    K->trial = make_launch(sh->fn, sh->grid, sh->block, sh->smem, ta);
     K->finish = make_launch(finish_kernel(), 1, kCtlThreads, 0, ia);
     *shape_out = sh;
     return IMRT_OK;
@@ -819,8 +939,31 @@ imrt_status add_node(Launch& l, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNo
 
 // init -> eval -> while(cond) { bwd -> trial } -> bwd -> finish (the controller runs in the
 // last CTA of eval and trial)
+// Adds one plan's solve as a branch of `graph`:
+//   init -> eval -> while (cond) { bwd -> trial } -> bwd -> finish
+// (the controller runs in the last CTA of eval and trial and clears `cond`).
+imrt_status add_solve_branch(cudaGraph_t graph, PhaseKernels& K, cudaGraphConditionalHandle* cond) {
+    CK(cudaGraphConditionalHandleCreate(cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t n_init, n_eval, n_loop, n_bwd_final, n_finish;
+    TRY(add_node(K.init, graph, nullptr, &n_init));
+    TRY(add_node(K.eval, graph, &n_init, &n_eval));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = *cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(cudaGraphAddNode(&n_loop, graph, &n_eval, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t b_bwd, b_trial;
+    TRY(add_node(K.bwd, body, nullptr, &b_bwd));
+    TRY(add_node(K.trial, body, &b_bwd, &b_trial));
+    TRY(add_node(K.bwd, graph, &n_loop, &n_bwd_final));
+    TRY(add_node(K.finish, graph, &n_bwd_final, &n_finish));
+    return IMRT_OK;
+}
+
 imrt_status get_graph(imrt_plan* p, int precision, int k_trials, PhaseKernels& K, SolveGraph** out) {
-    auto key = std::make_pair(precision, k_trials);
+    auto key = std::make_tuple(precision, k_trials, (int)p->opt.kernel_variant);
     auto it = p->graphs.find(key);
     if (it != p->graphs.end()) {
         *out = &it->second;
@@ -828,22 +971,7 @@ imrt_status get_graph(imrt_plan* p, int precision, int k_trials, PhaseKernels& K
     }
     SolveGraph sg;
     CK(cudaGraphCreate(&sg.graph, 0));
-    CK(cudaGraphConditionalHandleCreate(&sg.cond, sg.graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNode_t n_init, n_eval, n_loop, n_bwd_final, n_finish;
-    TRY(add_node(K.init, sg.graph, nullptr, &n_init));
-    TRY(add_node(K.eval, sg.graph, &n_init, &n_eval));
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = sg.cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    CK(cudaGraphAddNode(&n_loop, sg.graph, &n_eval, nullptr, 1, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t b_bwd, b_trial;
-    TRY(add_node(K.bwd, body, nullptr, &b_bwd));
-    TRY(add_node(K.trial, body, &b_bwd, &b_trial));
-    TRY(add_node(K.bwd, sg.graph, &n_loop, &n_bwd_final));
-    TRY(add_node(K.finish, sg.graph, &n_bwd_final, &n_finish));
+    TRY(add_solve_branch(sg.graph, K, &sg.cond));
     CK(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
     it = p->graphs.emplace(key, sg).first;
     *out = &it->second;
@@ -916,6 +1044,97 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
 
 }  // namespace
 
+namespace {
+
+// Batched solves: one instantiated graph per (plan list, phase settings), with one
+// independent solve branch per plan. Entries that mention a plan die with it.
+struct BatchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphConditionalHandle> conds;
+    std::vector<imrt_plan*> plans;
+};
+std::mutex g_batch_mu;
+std::map<std::vector<uintptr_t>, BatchGraph> g_batches;
+
+void destroy_batch(BatchGraph& b) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.graph) cudaGraphDestroy(b.graph);
+    b.exec = nullptr;
+    b.graph = nullptr;
+}
+
+void forget_plan_batches(imrt_plan* p) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        if (std::find(it->second.plans.begin(), it->second.plans.end(), p) != it->second.plans.end()) {
+            destroy_batch(it->second);
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// One phase of a batched solve: phase 0 = each plan at its own precision, phase 1 = the
+// FP32 polish of reduced-precision plans (x_init = 2 from their current x).
+imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vector<int>& precision,
+                            const std::vector<int>& max_iter, const std::vector<int>& x_init,
+                            const std::vector<const float*>& x0, cudaStream_t s, std::vector<imrt_result>& res) {
+    const size_t n = plans.size();
+    std::vector<PhaseKernels> K(n);
+    std::vector<FwdShape*> sh(n, nullptr);
+    std::vector<uintptr_t> key;
+    for (size_t i = 0; i < n; ++i) {
+        imrt_plan* p = plans[i];
+        TRY(phase_kernels(p, precision[i], p->opt.k_trials, &K[i], &sh[i]));
+        key.push_back((uintptr_t)p);
+        key.push_back(((uintptr_t)precision[i] << 16) | ((uintptr_t)p->opt.k_trials << 8) |
+                      (uintptr_t)p->opt.kernel_variant);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batches.find(key);
+    if (it == g_batches.end()) {
+        BatchGraph bg;
+        bg.plans = plans;
+        CK(cudaGraphCreate(&bg.graph, 0));
+        bg.conds.resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            const imrt_status st = add_solve_branch(bg.graph, K[i], &bg.conds[i]);
+            if (st != IMRT_OK) {
+                destroy_batch(bg);
+                return st;
+            }
+        }
+        const cudaError_t e = cudaGraphInstantiate(&bg.exec, bg.graph, 0);
+        if (e != cudaSuccess) {
+            destroy_batch(bg);
+            return set_error("batch graph instantiation failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;
+        }
+        it = g_batches.emplace(key, bg).first;
+    }
+    BatchGraph& bg = it->second;
+    std::vector<SolveParams> q(n);
+    for (size_t i = 0; i < n; ++i) {
+        q[i] = make_params(plans[i], *sh[i], max_iter[i], x_init[i], x0[i], (unsigned long long)bg.conds[i]);
+        CK(cudaMemcpyAsync(plans[i]->sp, &q[i], sizeof(SolveParams), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaGraphLaunch(bg.exec, s));
+    for (size_t i = 0; i < n; ++i)
+        CK(cudaMemcpyAsync(plans[i]->st_host, plans[i]->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < n; ++i) {
+        const DevState& d = *plans[i]->st_host;
+        res[i].launches += 2 + 2 * (d.passes - 1) + 2;
+        res[i].passes += d.passes;
+        res[i].grad_passes += d.grad_passes;
+        plans[i]->cur = d.cur;
+    }
+    return IMRT_OK;
+}
+
+}  // namespace
+
 void imrt::set_last_error_message(const char* msg) { g_error = msg ? msg : ""; }
 
 // =============================================================================
@@ -950,15 +1169,15 @@ const char* imrt_version(void) { return "imrt-gb300 1.0 sm_103a"; }
 
 void plan_destroy(imrt_plan* p) {
     if (!p) return;
+    forget_plan_batches(p);
     for (auto& kv : p->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
-    for (void* a : p->allocations) cudaFree(a);
-    if (p->st_host) cudaFreeHost(p->st_host);
-    if (p->cancel_host) cudaFreeHost(p->cancel_host);
+    for (void* a : p->allocations) cudaFreeAsync(a, stream_of(p));
+    if (p->pinned) pinned_release(p->pinned);
     delete p;
 }
 
@@ -1030,6 +1249,84 @@ imrt_status plan_set_options(imrt_plan* p, const imrt_options* opt) {
     return IMRT_OK;
 }
 
+imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_t* target, float w_under,
+                                   float w_over, int32_t normalise) {
+    g_error.clear();
+    if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    cudaStream_t s = stream_of(p);
+    g_temp_stream = s;
+    // graphs captured the old arguments: rebuild them on the next solve
+    for (auto& kv : p->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    p->graphs.clear();
+    forget_plan_batches(p);
+    p->lambda0_rule = 0.0;  // the step-size rule depends on the terms
+    Terms& T = p->terms;
+    if (!dose) {
+        p->vt_on = false;
+        T.has_vt = 0;
+        T.vcu = T.vco = 0.0f;
+        T.vcud = T.vcod = 0.0;
+        CK(cudaMemcpyAsync(p->terms_dev, &T, sizeof(Terms), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        return IMRT_OK;
+    }
+    if (!(w_under >= 0.0f) || !(w_over >= 0.0f) || !std::isfinite(w_under) || !std::isfinite(w_over))
+        return set_error("voxel-target weights must be finite and >= 0"), IMRT_EINVAL;
+    // host copies for validation and the sums of the x_init = 0 rule
+    std::vector<float> hd(p->m);
+    std::vector<uint8_t> ht(p->m, 0);
+    CK(cudaMemcpyAsync(hd.data(), dose, sizeof(float) * p->m, cudaMemcpyDefault, s));
+    if (target) CK(cudaMemcpyAsync(ht.data(), target, p->m, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    int64_t nt = 0;
+    double sum_t = 0.0;
+    for (int32_t j = 0; j < p->m; ++j) {
+        if (!std::isfinite(hd[j])) return set_error("voxel target dose must be finite"), IMRT_EINVAL;
+        if (ht[j]) {
+            ht[j] = 1;
+            ++nt;
+            sum_t += (double)hd[j];
+        }
+    }
+    if (!p->vt_p) {
+        TRY(dalloc(p, &p->vt_p, p->m_pad));
+        TRY(dalloc(p, &p->vtm_p, p->m_pad));
+    }
+    Temp td, tt;
+    float* dd;
+    uint8_t* dt;
+    TRY(talloc(td, &dd, p->m));
+    TRY(talloc(tt, &dt, p->m));
+    CK(cudaMemcpyAsync(dd, hd.data(), sizeof(float) * p->m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dt, ht.data(), p->m, cudaMemcpyHostToDevice, s));
+    CK(launch_permute_in(dd, dt, p->perm, p->m, p->m_pad, p->vt_p, p->vtm_p, s));
+    const double cu = nt > 0 ? (double)w_under / (normalise ? (double)nt : 1.0) : 0.0;
+    const double co = (double)w_over / (normalise ? (double)p->m : 1.0);
+    T.has_vt = 1;
+    T.vcu = (float)cu;
+    T.vco = (float)co;
+    T.vcud = cu;
+    T.vcod = co;
+    p->vt_on = true;
+    CK(cudaMemcpyAsync(p->terms_dev, &T, sizeof(Terms), cudaMemcpyHostToDevice, s));
+    // x_init = 0 without an under-dose structure: s = sum_VT T_j / sum_VT (D 1)_j
+    if (p->s_star < 0 && nt > 0) {
+        CK(launch_fill(p->x_stage, 1.0f, p->n, s));
+        TRY(run_eval(p, kFwdEval, p->x_stage, p->z_stage, p->r_stage, nullptr));
+        CK(launch_sum_masked(p->z_stage, p->vtm_p, 0, p->m, p->dscratch, s));
+        double sz = 0.0;
+        CK(cudaMemcpyAsync(&sz, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
+        CK(cudaStreamSynchronize(s));
+        p->x1_scale = sz > 0.0 ? sum_t / sz : 0.0;
+    }
+    CK(cudaStreamSynchronize(s));
+    return IMRT_OK;
+}
+
 imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     g_error.clear();
     if (!p || !res) return set_error("NULL argument"), IMRT_EINVAL;
@@ -1084,6 +1381,104 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
         set_error("solve stopped: %s", what);
     }
     return (imrt_status)d.status;
+}
+
+imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float* const* x0s, imrt_result* results,
+                             void* stream) {
+    g_error.clear();
+    if (!plans || !results || count < 1) return set_error("need count >= 1 plans and results"), IMRT_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<imrt_plan*> ps(plans, plans + count);
+    for (int i = 0; i < count; ++i) {
+        if (!ps[i]) return set_error("plan %d is NULL", i), IMRT_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ps[j] == ps[i]) return set_error("plan %d appears twice in the batch", i), IMRT_EINVAL;
+    }
+    std::vector<imrt_result> res(count);
+    memset(res.data(), 0, sizeof(imrt_result) * count);
+    std::vector<int> prec(count), iters(count), xinit(count);
+    std::vector<const float*> x0(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        imrt_plan* p = ps[i];
+        const imrt_options& o = p->opt;
+        if (o.x_init == 2 && (!x0s || !x0s[i])) return set_error("plan %d: x_init = 2 needs x0", i), IMRT_EINVAL;
+        *p->cancel_host = 0;
+        TRY(ensure_trace(p));
+        if (o.lambda0 <= 0.0) TRY(ensure_lambda0_rule(p));
+        if (o.x_init == 2) {
+            CK(cudaMemcpyAsync(p->x_stage, x0s[i], sizeof(float) * p->n, cudaMemcpyDefault, s));
+            x0[i] = p->x_stage;
+        }
+        const bool polish = o.precision != IMRT_FP32 && o.polish_iter > 0;
+        prec[i] = o.precision;
+        iters[i] = polish ? std::max(0, o.max_iter - std::min(o.polish_iter, o.max_iter)) : o.max_iter;
+        xinit[i] = o.x_init;
+    }
+    TRY(run_batch_phase(ps, prec, iters, xinit, x0, s, res));
+    // FP32 polish of the reduced-precision plans that ended without an error
+    std::vector<imrt_plan*> pp;
+    std::vector<int> pidx, pprec, piters, pxinit;
+    std::vector<const float*> px0;
+    for (int i = 0; i < count; ++i) {
+        imrt_plan* p = ps[i];
+        const DevState d = *p->st_host;
+        res[i].iterations = d.iter;
+        res[i].backtracks = d.total_bt;
+        res[i].initial_objective = d.G0;
+        res[i].status = d.status;
+        res[i].stop_reason = d.stop;
+        res[i].objective = d.G;
+        res[i].kkt = d.kkt;
+        res[i].rel_change = d.rel;
+        if (p->opt.precision != IMRT_FP32 && p->opt.polish_iter > 0 && d.status == IMRT_OK) {
+            CK(cudaMemcpyAsync(p->g_stage, p->v.x + (size_t)d.cur * p->n_pad, sizeof(float) * p->n_pad,
+                               cudaMemcpyDeviceToDevice, s));
+            pp.push_back(p);
+            pidx.push_back(i);
+            pprec.push_back(IMRT_FP32);
+            piters.push_back(std::min(p->opt.polish_iter, p->opt.max_iter));
+            pxinit.push_back(2);
+            px0.push_back(p->g_stage);
+        }
+    }
+    if (!pp.empty()) {
+        std::vector<int> saved(pp.size());
+        for (size_t k = 0; k < pp.size(); ++k) {
+            saved[k] = pp[k]->opt.trace;
+            pp[k]->opt.trace = 0;
+        }
+        std::vector<imrt_result> pres(pp.size());
+        memset(pres.data(), 0, sizeof(imrt_result) * pp.size());
+        const imrt_status st = run_batch_phase(pp, pprec, piters, pxinit, px0, s, pres);
+        for (size_t k = 0; k < pp.size(); ++k) pp[k]->opt.trace = saved[k];
+        TRY(st);
+        for (size_t k = 0; k < pp.size(); ++k) {
+            const DevState d = *pp[k]->st_host;
+            imrt_result& r = res[pidx[k]];
+            r.polish_iterations = d.iter;
+            r.status = d.status;
+            r.stop_reason = d.stop;
+            r.objective = d.G;
+            r.kkt = d.kkt;
+            r.rel_change = d.rel;
+            r.launches += pres[k].launches;
+            r.passes += pres[k].passes;
+            r.grad_passes += pres[k].grad_passes;
+        }
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    imrt_status first = IMRT_OK;
+    for (int i = 0; i < count; ++i) {
+        imrt_plan* p = ps[i];
+        res[i].lambda0 = p->opt.lambda0 > 0.0 ? p->opt.lambda0 : p->lambda0_rule;
+        res[i].ms = ms;
+        p->last_iterations = res[i].iterations;
+        results[i] = res[i];
+        if (first == IMRT_OK && res[i].status != IMRT_OK) first = (imrt_status)res[i].status;
+    }
+    if (first != IMRT_OK) set_error("at least one solve of the batch stopped with status %d", (int)first);
+    return first;
 }
 
 imrt_status plan_dose(imrt_plan* p, const float* x, float* z_out) {
@@ -1171,8 +1566,8 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     FwdShape* sh = nullptr;
     if (get_shape(p, p->opt.precision, p->opt.k_trials, &sh) == IMRT_OK) {
         info->fwd_grid = sh->grid;
+        info->fwd_block = sh->block;
     }
-    info->fwd_block = kFwdThreads;
     info->bwd_grid = p->bwd_grid;
     info->bwd_block = kBwdThreads;
     info->precision = p->opt.precision;

@@ -324,6 +324,17 @@ __global__ void k_unpermute(const float* __restrict__ zp, const int32_t* __restr
     if (j >= 0) z[j] = zp[p];
 }
 
+// Caller order -> permuted order for per-voxel arrays (padding positions get 0).
+__global__ void k_permute_in(const float* __restrict__ src, const uint8_t* __restrict__ src_mask,
+                             const int32_t* __restrict__ perm, int32_t m, int32_t m_pad, float* __restrict__ dst,
+                             uint8_t* __restrict__ dst_mask) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m_pad) return;
+    const int j = p < m ? perm[p] : -1;
+    dst[p] = j >= 0 ? src[j] : 0.0f;
+    dst_mask[p] = j >= 0 ? (src_mask ? src_mask[j] : (uint8_t)0) : (uint8_t)0;
+}
+
 __global__ void k_pad_copy(const float* __restrict__ src, int32_t n, int32_t n_pad, float* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_pad) dst[i] = i < n ? src[i] : 0.0f;
@@ -396,6 +407,20 @@ __global__ void __launch_bounds__(1024) k_sum_doubles(const double* __restrict__
     if (threadIdx.x == 0) *out = s;
 }
 
+// The dynamic shared-memory limit is per kernel function and shared by every plan (and
+// by plans built concurrently): always raise it to the device maximum, never lower it.
+template <class K>
+cudaError_t set_max_dynamic_smem(K kernel) {
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 }  // namespace
 
 cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
@@ -457,7 +482,7 @@ cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, co
     const int n_chunks = (m_pad + chunk_rows - 1) / chunk_rows;
     const size_t smem = (size_t)n * sizeof(int32_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_t_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = set_max_dynamic_smem(k_t_count);
         if (e != cudaSuccess) return e;
     }
     k_t_count<<<n_chunks, 256, smem, stream>>>(row_ptr, col, perm, m_pad, n, chunk_rows, counts);
@@ -473,7 +498,7 @@ cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, co
     const int n_chunks = (m_pad + chunk_rows - 1) / chunk_rows;
     const size_t smem = (size_t)n * sizeof(int32_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_t_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = set_max_dynamic_smem(k_t_scatter);
         if (e != cudaSuccess) return e;
     }
     k_t_scatter<<<n_chunks, 256, smem, stream>>>(row_ptr, col, val, perm, m_pad, n, chunk_rows, counts, t_off, t_val,
@@ -515,6 +540,12 @@ cudaError_t launch_mask_counts(const uint8_t* mask, int32_t m, int32_t* counts, 
 
 cudaError_t launch_unpermute(const float* zp, const int32_t* perm, int32_t m, float* z, cudaStream_t stream) {
     k_unpermute<<<blocks_for(m, 256), 256, 0, stream>>>(zp, perm, m, z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_in(const float* src, const uint8_t* src_mask, const int32_t* perm, int32_t m,
+                              int32_t m_pad, float* dst, uint8_t* dst_mask, cudaStream_t stream) {
+    k_permute_in<<<blocks_for(m_pad, 256), 256, 0, stream>>>(src, src_mask, perm, m, m_pad, dst, dst_mask);
     return cudaGetLastError();
 }
 

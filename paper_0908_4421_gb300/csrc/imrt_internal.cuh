@@ -27,6 +27,10 @@ constexpr int kSets = kMaxTrials + 1;  // x/z/r buffer sets: accepted + trials
 constexpr int kFwdThreads = 512;
 constexpr int kBwdThreads = 512;
 constexpr int kCtlThreads = 256;
+constexpr int kTmaMaxConsumers = 8;   // bulk-copy forward kernel: 1 producer + up to 8 consumer warps
+constexpr int kTmaThreads = 32 * (1 + kTmaMaxConsumers);
+constexpr int kTmaStageGroups = 16;    // groups per ring stage
+constexpr int kTmaMaxStages = 24;
 
 // Forward-kernel modes.
 enum FwdMode : int32_t {
@@ -42,6 +46,10 @@ struct Terms {
     float Tu[kMaxStruct], To[kMaxStruct];
     float cu[kMaxStruct], co[kMaxStruct];    // FP32 copies for r
     double cud[kMaxStruct], cod[kMaxStruct]; // FP64 copies for G
+    // Eq. (1) with a per-voxel dose T_j: under-dose on V_T, over-dose on every voxel
+    int32_t has_vt, pad;
+    float vcu, vco;
+    double vcud, vcod;
 };
 
 // Solver state, device-resident, updated only by the single-CTA controller.
@@ -124,6 +132,8 @@ struct FwdArgs {
     FwdUnits u;
     const uint8_t* mask;         // m_pad, permuted order
     const float* scale;          // n_pad per-beamlet value scale, or NULL (FP32)
+    const float* vt;             // m_pad per-voxel target dose T_j (permuted), or NULL
+    const uint8_t* vtm;          // m_pad: 1 => voxel in V_T
     const Terms* terms;
     DevState* st;
     const SolveParams* sp;
@@ -131,6 +141,7 @@ struct FwdArgs {
     int32_t m, n, n_pad, m_pad;
     int32_t mode;        // FwdMode
     int32_t control;     // 1: the last CTA runs the Armijo controller (inside a solve)
+    int32_t stages;      // bulk-copy kernel: ring stages per consumer warp
     const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x
     float* z_dst;        // kFwdEval / kFwdPower; NULL => accepted set
     float* r_dst;
@@ -160,6 +171,8 @@ void set_last_error_message(const char* msg);
 
 // Kernel launchers / function pointers (kernels.cu).
 const void* fwd_kernel(int precision, int k_trials);
+const void* fwd_tma_kernel(int precision, int k_trials);
+int fwd_tma_stage_bytes(int precision);
 const void* bwd_kernel(int precision);
 const void* bwd_fixed_kernel(int precision);
 const void* init_kernel();
@@ -196,6 +209,8 @@ cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* d
 cudaError_t launch_fill(float* dst, float v, int32_t count, cudaStream_t stream);
 cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, int32_t m, double* out,
                               cudaStream_t stream);
+cudaError_t launch_permute_in(const float* src, const uint8_t* src_mask, const int32_t* perm, int32_t m,
+                              int32_t m_pad, float* dst, uint8_t* dst_mask, cudaStream_t stream);
 cudaError_t launch_power_update(float* v, const float* w, int32_t n, double* lam, cudaStream_t stream);
 cudaError_t launch_col_absmax(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m,
                               int32_t n, uint32_t* absmax_bits, cudaStream_t stream);

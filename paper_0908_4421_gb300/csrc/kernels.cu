@@ -30,12 +30,33 @@
 
 namespace imrt {
 
+// Tuning knobs of the warp-streaming forward kernel (compile-time).
+#ifndef IMRT_FWD_MINB1
+#define IMRT_FWD_MINB1 2  // resident CTAs per SM the single-trial instance is built for
+#endif
+#ifndef IMRT_FWD_UNROLL
+#define IMRT_FWD_UNROLL 4  // FP32 groups in flight per lane
+#endif
+
 // ---------------------------------------------------------------------------
 // Per-voxel penalty (Eq. (1)): F_j and r_j = dF_j / dz_j at dose z.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void penalty(float z, uint32_t bits, const Terms& T, double& F, float& r) {
+__device__ __forceinline__ void penalty(float z, uint32_t bits, const Terms& T, double& F, float& r, float tj = 0.0f,
+                                        uint32_t tg = 0u) {
     F = 0.0;
     r = 0.0f;
+    if (T.has_vt) {  // per-voxel dose T_j (Eq. (1) as printed)
+        const float eo = z - tj;
+        if (eo > 0.0f) {
+            F += T.vcod * ((double)eo * (double)eo);
+            r += 2.0f * T.vco * eo;
+        }
+        const float eu = tj - z;
+        if (tg && eu > 0.0f) {
+            F += T.vcud * ((double)eu * (double)eu);
+            r -= 2.0f * T.vcu * eu;
+        }
+    }
     while (bits) {
         const int s = __ffs(bits) - 1;
         bits &= bits - 1;
@@ -57,8 +78,8 @@ __device__ __forceinline__ void penalty(float z, uint32_t bits, const Terms& T, 
     if (!isfinite(z)) F = __longlong_as_double(0x7ff8000000000000LL);
 }
 
-__device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T) {
-    float c = 0.0f;
+__device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T, uint32_t tg = 0u) {
+    float c = T.has_vt ? T.vco + (tg ? T.vcu : 0.0f) : 0.0f;
     while (bits) {
         const int s = __ffs(bits) - 1;
         bits &= bits - 1;
@@ -71,17 +92,18 @@ __device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T) {
 // ---------------------------------------------------------------------------
 // Storage formats of the voxel-major copy. GE = entries per 16-byte value load.
 // ---------------------------------------------------------------------------
+// VB / CB: bytes of values / column indices per lane and group.
 struct FmtF32 {
-    static constexpr int GE = 4;
+    static constexpr int GE = 4, VB = 16, CB = 16;
 };
 struct FmtF16 {
-    static constexpr int GE = 8;
+    static constexpr int GE = 8, VB = 16, CB = 16;
 };
 struct FmtBF16 {
-    static constexpr int GE = 8;
+    static constexpr int GE = 8, VB = 16, CB = 16;
 };
 struct FmtF8 {
-    static constexpr int GE = 16;
+    static constexpr int GE = 16, VB = 16, CB = 32;
 };
 
 // acc[q] += v * xs[c * KT + q] for one entry (x_t of all trials interleaved in shared memory).
@@ -129,6 +151,24 @@ __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, cons
         const float4* vp = reinterpret_cast<const float4*>(static_cast<const float*>(val) + off) + lane;
         const int4* cp = reinterpret_cast<const int4*>(static_cast<const int32_t*>(col) + off) + lane;
         int k = g0;
+#if IMRT_FWD_UNROLL >= 4
+        for (; k + 4 <= L; k += 4) {
+            float4 v[4];
+            int4 c[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                v[h] = ld_stream(vp + (size_t)(k + h) * 32);
+                c[h] = ld_stream(cp + (size_t)(k + h) * 32);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                fma_entry<KT>(v[h].x, c[h].x, xs, acc);
+                fma_entry<KT>(v[h].y, c[h].y, xs, acc);
+                fma_entry<KT>(v[h].z, c[h].z, xs, acc);
+                fma_entry<KT>(v[h].w, c[h].w, xs, acc);
+            }
+        }
+#endif
         for (; k + 2 <= L; k += 2) {
             const float4 v0 = ld_stream(vp + (size_t)k * 32);
             const int4 c0 = ld_stream(cp + (size_t)k * 32);
@@ -398,12 +438,67 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
     }
 }
 
+// After a unit's dot products: a piece of a split slice publishes its partial row sums and
+// the last piece to arrive adds them in piece order; then, for complete rows, the penalty
+// epilogue writes z and r and the slice's objective partial.
+template <int KT>
+__device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, int mode, float* const (&zq)[KT],
+                                              float* const (&rq)[KT], int s, int sid, int piece, int lane,
+                                              float (&acc)[KT]) {
+    const FwdUnits& U = a.u;
+    if (sid >= 0) {
+        float* part = U.partials + ((size_t)(U.split_base[sid] + piece) * kSlice + lane) * KT;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) part[q] = acc[q];
+        __threadfence();
+        __syncwarp();
+        int old = 0;
+        if (lane == 0) old = atomicAdd(&U.counters[sid], 1);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        const int P = U.split_pieces[sid];
+        if (old != P - 1) return;
+        __threadfence();
+        const float* base = U.partials + (size_t)U.split_base[sid] * kSlice * KT;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+        for (int k = 0; k < P; ++k) {
+#pragma unroll
+            for (int q = 0; q < KT; ++q) acc[q] += __ldcg(base + ((size_t)k * kSlice + lane) * KT + q);
+        }
+        if (lane == 0) U.counters[sid] = 0;
+    }
+    const int p = s * kSlice + lane;
+    double Fq[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+    if (p < a.m) {
+        const uint32_t bits = a.mask[p];
+        const float tj = a.vt ? a.vt[p] : 0.0f;
+        const uint32_t tg = a.vt ? a.vtm[p] : 0u;
+        if (mode == kFwdPower) {
+            zq[0][p] = acc[0];
+            rq[0][p] = cdiag(bits, T, tg) * acc[0];
+        } else {
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                float rj;
+                penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
+                zq[q][p] = acc[q];
+                rq[q][p] = rj;
+            }
+        }
+    }
+    // objective share of this slice (one partial per slice: scheduling-independent)
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const double g = warp_sum(Fq[q]);
+        if (lane == 0) U.gpart[(size_t)q * U.gstride + s] = g;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward pass (fused step + dose + penalty + objective partials).
 // ---------------------------------------------------------------------------
-#ifndef IMRT_FWD_MINB1
-#define IMRT_FWD_MINB1 3
-#endif
 template <class F, int KT>
 __global__ void __launch_bounds__(kFwdThreads, KT == 1 ? IMRT_FWD_MINB1 : (KT == 2 ? 2 : 1)) k_forward(const FwdArgs a) {
     extern __shared__ __align__(128) float smem[];
@@ -530,61 +625,362 @@ __global__ void __launch_bounds__(kFwdThreads, KT == 1 ? IMRT_FWD_MINB1 : (KT ==
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
         slice_row_dot<F, KT>(a.val, a.col, off, U.unit_g0[u], U.unit_g1[u], lane, xs, acc);
-        bool finish = true;
-        if (sid >= 0) {
-            // piece of a split slice: publish the partial row sums; the last piece finishes the rows
-            float* part = U.partials + ((size_t)(U.split_base[sid] + piece) * kSlice + lane) * KT;
+        unit_epilogue<KT>(a, T, mode, zq, rq, s, sid, piece, lane, acc);
+        u = __shfl_sync(0xffffffffu, u_next, 0);
+    }
+    // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (a.control) control_step(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, gridDim.x);
+    if (tid == 0) {
+        *U.next_unit = 0;
+        *U.ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward pass, bulk-copy pipeline. One producer warp streams slices into a ring
+// of shared-memory stages with cp.async.bulk (values, column indices and, with a
+// slice's last piece, its 32 voxel-mask bytes; all contiguous in HBM), and each
+// consumer warp computes whole slices from shared memory: the producer cuts a
+// slice into pieces of at most kTmaStageGroups groups and sends every piece of it
+// to the same consumer (stage i goes to consumer i mod NC), so the row sums stay
+// in registers across pieces and no slice is ever split between warps. The bytes
+// in flight per SM are the ring's size, independent of registers and occupancy.
+// Slices are dealt to CTAs round-robin over the longest-first list; every wait is
+// bounded.
+// ---------------------------------------------------------------------------
+struct StageMeta {
+    int32_t s;       // slice, or -1: end of this consumer's stream
+    int32_t ng;      // groups in this stage
+    int32_t first;   // the slice's first piece
+    int32_t last;    // the slice's last piece (the stage also carries the mask bytes)
+};
+
+template <class F>
+__host__ __device__ constexpr int tma_stage_bytes() {
+    return kTmaStageGroups * kSlice * (F::VB + F::CB) + 128;  // + mask bytes, 128-byte aligned
+}
+
+// Dot products of one staged piece (groups [0, ng) of the stage, lane = row).
+template <class F, int KT>
+__device__ __forceinline__ void staged_dot(const unsigned char* __restrict__ stage, int ng, int lane,
+                                           const float* __restrict__ xs, float (&acc)[KT]) {
+    const unsigned char* vbase = stage;
+    const unsigned char* cbase = stage + kTmaStageGroups * kSlice * F::VB;
+    for (int k = 0; k < ng; ++k) {
+        const uint4 vw = *reinterpret_cast<const uint4*>(vbase + ((size_t)k * kSlice + lane) * F::VB);
+        if constexpr (F::GE == 4) {
+            const int4 cw = *reinterpret_cast<const int4*>(cbase + ((size_t)k * kSlice + lane) * F::CB);
+            fma_entry<KT>(__uint_as_float(vw.x), cw.x, xs, acc);
+            fma_entry<KT>(__uint_as_float(vw.y), cw.y, xs, acc);
+            fma_entry<KT>(__uint_as_float(vw.z), cw.z, xs, acc);
+            fma_entry<KT>(__uint_as_float(vw.w), cw.w, xs, acc);
+        } else if constexpr (F::GE == 8) {
+            const uint4 cw = *reinterpret_cast<const uint4*>(cbase + ((size_t)k * kSlice + lane) * F::CB);
+            const uint32_t vv[4] = {vw.x, vw.y, vw.z, vw.w};
+            const uint32_t cc[4] = {cw.x, cw.y, cw.z, cw.w};
 #pragma unroll
-            for (int q = 0; q < KT; ++q) part[q] = acc[q];
-            __threadfence();
-            __syncwarp();
-            int old = 0;
-            if (lane == 0) old = atomicAdd(&U.counters[sid], 1);
-            old = __shfl_sync(0xffffffffu, old, 0);
-            const int P = U.split_pieces[sid];
-            finish = (old == P - 1);
-            if (finish) {
-                __threadfence();
-                const float* base = U.partials + (size_t)U.split_base[sid] * kSlice * KT;
+            for (int h = 0; h < 4; ++h) {
+                const float2 f = std::is_same<F, FmtF16>::value ? h2f(vv[h]) : b2f(vv[h]);
+                fma_entry<KT>(f.x, (int)(cc[h] & 0xffffu), xs, acc);
+                fma_entry<KT>(f.y, (int)(cc[h] >> 16), xs, acc);
+            }
+        } else {
+            const uint4 c0 = *reinterpret_cast<const uint4*>(cbase + ((size_t)k * kSlice + lane) * F::CB);
+            const uint4 c1 = *reinterpret_cast<const uint4*>(cbase + ((size_t)k * kSlice + lane) * F::CB + 16);
+            const uint32_t vv[4] = {vw.x, vw.y, vw.z, vw.w};
+            const uint32_t cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-                for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-                for (int k = 0; k < P; ++k) {
-#pragma unroll
-                    for (int q = 0; q < KT; ++q) acc[q] += __ldcg(base + ((size_t)k * kSlice + lane) * KT + q);
-                }
-                if (lane == 0) U.counters[sid] = 0;
+            for (int h = 0; h < 4; ++h) {
+                const float2 lo = e4m3x2f((uint16_t)(vv[h] & 0xffffu));
+                const float2 hi = e4m3x2f((uint16_t)(vv[h] >> 16));
+                fma_entry<KT>(lo.x, (int)(cc[2 * h] & 0xffffu), xs, acc);
+                fma_entry<KT>(lo.y, (int)(cc[2 * h] >> 16), xs, acc);
+                fma_entry<KT>(hi.x, (int)(cc[2 * h + 1] & 0xffffu), xs, acc);
+                fma_entry<KT>(hi.y, (int)(cc[2 * h + 1] >> 16), xs, acc);
             }
         }
-        if (finish) {
-            const int p = s * kSlice + lane;
+    }
+}
+
+template <class F, int KT>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a) {
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t full_bar[kTmaMaxStages];
+    __shared__ __align__(8) uint64_t empty_bar[kTmaMaxStages];
+    __shared__ __align__(8) uint64_t xbar;
+    __shared__ StageMeta meta[kTmaMaxStages];  // written by the producer before a stage's arrive
+    __shared__ Terms T;
+    constexpr int SB = tma_stage_bytes<F>();
+    constexpr int MASK_OFF = kTmaStageGroups * kSlice * (F::VB + F::CB);
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const int NC = (int)(blockDim.x >> 5) - 1;  // consumer warps
+    const int NS = NC * a.stages;              // ring stages
+    const int n_pad = a.n_pad;
+    DevState* st = a.st;
+    const int mode = a.mode;
+
+    int cur = 0;
+    double lam = 0.0, alpha = 2.0;
+    if (mode == kFwdTrial) {
+        if (st->done) return;
+        cur = st->cur;
+        lam = st->lambda;
+        alpha = a.sp->alpha;
+    }
+    const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)(mode == kFwdTrial ? cur : st->cur) * n_pad;
+    float* xs = reinterpret_cast<float*>(tsm);
+    unsigned char* ring = tsm + (((size_t)n_pad * KT * 4 + 127) & ~(size_t)127);
+    float* xstage = reinterpret_cast<float*>(ring);
+    float* gstage = reinterpret_cast<float*>(ring + (((size_t)n_pad * 4 + 127) & ~(size_t)127));
+
+    if (tid == 0) {
+        mbar_init(&xbar, 1);
+        for (int k = 0; k < NS; ++k) {
+            mbar_init(&full_bar[k], 1);
+            mbar_init(&empty_bar[k], 1);
+        }
+        fence_mbar_init();
+    }
+    if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
+    __syncthreads();
+    const uint32_t bytes = (uint32_t)n_pad * 4u;
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&xbar, mode == kFwdTrial ? 2u * bytes : bytes);
+        bulk_g2s(xstage, xsrc, bytes, &xbar);
+        if (mode == kFwdTrial) bulk_g2s(gstage, a.v.g, bytes, &xbar);
+    }
+    const bool failed = __syncthreads_or(!mbar_wait_bounded(&xbar, 0)) != 0;
+    float lamf[KT];
+    {
+        double l = lam;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            lamf[q] = (float)l;
+            l = l / alpha;
+        }
+    }
+    for (int i = tid; i < n_pad; i += blockDim.x) {
+        const float sc = a.scale ? a.scale[i] : 1.0f;
+        if (mode == kFwdTrial) {
+            const float xv = xstage[i], gv = gstage[i];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) xs[(size_t)i * KT + q] = fmaxf(0.0f, fmaf(-lamf[q], gv, xv)) * sc;
+        } else {
+            xs[i] = xstage[i] * sc;
+        }
+    }
+    __syncthreads();  // xs ready; the ring is free
+
+    // Trial points: this CTA writes its chunk of every x_t and its ||x_t - x||^2 partials.
+    if (mode == kFwdTrial && wib == 1) {
+        const int n = a.n;
+        const int chunk = (n + gridDim.x - 1) / gridDim.x;
+        const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+        double d2[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) d2[q] = 0.0;
+        const float* xg = a.v.x + (size_t)cur * n_pad;
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const float xv = xg[i], gv = a.v.g[i];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                const float xt = fmaxf(0.0f, fmaf(-lamf[q], gv, xv));
+                const int set = (cur + 1 + q) % kSets;
+                a.v.x[(size_t)set * n_pad + i] = xt;
+                const double e = (double)xt - (double)xv;
+                d2[q] += e * e;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const double sum = warp_sum(d2[q]);
+            if (lane == 0) a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = sum;
+        }
+    }
+
+    const FwdUnits& U = a.u;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int n_mine = (!failed && U.n_units > b) ? (U.n_units - b + G - 1) / G : 0;  // this CTA's slices
+    const int R = a.stages;  // ring stages per consumer (consumer c owns slots [c R, c R + R))
+    if (wib == 0) {
+        // ---- producer: keeps every consumer's stages filled with pieces of its current slice ----
+        __shared__ int tb_s[32], tb_L[32];
+        __shared__ long long tb_off[32];
+        __shared__ int pc_s[kTmaMaxConsumers], pc_g[kTmaMaxConsumers], pc_L[kTmaMaxConsumers];
+        __shared__ int pc_issued[kTmaMaxConsumers], pc_done[kTmaMaxConsumers];
+        __shared__ long long pc_off[kTmaMaxConsumers];
+        auto refill = [&](int base) {  // metadata of this CTA's local slices base .. base + 31
+            const int li = base + lane;
+            if (li < n_mine) {
+                const int sl = U.unit_slice[b + li * G];
+                tb_s[lane] = sl;
+                tb_L[lane] = a.slice_len[sl];
+                tb_off[lane] = a.slice_off[sl];
+            }
+            __syncwarp();
+        };
+        if (lane < NC) {
+            pc_s[lane] = -1;
+            pc_g[lane] = pc_L[lane] = pc_issued[lane] = pc_done[lane] = 0;
+            pc_off[lane] = 0;
+        }
+        int tb_base = 0;
+        refill(0);
+        int next_li = 0, finished = 0;
+        uint32_t idle = 0;
+        bool perr = false;
+        while (finished < NC && !perr) {
+            int progress = 0, want_refill = 0;
+            if (lane == 0) {
+                for (int c = 0; c < NC; ++c) {
+                    if (pc_done[c]) continue;
+                    const int k = pc_issued[c];
+                    const int slot = c * R + k % R;
+                    if (!mbar_test_wait(&empty_bar[slot], ((k / R) & 1) ^ 1)) continue;  // slot still in use
+                    if (pc_s[c] < 0 || pc_g[c] >= pc_L[c]) {
+                        if (next_li < n_mine) {
+                            const int j = next_li - tb_base;
+                            if (j >= 32) {
+                                want_refill = 1;
+                                break;
+                            }
+                            pc_s[c] = tb_s[j];
+                            pc_L[c] = tb_L[j];
+                            pc_off[c] = tb_off[j];
+                            pc_g[c] = 0;
+                            ++next_li;
+                        } else {
+                            meta[slot] = StageMeta{-1, 0, 0, 0};  // end of consumer c's stream
+                            mbar_arrive(&full_bar[slot]);
+                            pc_done[c] = 1;
+                            pc_issued[c] = k + 1;
+                            ++finished;
+                            progress = 1;
+                            continue;
+                        }
+                    }
+                    const int cs = pc_s[c], cg = pc_g[c], cL = pc_L[c];
+                    const int ng = min(kTmaStageGroups, cL - cg);
+                    const int last = cg + ng >= cL;
+                    meta[slot] = StageMeta{cs, ng, cg == 0 ? 1 : 0, last};
+                    const size_t e0 = (size_t)pc_off[c] + (size_t)cg * kSlice * F::GE;
+                    const uint32_t vb = (uint32_t)ng * kSlice * F::VB, cb = (uint32_t)ng * kSlice * F::CB;
+                    unsigned char* stg = ring + (size_t)slot * SB;
+                    mbar_arrive_expect_tx(&full_bar[slot], vb + cb + (last ? 32u : 0u));
+                    if (ng > 0) {
+                        bulk_g2s(stg, static_cast<const unsigned char*>(a.val) + e0 * (F::VB / F::GE), vb,
+                                 &full_bar[slot]);
+                        bulk_g2s(stg + kTmaStageGroups * kSlice * F::VB,
+                                 static_cast<const unsigned char*>(a.col) + e0 * (F::CB / F::GE), cb,
+                                 &full_bar[slot]);
+                    }
+                    if (last) bulk_g2s(stg + MASK_OFF, a.mask + (size_t)cs * kSlice, 32u, &full_bar[slot]);
+                    pc_g[c] = cg + ng;
+                    pc_issued[c] = k + 1;
+                    progress = 1;
+                }
+            }
+            want_refill = __shfl_sync(0xffffffffu, want_refill, 0);
+            progress = __shfl_sync(0xffffffffu, progress, 0);
+            finished = __shfl_sync(0xffffffffu, finished, 0);
+            next_li = __shfl_sync(0xffffffffu, next_li, 0);
+            if (want_refill) {
+                tb_base = next_li;
+                refill(tb_base);
+                continue;
+            }
+            if (progress) {
+                idle = 0;
+            } else if (++idle > (1u << 22)) {
+                perr = true;  // no consumer released a stage for a very long time
+            } else {
+                __nanosleep(64);
+            }
+        }
+        if (perr && lane == 0) {
+            atomicExch(&st->status, (int)IMRT_ECUDA);
+            // let copies already issued land before the CTA may exit
+            for (int c = 0; c < NC; ++c)
+                for (int k = max(0, pc_issued[c] - R); k < pc_issued[c]; ++k)
+                    mbar_wait_bounded(&full_bar[c * R + k % R], (k / R) & 1);
+        }
+    } else if (wib - 1 < NC) {
+        // ---- consumers ----
+        const int c = wib - 1;
+        float* zq[KT];
+        float* rq[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            if (mode == kFwdTrial) {
+                const int set = (cur + 1 + q) % kSets;
+                zq[q] = a.v.z + (size_t)set * a.m_pad;
+                rq[q] = a.v.r + (size_t)set * a.m_pad;
+            } else {
+                zq[q] = a.z_dst ? a.z_dst : a.v.z + (size_t)st->cur * a.m_pad;
+                rq[q] = a.r_dst ? a.r_dst : a.v.r + (size_t)st->cur * a.m_pad;
+            }
+        }
+        float acc[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+        for (int k = 0;; ++k) {
+            const int slot = c * R + k % R;
+            if (!mbar_wait_bounded(&full_bar[slot], (k / R) & 1)) {
+                if (lane == 0) atomicExch(&st->status, (int)IMRT_ECUDA);
+                break;
+            }
+            const StageMeta mt = meta[slot];
+            const unsigned char* stg = ring + (size_t)slot * SB;
+            if (mt.s < 0) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty_bar[slot]);
+                break;
+            }
+            if (mt.first) {
+#pragma unroll
+                for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+            }
+            staged_dot<F, KT>(stg, mt.ng, lane, xs, acc);
+            const uint32_t bits = mt.last ? (uint32_t)stg[MASK_OFF + lane] : 0u;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[slot]);
+            if (!mt.last) continue;
+            // rows of slice mt.s are complete: penalty epilogue and the slice's objective partial
+            const int p = mt.s * kSlice + lane;
             double Fq[KT];
 #pragma unroll
             for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
             if (p < a.m) {
-                const uint32_t bits = a.mask[p];
+                const float tj = a.vt ? a.vt[p] : 0.0f;
+                const uint32_t tg = a.vt ? a.vtm[p] : 0u;
                 if (mode == kFwdPower) {
                     zq[0][p] = acc[0];
-                    rq[0][p] = cdiag(bits, T) * acc[0];
+                    rq[0][p] = cdiag(bits, T, tg) * acc[0];
                 } else {
 #pragma unroll
                     for (int q = 0; q < KT; ++q) {
                         float rj;
-                        penalty(acc[q], bits, T, Fq[q], rj);
+                        penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
                         zq[q][p] = acc[q];
                         rq[q][p] = rj;
                     }
                 }
             }
-            // objective share of this slice (one partial per slice: scheduling-independent)
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
                 const double g = warp_sum(Fq[q]);
-                if (lane == 0) U.gpart[(size_t)q * U.gstride + s] = g;
+                if (lane == 0) U.gpart[(size_t)q * U.gstride + mt.s] = g;
             }
         }
-        u = __shfl_sync(0xffffffffu, u_next, 0);
     }
-    // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
+    // count finished CTAs: the last one runs the controller inside a solve
     __shared__ int is_last;
     __threadfence();
     __syncthreads();
@@ -876,6 +1272,36 @@ const void* fwd_kernel(int precision, int k_trials) {
         case IMRT_BF16: return fwd_for_kt<FmtBF16>(k_trials);
         case IMRT_FP8E4M3: return fwd_for_kt<FmtF8>(k_trials);
         default: return nullptr;
+    }
+}
+
+template <class F>
+static const void* fwd_tma_for_kt(int kt) {
+    switch (kt) {
+        case 1: return (const void*)k_forward_tma<F, 1>;
+        case 2: return (const void*)k_forward_tma<F, 2>;
+        case 4: return (const void*)k_forward_tma<F, 4>;
+        case 8: return (const void*)k_forward_tma<F, 8>;
+        default: return nullptr;
+    }
+}
+
+const void* fwd_tma_kernel(int precision, int k_trials) {
+    switch (precision) {
+        case IMRT_FP32: return fwd_tma_for_kt<FmtF32>(k_trials);
+        case IMRT_FP16: return fwd_tma_for_kt<FmtF16>(k_trials);
+        case IMRT_BF16: return fwd_tma_for_kt<FmtBF16>(k_trials);
+        case IMRT_FP8E4M3: return fwd_tma_for_kt<FmtF8>(k_trials);
+        default: return nullptr;
+    }
+}
+
+int fwd_tma_stage_bytes(int precision) {
+    switch (precision) {
+        case IMRT_FP32: return tma_stage_bytes<FmtF32>();
+        case IMRT_FP16: return tma_stage_bytes<FmtF16>();
+        case IMRT_BF16: return tma_stage_bytes<FmtBF16>();
+        default: return tma_stage_bytes<FmtF8>();
     }
 }
 

@@ -56,6 +56,7 @@ class PhantomSpec:
     mu_per_mm: float = 0.005
     sigma_mm: float = 2.5
     cutoff: float = 1e-3
+    coarse_unspecified: bool = False  # unspecified tissue only on the 2x coarser grid (Sec. 3.1)
     # per-structure (under, over) thresholds in Gy (NaN: no term) and weights
     thresholds: Tuple[Tuple[float, float], ...] = ((76.0, 78.0), (NAN, 40.0), (NAN, 45.0), (NAN, 30.0))
     weights: Tuple[Tuple[float, float], ...] = ((100.0, 100.0), (0.0, 10.0), (0.0, 5.0), (0.0, 1.0))
@@ -74,6 +75,7 @@ class _CSpec(ctypes.Structure):
         ("angle0_deg", ctypes.c_double), ("beamlet_mm", ctypes.c_double),
         ("margin_mm", ctypes.c_double), ("mu_per_mm", ctypes.c_double),
         ("sigma_mm", ctypes.c_double), ("cutoff", ctypes.c_double),
+        ("coarse_unspecified", ctypes.c_int32),
     ]
 
 
@@ -95,6 +97,7 @@ def _to_c(s: PhantomSpec) -> _CSpec:
     c.mu_per_mm = s.mu_per_mm
     c.sigma_mm = s.sigma_mm
     c.cutoff = s.cutoff
+    c.coarse_unspecified = 1 if s.coarse_unspecified else 0
     return c
 
 
@@ -134,6 +137,18 @@ def _lib() -> ctypes.CDLL:
 
 
 @dataclasses.dataclass
+class VoxelTargets:
+    """Per-voxel dose targets of Eq. (1) as printed: T_j is the original plan's dose, V_T the
+    target voxels (under-dose term), every voxel carries the over-dose term."""
+
+    dose: np.ndarray        # float32 [m], T_j
+    target: np.ndarray      # uint8 [m], 1 => j in V_T
+    w_under: float = 1.0
+    w_over: float = 1.0
+    normalise: bool = False  # divide the terms by |V_T| and m
+
+
+@dataclasses.dataclass
 class Case:
     """One generated planning problem (host arrays)."""
 
@@ -146,6 +161,7 @@ class Case:
     weights: np.ndarray      # float32 [S, 2]
     voxels: np.ndarray       # float32 [m, 3] voxel centres (mm)
     beamlets: np.ndarray     # float32 [n, 3] (beam, u, v)
+    voxel_targets: Optional[VoxelTargets] = None
 
     @property
     def m(self) -> int:
@@ -206,11 +222,26 @@ PROSTATE_2P5MM_9BEAM = dataclasses.replace(
 PROSTATE_2P5MM_9BEAM_L = dataclasses.replace(
     PROSTATE_2P5MM_9BEAM, beamlet_mm=2.5, sigma_mm=6.0, cutoff=1e-4)
 
+#: The literal paper-shaped grid with the unspecified tissue on the 2x coarser grid (Sec. 3.1).
+PROSTATE_2P5MM_9BEAM_MIXED = dataclasses.replace(PROSTATE_2P5MM_9BEAM, coarse_unspecified=True)
+
 WORKLOADS: Dict[str, PhantomSpec] = {
     "tiny-40x40x30-5mm-5beam": TINY_5MM_5BEAM,
     "prostate-192x160x96-2.5mm-9beam": PROSTATE_2P5MM_9BEAM,
     "prostate-192x160x96-2.5mm-9beam-2.5mm-beamlets": PROSTATE_2P5MM_9BEAM_L,
+    "prostate-192x160x96-2.5mm-9beam-mixed-resolution": PROSTATE_2P5MM_9BEAM_MIXED,
 }
+
+
+def with_voxel_targets(case: Case, dose: np.ndarray, target: Optional[np.ndarray] = None, w_under: float = 1.0,
+                       w_over: float = 1.0, normalise: bool = False) -> Case:
+    """A copy of `case` whose objective also carries Eq. (1)'s per-voxel terms around `dose`
+    (default V_T: the PTV, structure bit 0)."""
+    if target is None:
+        target = (case.mask & 1).astype(np.uint8)
+    vt = VoxelTargets(np.ascontiguousarray(dose, np.float32), np.ascontiguousarray(target, np.uint8),
+                      float(w_under), float(w_over), bool(normalise))
+    return dataclasses.replace(case, voxel_targets=vt)
 
 
 def jittered_spec(seed: int, shift_mm: float = 0.0, base: PhantomSpec = TINY_5MM_5BEAM,

@@ -23,7 +23,11 @@
  *             the path length inside the body from the entry surface to voxel j
  *             along the beam, and rho is the distance of voxel j's centre from
  *             beamlet i's central ray. Entries below `cutoff` are dropped.
- *   Rows    : body voxels only, raster order (z slowest, then y, then x).
+ *   Rows    : body voxels only, raster order (z slowest, then y, then x). With
+ *             coarse_unspecified, voxels in no structure but the body are kept
+ *             only where all three grid indices are even (the 2x coarser grid
+ *             of the paper's Sec. 3.1 for unspecified tissue), at that voxel's
+ *             centre.
  *   Columns : beam-major, then v row, then u, over kept beamlets; each row's
  *             columns come out strictly increasing.
  *
@@ -50,6 +54,7 @@ typedef struct {
     double mu_per_mm;
     double sigma_mm;
     double cutoff;
+    int32_t coarse_unspecified; /* 1: tissue outside the PTV and organs only on the 2x coarser grid */
 } phantom_spec;
 
 #define BIT_PTV 1u
@@ -64,12 +69,35 @@ static int in_body(const phantom_spec* s, double x, double y) {
     return a * a + b * b <= 1.0;
 }
 
+static uint8_t structure_bits(const phantom_spec* s, double x, double y, double z) {
+    uint8_t b = BIT_BODY;
+    double px = (x - s->ptv_c[0]) / s->ptv_r[0];
+    double py = (y - s->ptv_c[1]) / s->ptv_r[1];
+    double pz = (z - s->ptv_c[2]) / s->ptv_r[2];
+    if (px * px + py * py + pz * pz <= 1.0) b |= BIT_PTV;
+    double ry = y - s->rect_y;
+    if (x * x + ry * ry <= s->rect_r * s->rect_r && z >= s->rect_z0 && z <= s->rect_z1) b |= BIT_RECTUM;
+    double bx = x - s->blad_c[0], by = y - s->blad_c[1], bz = z - s->blad_c[2];
+    if (bx * bx + by * by + bz * bz <= s->blad_r * s->blad_r) b |= BIT_BLADDER;
+    return b;
+}
+
+/* Whether grid voxel (ix, iy, iz) is a row of D. */
+static int keep_voxel(const phantom_spec* s, int32_t ix, int32_t iy, int32_t iz) {
+    double x = coord(ix, s->nx, s->spacing), y = coord(iy, s->ny, s->spacing), z = coord(iz, s->nz, s->spacing);
+    if (!in_body(s, x, y)) return 0;
+    if (!s->coarse_unspecified) return 1;
+    if (structure_bits(s, x, y, z) != BIT_BODY) return 1;
+    return (ix % 2 == 0) && (iy % 2 == 0) && (iz % 2 == 0);
+}
+
 int64_t phantom_count_body(const phantom_spec* s) {
-    int64_t per_slice = 0;
-    for (int32_t iy = 0; iy < s->ny; ++iy)
-        for (int32_t ix = 0; ix < s->nx; ++ix)
-            if (in_body(s, coord(ix, s->nx, s->spacing), coord(iy, s->ny, s->spacing))) ++per_slice;
-    return per_slice * (int64_t)s->nz;
+    int64_t m = 0;
+    for (int32_t iz = 0; iz < s->nz; ++iz)
+        for (int32_t iy = 0; iy < s->ny; ++iy)
+            for (int32_t ix = 0; ix < s->nx; ++ix)
+                if (keep_voxel(s, ix, iy, iz)) ++m;
+    return m;
 }
 
 /* Voxel centres (m x 3, mm) and structure bitmask (m). */
@@ -81,22 +109,13 @@ void phantom_fill_voxels(const phantom_spec* s, float* xyz, uint8_t* mask) {
             double y = coord(iy, s->ny, s->spacing);
             for (int32_t ix = 0; ix < s->nx; ++ix) {
                 double x = coord(ix, s->nx, s->spacing);
-                if (!in_body(s, x, y)) continue;
-                uint8_t b = BIT_BODY;
-                double px = (x - s->ptv_c[0]) / s->ptv_r[0];
-                double py = (y - s->ptv_c[1]) / s->ptv_r[1];
-                double pz = (z - s->ptv_c[2]) / s->ptv_r[2];
-                if (px * px + py * py + pz * pz <= 1.0) b |= BIT_PTV;
-                double ry = y - s->rect_y;
-                if (x * x + ry * ry <= s->rect_r * s->rect_r && z >= s->rect_z0 && z <= s->rect_z1) b |= BIT_RECTUM;
-                double bx = x - s->blad_c[0], by = y - s->blad_c[1], bz = z - s->blad_c[2];
-                if (bx * bx + by * by + bz * bz <= s->blad_r * s->blad_r) b |= BIT_BLADDER;
+                if (!keep_voxel(s, ix, iy, iz)) continue;
                 if (xyz) {
                     xyz[3 * j + 0] = (float)x;
                     xyz[3 * j + 1] = (float)y;
                     xyz[3 * j + 2] = (float)z;
                 }
-                mask[j] = b;
+                mask[j] = structure_bits(s, x, y, z);
                 ++j;
             }
         }
@@ -240,8 +259,8 @@ static double* body_centres(const phantom_spec* s, int64_t m) {
     for (int32_t iz = 0; iz < s->nz; ++iz)
         for (int32_t iy = 0; iy < s->ny; ++iy)
             for (int32_t ix = 0; ix < s->nx; ++ix) {
+                if (!keep_voxel(s, ix, iy, iz)) continue;
                 double x = coord(ix, s->nx, s->spacing), y = coord(iy, s->ny, s->spacing);
-                if (!in_body(s, x, y)) continue;
                 c[3 * j + 0] = x;
                 c[3 * j + 1] = y;
                 c[3 * j + 2] = coord(iz, s->nz, s->spacing);

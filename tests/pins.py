@@ -289,8 +289,84 @@ def pin_stops(orc):
     np.testing.assert_array_equal(res3.x, 0.0)
 
 
+def _vt_case(d, dose, target, wu, wo, normalise):
+    m = d.shape[0]
+    base = _case_from_dense(d, np.ones(m, np.uint8), [(float("nan"), float("nan"))], [(0.0, 0.0)])
+    return phantom.with_voxel_targets(base, np.asarray(dose, np.float32), np.asarray(target, np.uint8), wu, wo,
+                                      normalise)
+
+
+def pin_voxel_targets_hand(orc):
+    """Eq. (1) as printed, per-voxel T_j on D = I, values worked out by hand (G = 2, and 0.625 normalised)."""
+    x = np.array([0.5, 2.5, 3.5, 3.0])
+    for normalise, G_exp, r_exp in ((False, 2.0, [-2.0, 3.0, 3.0, 0.0]), (True, 0.625, [-1.0, 0.75, 0.75, 0.0])):
+        case = _vt_case(np.eye(4), [1.0, 2.0, 3.0, 4.0], [1, 1, 0, 0], 2.0, 3.0, normalise)
+        G, z, r, g = orc.eval(case, x)
+        assert abs(G - G_exp) < 1e-12, (normalise, G)
+        np.testing.assert_allclose(r, r_exp, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(g, r_exp, rtol=0, atol=1e-14)
+
+
+def pin_voxel_targets_exact_fit(orc):
+    """D = I, every voxel in V_T: G = w sum (x - T)^2 and the step 1/(2w) lands on x = T (G = 0)."""
+    from oracle import STOP_EXACT
+    t = np.array([1.0, 2.0, 0.5, 3.0, 1.5])
+    case = _vt_case(np.eye(5), t, np.ones(5), 4.0, 4.0, False)
+    res = orc.solve(case, lambda0=1.0 / 8.0, x_init=1, max_iter=10)
+    assert res.status == 0 and res.stop_reason == STOP_EXACT and res.iterations == 1
+    np.testing.assert_allclose(res.x, t, rtol=0, atol=0)
+    # the x_init = 0 rule: s = sum_VT T / sum_VT (D 1) = mean(T) on D = I
+    np.testing.assert_allclose(orc.initial_point(case, 0), np.full(5, t.mean()), rtol=1e-15)
+
+
+def pin_voxel_targets_fd(orc, seed=13):
+    """Central differences of G with per-voxel targets on a random sparse D."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = phantom.random_case(seed, m=70, n=12, density=0.35, n_structures=2)
+    dose = rng.uniform(0.2, 1.5, base.m)
+    case = phantom.with_voxel_targets(base, dose, (rng.uniform(size=base.m) < 0.4).astype(np.uint8), 3.0, 2.0,
+                                      True)
+    x = rng.uniform(0.1, 1.0, base.n)
+    G0, z0, r0, g = orc.eval(case, x)
+    G_ref, g_ref = dense_objective_vt(case, x)
+    assert abs(G0 - G_ref) <= 1e-12 * max(1.0, G_ref)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-11, atol=1e-12)
+    checked = 0
+    for i in range(base.n):
+        h = 1e-5
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        Gp, zp, _, _ = orc.eval(case, xp, gradient=False)
+        Gm, zm, _, _ = orc.eval(case, xm, gradient=False)
+        kinks = [dose] + [np.full(base.m, t) for t in case.thresholds[~np.isnan(case.thresholds)]]
+        if any(np.any(np.sign(zp - k) != np.sign(zm - k)) for k in kinks):
+            continue
+        assert abs((Gp - Gm) / (2 * h) - g[i]) <= 1e-7 * max(1.0, abs(g[i]))
+        checked += 1
+    assert checked >= 3
+
+
+def dense_objective_vt(case, x):
+    """dense_objective plus Eq. (1)'s per-voxel terms (test-side restatement)."""
+    G, g = dense_objective(case, x)
+    vt = case.voxel_targets
+    d = phantom.csr_to_dense(case)
+    z = d @ x
+    nt = int(vt.target.sum())
+    cu = vt.w_under / (nt if vt.normalise else 1)
+    co = vt.w_over / (case.m if vt.normalise else 1)
+    t = vt.dose.astype(np.float64)
+    over = np.maximum(0.0, z - t)
+    under = np.maximum(0.0, t - z) * vt.target
+    G += co * float(np.sum(over ** 2)) + cu * float(np.sum(under ** 2))
+    r = 2 * co * over - 2 * cu * under
+    return G, g + d.T @ r
+
+
 ALL_PINS = ("pin_objective_hand", "pin_dose_dense", "pin_gradient_dense", "pin_nnls", "pin_lbfgsb",
-            "pin_scalar_exact", "pin_lambda0_rule", "pin_stops", "pin_sufficient_decrease")
+            "pin_scalar_exact", "pin_lambda0_rule", "pin_stops", "pin_sufficient_decrease",
+            "pin_voxel_targets_hand", "pin_voxel_targets_exact_fit", "pin_voxel_targets_fd")
 
 
 def pin_sufficient_decrease(orc, case=None):

@@ -30,12 +30,13 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def test_full_size_eval(big):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_full_size_eval(big, variant):
     case = big
     orc = oracle.get()
     threads = os.cpu_count() or 1
     x1 = orc.initial_point(case).astype(np.float32)
-    with Plan.from_case(case, device=True) as plan:
+    with Plan.from_case(case, Options(kernel_variant=variant), device=True) as plan:
         G, z, g = plan.eval(x1)
         info = plan.info()
     G_ref, z_ref, _, g_ref = orc.eval(case, x1.astype(np.float64), threads=threads)
@@ -47,12 +48,14 @@ def test_full_size_eval(big):
     assert np.all(np.abs(z - z_ref) <= 1e-5 * np.abs(z_ref) + 1e-6 * np.abs(z_ref).max())
 
 
-@pytest.mark.parametrize("k_trials", [1, 4])
-def test_full_size_iterations(big, k_trials):
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("k_trials", [1, 2])
+def test_full_size_iterations(big, k_trials, variant):
     case = big
     orc = oracle.get()
     threads = os.cpu_count() or 1
-    with Plan.from_case(case, Options(max_iter=4, trace=2, k_trials=k_trials), device=True) as plan:
+    with Plan.from_case(case, Options(max_iter=4, trace=2, k_trials=k_trials, kernel_variant=variant),
+                        device=True) as plan:
         lam0 = plan.info()["lambda0_rule"]
         res = plan.solve()
         G, lam, bt, xs = plan.trace(res.iterations, with_x=True)

@@ -52,12 +52,16 @@ def orc():
     return oracle.get()
 
 
+VARIANTS = [0, 1]  # forward kernel: warp streaming, bulk-copy (TMA) pipeline
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("name", sorted(RANDOM_CASES))
 @pytest.mark.parametrize("device_inputs", [False, True])
-def test_dose_and_eval_random(orc, name, device_inputs):
+def test_dose_and_eval_random(orc, name, device_inputs, variant):
     case = phantom.random_case(n_structures=3, **RANDOM_CASES[name])
     rng = np.random.Generator(np.random.PCG64(7))
-    with Plan.from_case(case, Options(), device=device_inputs) as plan:
+    with Plan.from_case(case, Options(kernel_variant=variant), device=device_inputs) as plan:
         for trial in range(3):
             x = rng.uniform(0, 2, case.n).astype(np.float32)
             G, z, g = plan.eval(x)
@@ -117,12 +121,13 @@ def _solve_pair(orc, case, lam0, **kw):
     return ref, res, G, lam, bt, xs, z_final, x_final
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("mode", [L.MODE_GRAPH, L.MODE_HOST])
-def test_tiny_phantom_solve_parity(orc, tiny, mode):
+def test_tiny_phantom_solve_parity(orc, tiny, mode, variant):
     """Per iteration: dose of the GPU iterate within 1e-5 of the oracle's, until the first
     disagreement in the accepted step; final objective within 1e-4."""
     case, lam0 = tiny
-    ref, res, G, lam, bt, xs, z_final, x_final = _solve_pair(orc, case, lam0, mode=mode)
+    ref, res, G, lam, bt, xs, z_final, x_final = _solve_pair(orc, case, lam0, mode=mode, kernel_variant=variant)
     assert res.status == 0
     assert abs(res.objective - ref.objective) <= FINAL_RTOL * ref.objective
     assert abs(res.initial_objective - ref.initial_objective) <= OBJ_RTOL * ref.initial_objective
@@ -156,14 +161,16 @@ def test_graph_and_host_modes_agree_bitwise(tiny):
     np.testing.assert_array_equal(out[0][3], out[1][3])
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("k_trials", [2, 4, 8])
-def test_k_trials_same_trajectory(tiny, k_trials):
+def test_k_trials_same_trajectory(tiny, k_trials, variant):
     """Evaluating k step sizes per pass over D takes exactly the sequential Armijo decisions."""
     case, lam0 = tiny
     big = 16 * lam0  # forces backtracking so batches matter
     runs = []
     for kt in (1, k_trials):
-        with Plan.from_case(case, Options(lambda0=big, max_iter=40, trace=1, k_trials=kt)) as plan:
+        with Plan.from_case(case, Options(lambda0=big, max_iter=40, trace=1, k_trials=kt,
+                                          kernel_variant=variant)) as plan:
             res = plan.solve()
             G, lam, bt, _ = plan.trace(res.iterations)
             runs.append((res, G, lam, bt))
@@ -264,13 +271,14 @@ def gradient_scale(case, z_ref, r_ref):
     return d.T @ (np.abs(r_ref) + 2 * c * np.abs(z_ref))
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("prec,dose_tol,obj_tol", REDUCED)
-def test_reduced_precision_eval(orc, tiny, prec, dose_tol, obj_tol):
+def test_reduced_precision_eval(orc, tiny, prec, dose_tol, obj_tol, variant):
     """The reduced-precision copies (forward and transposed) against the FP64 oracle at x_1."""
     case, lam0 = tiny
     x1 = orc.initial_point(case).astype(np.float32)
     G_ref, z_ref, r_ref, g_ref = orc.eval(case, x1.astype(np.float64))
-    with Plan.from_case(case, Options(lambda0=lam0, precision=prec)) as plan:
+    with Plan.from_case(case, Options(lambda0=lam0, precision=prec, kernel_variant=variant)) as plan:
         G, z, g = plan.eval(x1)
         z32 = plan.dose(x1)  # always the FP32 copy
     assert rel(z32, z_ref) <= DOSE_RTOL

@@ -25,6 +25,9 @@ MUTANTS = {
     "dose_wrong_operand": ("s += (double)P->val[k] * x[P->col[k]];", "s += (double)P->val[k] * x[j % P->n];"),
     "gradient_drops_value": ("s += (double)tval[k] * r[trow[k]];", "s += r[trow[k]];"),
     "backtrack_wrong_direction": ("lam = lam / q->alpha; /* step 4 */", "lam = lam * q->alpha; /* step 4 */"),
+    "voxel_target_under_sign": ("d -= 2.0 * vcu * e;", "d += 2.0 * vcu * e;"),
+    "voxel_target_no_normalise": ("*co = P->m > 0 ? P->vt_wo / (P->vt_normalise ? (double)P->m : 1.0) : 0.0;",
+                                  "*co = P->m > 0 ? P->vt_wo : 0.0;"),
 }
 
 

@@ -68,3 +68,12 @@ def test_random_case_ragged():
     c = phantom.random_case(0, m=50, n=9, density=0.2, empty_rows=5, long_rows=3)
     lens = np.diff(c.row_ptr)
     assert (lens == 0).sum() >= 5 and (lens == 9).sum() >= 3
+
+
+def test_mixed_resolution_keeps_organs_full():
+    fine = phantom.make_case(phantom.PROSTATE_2P5MM_9BEAM)
+    mixed = phantom.make_case(phantom.PROSTATE_2P5MM_9BEAM_MIXED)
+    for b in range(3):  # PTV, rectum and bladder keep every voxel
+        assert int(((fine.mask >> b) & 1).sum()) == int(((mixed.mask >> b) & 1).sum())
+    unspecified = lambda c: int((c.mask == 8).sum())
+    assert unspecified(mixed) < unspecified(fine) / 7
