@@ -284,6 +284,10 @@ imrt_status validate_options(const imrt_options* o) {
 // Work units of one copy for a given forward grid: slices whose cost exceeds half a warp's
 // share are cut into near-equal pieces (ranges of groups); units are then dealt to warps in
 // contiguous runs of near-equal cost (stored entries plus an epilogue allowance per slice).
+#ifndef IMRT_FWD_PIECES
+#define IMRT_FWD_PIECES 4  // pieces of a warp's share that bound a forward work unit
+#endif
+
 imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int variant, FwdShape* out) {
     int max_smem = 0;
     CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
@@ -359,8 +363,11 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
     for (int s = 0; s < p->n_slices; ++s) total += c.host_cost[s];
     const double budget = (double)total / W;
     // the bulk-copy kernel streams whole slices (its producer cuts them into stage-sized pieces)
+    // Heavy slices are cut into pieces of at most 1/IMRT_FWD_PIECES of a warp's share, so the
+    // last units taken are short and the warps finish together.
     const int64_t piece_groups =
-        variant == 1 ? INT64_MAX / 4 : std::max<int64_t>(4, (int64_t)(budget / group_entries));
+        variant == 1 ? INT64_MAX / 4
+                     : std::max<int64_t>(4, (int64_t)(budget / ((double)group_entries * IMRT_FWD_PIECES)));
     std::vector<int32_t> us, ug0, ug1, usplit, upiece, spieces, sbase;
     std::vector<int64_t> ucost;
     int32_t parts = 0;
@@ -418,6 +425,11 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
     TRY(dalloc(p, &U.counters, std::max(out->n_splits, 1)));
     CK(cudaMemsetAsync(U.counters, 0, sizeof(int32_t) * std::max(out->n_splits, 1), stream_of(p)));
     TRY(dalloc(p, &U.gpart, (size_t)k_trials * out->gstride));
+    U.n_slices = p->n_slices;
+    U.n_groups = (p->n_slices + kGroupSlices - 1) / kGroupSlices;
+    TRY(dalloc(p, &U.gsum, (size_t)k_trials * std::max(U.n_groups, 1)));
+    TRY(dalloc(p, &U.gcount, std::max(U.n_groups, 1)));
+    CK(cudaMemsetAsync(U.gcount, 0, sizeof(int32_t) * std::max(U.n_groups, 1), stream_of(p)));
     TRY(dalloc(p, &U.ticket, 1));
     TRY(dalloc(p, &U.next_unit, 1));
     CK(cudaMemsetAsync(U.ticket, 0, sizeof(int32_t), stream_of(p)));
@@ -503,7 +515,7 @@ imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, f
     a.r_dst = r_dst;
     void* args[] = {&a};
     CK(cudaLaunchKernel(sh->fn1, dim3(sh->grid), dim3(sh->block), args, sh->smem1, stream_of(p)));
-    if (G_out) CK(launch_g_objective(sh->units.gpart, sh->gstride, G_out, stream_of(p)));
+    if (G_out) CK(launch_g_objective(sh->units.gsum, sh->units.n_groups, G_out, stream_of(p)));
     return IMRT_OK;
 }
 
@@ -826,8 +838,8 @@ SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_in
     q.m = p->m;
     q.m_pad = p->m_pad;
     q.fwd_grid = sh.grid;
-    q.gstride = sh.gstride;
-    q.gpart = sh.units.gpart;
+    q.n_groups = sh.units.n_groups;
+    q.gsum = sh.units.gsum;
     q.timeout_ns = o.timeout_ms > 0.0 ? (unsigned long long)(o.timeout_ms * 1e6) : 0ull;
     q.tr_G = o.trace >= 1 ? p->tr_G : nullptr;
     q.tr_lam = o.trace >= 1 ? p->tr_lam : nullptr;

@@ -23,6 +23,7 @@ constexpr int kSlice = 32;        // SELL chunk height: rows per warp
 constexpr int kSigma = 1024;      // sorting window (rows)
 constexpr int kMaxStruct = 8;
 constexpr int kMaxTrials = 8;     // Armijo step sizes per forward pass
+constexpr int kGroupSlices = 32;  // slices per objective group sum
 constexpr int kSets = kMaxTrials + 1;  // x/z/r buffer sets: accepted + trials
 constexpr int kFwdThreads = 512;
 constexpr int kBwdThreads = 512;
@@ -80,8 +81,8 @@ struct DevState {
 struct SolveParams {
     double eps, alpha, delta, lambda0, x1_scale;
     int32_t max_iter, max_bt, x_init, k_trials, trace, n, n_pad, m, m_pad;
-    int32_t fwd_grid, gstride;  // forward grid; objective partials per trial
-    const double* gpart;        // objective partials of the forward shape in use
+    int32_t fwd_grid, n_groups;  // forward grid; objective group sums per trial
+    const double* gsum;          // objective group sums of the forward shape in use
     unsigned long long timeout_ns;
     double* tr_G;
     double* tr_lam;
@@ -119,9 +120,11 @@ struct FwdUnits {
     float* partials;             // (sum of pieces) * 32 * k_trials
     int32_t* counters;           // n_splits arrival counters, left at 0
     double* gpart;               // k_trials * gstride objective partials, one per slice
+    double* gsum;                // k_trials * n_groups sums of kGroupSlices consecutive slice partials
+    int32_t* gcount;             // n_groups arrival counters, left at 0
     int32_t* next_unit;          // dynamic schedule counter, reset by the last CTA
     int32_t* ticket;             // CTAs finished in the current launch
-    int32_t n_units, n_splits, gstride;
+    int32_t n_units, n_splits, gstride, n_slices, n_groups;
 };
 
 struct FwdArgs {

@@ -32,10 +32,10 @@ namespace imrt {
 
 // Tuning knobs of the warp-streaming forward kernel (compile-time).
 #ifndef IMRT_FWD_MINB1
-#define IMRT_FWD_MINB1 2  // resident CTAs per SM the single-trial instance is built for
+#define IMRT_FWD_MINB1 1  // resident CTAs per SM the single-trial instance is built for
 #endif
 #ifndef IMRT_FWD_UNROLL
-#define IMRT_FWD_UNROLL 4  // FP32 groups in flight per lane
+#define IMRT_FWD_UNROLL 8  // groups in flight per lane (FP8: half as many, each is 48 bytes)
 #endif
 
 // ---------------------------------------------------------------------------
@@ -141,98 +141,77 @@ __device__ __forceinline__ float2 e4m3x2f(uint16_t w) {
     return __half22float2(h);
 }
 
-// One row (one lane) of a slice: acc[q] = sum over the row's entries in storage order.
-// Groups [g0, g1) of one slice; lane = row within the slice.
+// One group of one lane: GE consecutive entries of the lane's row (values, then columns).
+struct GroupRegs {
+    uint4 v;   // FP32: 4 values; FP16 / BF16: 8 values; FP8: 16 values
+    uint4 c0;  // FP32: 4 int32 columns; 16-bit formats: 8 uint16 columns
+    uint4 c1;  // FP8: columns 8..15
+};
+
+template <class F>
+__device__ __forceinline__ void load_group(const void* __restrict__ val, const void* __restrict__ col, int64_t off,
+                                           int k, int lane, GroupRegs& g) {
+    if constexpr (F::GE == 4) {
+        g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 32 + lane);
+        g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const int32_t*>(col) + off) + (size_t)k * 32 + lane);
+    } else if constexpr (F::GE == 8) {
+        g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + off) + (size_t)k * 32 + lane);
+        g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane);
+    } else {
+        const uint4* cp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 64 + 2 * lane;
+        g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(val) + off) + (size_t)k * 32 + lane);
+        g.c0 = ld_stream(cp);
+        g.c1 = ld_stream(cp + 1);
+    }
+}
+
+// acc[q] += the group's entries in storage order.
+template <class F, int KT>
+__device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __restrict__ xs, float (&acc)[KT]) {
+    const uint32_t vv[4] = {g.v.x, g.v.y, g.v.z, g.v.w};
+    const uint32_t cc[4] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w};
+    if constexpr (F::GE == 4) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) fma_entry<KT>(__uint_as_float(vv[h]), (int)cc[h], xs, acc);
+    } else if constexpr (F::GE == 8) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 f = std::is_same<F, FmtF16>::value ? h2f(vv[h]) : b2f(vv[h]);
+            fma_entry<KT>(f.x, (int)(cc[h] & 0xffffu), xs, acc);
+            fma_entry<KT>(f.y, (int)(cc[h] >> 16), xs, acc);
+        }
+    } else {
+        const uint32_t c8[8] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w, g.c1.x, g.c1.y, g.c1.z, g.c1.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 lo = e4m3x2f((uint16_t)(vv[h] & 0xffffu));
+            const float2 hi = e4m3x2f((uint16_t)(vv[h] >> 16));
+            fma_entry<KT>(lo.x, (int)(c8[2 * h] & 0xffffu), xs, acc);
+            fma_entry<KT>(lo.y, (int)(c8[2 * h] >> 16), xs, acc);
+            fma_entry<KT>(hi.x, (int)(c8[2 * h + 1] & 0xffffu), xs, acc);
+            fma_entry<KT>(hi.y, (int)(c8[2 * h + 1] >> 16), xs, acc);
+        }
+    }
+}
+
+// One row (one lane) of a slice: acc[q] += the row's entries in groups [g0, g1), in storage
+// order. Rounds of IMRT_FWD_UNROLL groups: all of a round's 128-bit loads are issued before
+// any is used, so each lane keeps UNROLL x (value + column) bytes in flight; the last round
+// is guarded per group (the guard is uniform across the warp).
 template <class F, int KT>
 __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, const void* __restrict__ col,
-                                              int64_t off, int g0, int L, int lane, const float* __restrict__ xs,
+                                              int64_t off, int g0, int g1, int lane, const float* __restrict__ xs,
                                               float (&acc)[KT]) {
-    if constexpr (F::GE == 4) {  // FP32 values, int32 columns
-        const float4* vp = reinterpret_cast<const float4*>(static_cast<const float*>(val) + off) + lane;
-        const int4* cp = reinterpret_cast<const int4*>(static_cast<const int32_t*>(col) + off) + lane;
-        int k = g0;
-#if IMRT_FWD_UNROLL >= 4
-        for (; k + 4 <= L; k += 4) {
-            float4 v[4];
-            int4 c[4];
+    // FP8 groups are 48 bytes and four or more trials need their accumulators: half the rounds
+    constexpr int U = ((F::GE == 16 || KT >= 4) && IMRT_FWD_UNROLL > 4) ? IMRT_FWD_UNROLL / 2 : IMRT_FWD_UNROLL;
+    for (int k = g0; k < g1; k += U) {
+        GroupRegs r[U];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                v[h] = ld_stream(vp + (size_t)(k + h) * 32);
-                c[h] = ld_stream(cp + (size_t)(k + h) * 32);
-            }
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) load_group<F>(val, col, off, k + h, lane, r[h]);
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                fma_entry<KT>(v[h].x, c[h].x, xs, acc);
-                fma_entry<KT>(v[h].y, c[h].y, xs, acc);
-                fma_entry<KT>(v[h].z, c[h].z, xs, acc);
-                fma_entry<KT>(v[h].w, c[h].w, xs, acc);
-            }
-        }
-#endif
-        for (; k + 2 <= L; k += 2) {
-            const float4 v0 = ld_stream(vp + (size_t)k * 32);
-            const int4 c0 = ld_stream(cp + (size_t)k * 32);
-            const float4 v1 = ld_stream(vp + (size_t)(k + 1) * 32);
-            const int4 c1 = ld_stream(cp + (size_t)(k + 1) * 32);
-            fma_entry<KT>(v0.x, c0.x, xs, acc);
-            fma_entry<KT>(v0.y, c0.y, xs, acc);
-            fma_entry<KT>(v0.z, c0.z, xs, acc);
-            fma_entry<KT>(v0.w, c0.w, xs, acc);
-            fma_entry<KT>(v1.x, c1.x, xs, acc);
-            fma_entry<KT>(v1.y, c1.y, xs, acc);
-            fma_entry<KT>(v1.z, c1.z, xs, acc);
-            fma_entry<KT>(v1.w, c1.w, xs, acc);
-        }
-        if (k < L) {
-            const float4 v0 = ld_stream(vp + (size_t)k * 32);
-            const int4 c0 = ld_stream(cp + (size_t)k * 32);
-            fma_entry<KT>(v0.x, c0.x, xs, acc);
-            fma_entry<KT>(v0.y, c0.y, xs, acc);
-            fma_entry<KT>(v0.z, c0.z, xs, acc);
-            fma_entry<KT>(v0.w, c0.w, xs, acc);
-        }
-    } else if constexpr (F::GE == 8) {  // 16-bit values, 16-bit columns
-        const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + off) + lane;
-        const uint4* cp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + lane;
-        auto group = [&](const uint4& vw, const uint4& cw) {
-            const uint32_t vv[4] = {vw.x, vw.y, vw.z, vw.w};
-            const uint32_t cc[4] = {cw.x, cw.y, cw.z, cw.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float2 f = std::is_same<F, FmtF16>::value ? h2f(vv[h]) : b2f(vv[h]);
-                fma_entry<KT>(f.x, (int)(cc[h] & 0xffffu), xs, acc);
-                fma_entry<KT>(f.y, (int)(cc[h] >> 16), xs, acc);
-            }
-        };
-        int k = g0;
-        for (; k + 2 <= L; k += 2) {
-            const uint4 v0 = ld_stream(vp + (size_t)k * 32);
-            const uint4 c0 = ld_stream(cp + (size_t)k * 32);
-            const uint4 v1 = ld_stream(vp + (size_t)(k + 1) * 32);
-            const uint4 c1 = ld_stream(cp + (size_t)(k + 1) * 32);
-            group(v0, c0);
-            group(v1, c1);
-        }
-        if (k < L) group(ld_stream(vp + (size_t)k * 32), ld_stream(cp + (size_t)k * 32));
-    } else {  // FP8 e4m3 values (16 per 16 bytes), 16-bit columns
-        const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(val) + off) + lane;
-        const uint4* cp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + 2 * lane;
-        for (int k = g0; k < L; ++k) {
-            const uint4 vw = ld_stream(vp + (size_t)k * 32);
-            const uint4 c0 = ld_stream(cp + (size_t)k * 64);
-            const uint4 c1 = ld_stream(cp + (size_t)k * 64 + 1);
-            const uint32_t vv[4] = {vw.x, vw.y, vw.z, vw.w};
-            const uint32_t cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float2 lo = e4m3x2f((uint16_t)(vv[h] & 0xffffu));
-                const float2 hi = e4m3x2f((uint16_t)(vv[h] >> 16));
-                fma_entry<KT>(lo.x, (int)(cc[2 * h] & 0xffffu), xs, acc);
-                fma_entry<KT>(lo.y, (int)(cc[2 * h] >> 16), xs, acc);
-                fma_entry<KT>(hi.x, (int)(cc[2 * h + 1] & 0xffffu), xs, acc);
-                fma_entry<KT>(hi.y, (int)(cc[2 * h + 1] >> 16), xs, acc);
-            }
-        }
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) fma_group<F, KT>(r[h], xs, acc);
     }
 }
 
@@ -296,14 +275,20 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
     __shared__ float shf[32];
     __shared__ int acc_set;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
+    // the cancel flag lives in mapped host memory: its load is issued first and used last
+    int cancel_req = 0;
+    if (tid == 0 && phase == 1) {
+        const volatile int32_t* cf = sp->cancel;
+        if (cf) cancel_req = *cf;
+    }
     cta_copy_in(&S, st);
     cta_copy_in(&P, sp);
     __syncthreads();
     const int KT = phase == 0 ? 1 : P.k_trials;
-    const int W = P.gstride;
+    const int W = P.n_groups;
     // all objective and step-length sums of the launch, fixed order per thread and per warp
     for (int q = 0; q < KT; ++q) {
-        const double* g = P.gpart + (size_t)q * W;
+        const double* g = P.gsum + (size_t)q * W;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int i = tid;
         for (; i + 3 * (int)blockDim.x < W; i += 4 * blockDim.x) {
@@ -420,7 +405,7 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
             if (status == IMRT_ELINESEARCH) S.total_bt += P.max_bt;
             if (status == 0 && stop == 0) {
                 if (P.timeout_ns && global_timer_ns() - S.t_start > P.timeout_ns) status = IMRT_ETIMEOUT;
-                else if (P.cancel && *P.cancel) status = IMRT_ECANCELLED;
+                else if (cancel_req) status = IMRT_ECANCELLED;
             }
             if (status != 0 || stop != 0) finish_loop(S, P, status, stop);
         }
@@ -436,6 +421,41 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
                 P.tr_x[(size_t)k * P.n + i] = __ldcg(v.x + (size_t)acc_set * P.n_pad + i);
         }
     }
+}
+
+// A slice's objective partials (one per trial, fixed shuffle order), then the group of
+// kGroupSlices consecutive slices it belongs to: the warp that completes the group (integer
+// arrival counter) adds the group's partials in slice order, so the controller only adds
+// n_groups values and every sum is independent of the schedule. The counters are cleared by
+// the last CTA of the launch.
+template <int KT>
+__device__ __forceinline__ void publish_objective(const FwdUnits& U, int s, int lane, const double (&Fq)[KT]) {
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const double g = warp_sum(Fq[q]);
+        if (lane == 0) U.gpart[(size_t)q * U.gstride + s] = g;
+    }
+    const int grp = s / kGroupSlices;
+    int old = 0;
+    if (lane == 0) {
+        __threadfence();
+        old = atomicAdd(&U.gcount[grp], 1);
+    }
+    old = __shfl_sync(0xffffffffu, old, 0);
+    const int size = min(kGroupSlices, U.n_slices - grp * kGroupSlices);
+    if (old != size - 1) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        double v = lane < size ? __ldcg(U.gpart + (size_t)q * U.gstride + (size_t)grp * kGroupSlices + lane) : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) U.gsum[(size_t)q * U.n_groups + grp] = v;
+    }
+}
+
+// Clears the group arrival counters (last CTA of a launch, after every group completed).
+__device__ __forceinline__ void clear_group_counters(const FwdUnits& U) {
+    for (int i = threadIdx.x; i < U.n_groups; i += blockDim.x) U.gcount[i] = 0;
 }
 
 // After a unit's dot products: a piece of a split slice publishes its partial row sums and
@@ -488,19 +508,14 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
             }
         }
     }
-    // objective share of this slice (one partial per slice: scheduling-independent)
-#pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        const double g = warp_sum(Fq[q]);
-        if (lane == 0) U.gpart[(size_t)q * U.gstride + s] = g;
-    }
+    publish_objective<KT>(U, s, lane, Fq);
 }
 
 // ---------------------------------------------------------------------------
 // Forward pass (fused step + dose + penalty + objective partials).
 // ---------------------------------------------------------------------------
 template <class F, int KT>
-__global__ void __launch_bounds__(kFwdThreads, KT == 1 ? IMRT_FWD_MINB1 : (KT == 2 ? 2 : 1)) k_forward(const FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_forward(const FwdArgs a) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ Terms T;
@@ -636,6 +651,7 @@ __global__ void __launch_bounds__(kFwdThreads, KT == 1 ? IMRT_FWD_MINB1 : (KT ==
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    clear_group_counters(U);
     if (a.control) control_step(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, gridDim.x);
     if (tid == 0) {
         *U.next_unit = 0;
@@ -973,11 +989,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
                     }
                 }
             }
-#pragma unroll
-            for (int q = 0; q < KT; ++q) {
-                const double g = warp_sum(Fq[q]);
-                if (lane == 0) U.gpart[(size_t)q * U.gstride + mt.s] = g;
-            }
+            publish_objective<KT>(U, mt.s, lane, Fq);
         }
     }
     // count finished CTAs: the last one runs the controller inside a solve
@@ -988,6 +1000,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    clear_group_counters(U);
     if (a.control) control_step(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, gridDim.x);
     if (tid == 0) {
         *U.next_unit = 0;
