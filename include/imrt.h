@@ -101,7 +101,9 @@ typedef struct {
     int32_t profile;        /* 1: time every forward and transposed-product launch with CUDA events */
     int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
     int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy; default 20 */
-    int32_t kernel_variant; /* forward pass: 0 warp streaming (default), 1 bulk-copy (TMA) pipeline */
+    int32_t kernel_variant; /* forward pass: 0 warp streaming with a CTA-local schedule (default; falls back
+                               to 2 when a CTA's tables do not fit in shared memory), 1 bulk-copy (TMA)
+                               pipeline, 2 warp streaming with one device-wide schedule */
     double timeout_ms;      /* 0: none; else the device loop stops with IMRT_ETIMEOUT */
     void* stream;           /* cudaStream_t */
 } imrt_options;
@@ -139,6 +141,8 @@ typedef struct {
     int32_t precision, k_trials;
     double lambda0_rule;       /* 8 / L from the power iteration (computed at plan_create) */
     double x1_scale;           /* s of the x_init = 0 rule */
+    int32_t fwd_schedule;      /* forward work schedule in use: 0 CTA-local, 1 bulk-copy pipeline, 2 global */
+    int32_t fwd_units;         /* forward work units (slices and pieces of heavy slices) */
 } imrt_plan_info;
 
 /* Fills *opt with the defaults listed above. */

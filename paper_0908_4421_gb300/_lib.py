@@ -58,7 +58,8 @@ class imrt_plan_info(ctypes.Structure):
                 ("t_entries", ctypes.c_int64), ("fwd_bytes", ctypes.c_int64), ("bwd_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("fwd_grid", ctypes.c_int32), ("fwd_block", ctypes.c_int32),
                 ("bwd_grid", ctypes.c_int32), ("bwd_block", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("k_trials", ctypes.c_int32), ("lambda0_rule", ctypes.c_double), ("x1_scale", ctypes.c_double)]
+                ("k_trials", ctypes.c_int32), ("lambda0_rule", ctypes.c_double), ("x1_scale", ctypes.c_double),
+                ("fwd_schedule", ctypes.c_int32), ("fwd_units", ctypes.c_int32)]
 
 
 _lib: Optional[ctypes.CDLL] = None

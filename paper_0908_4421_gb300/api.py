@@ -33,7 +33,7 @@ class Options:
     profile: int = 0
     trace: int = 0
     polish_iter: int = 20
-    kernel_variant: int = 0  # forward pass: 0 warp streaming, 1 bulk-copy (TMA) pipeline
+    kernel_variant: int = 0  # forward pass: 0 warp streaming, CTA-local schedule; 1 bulk-copy (TMA); 2 global schedule
     timeout_ms: float = 0.0
     stream: int = 0  # cudaStream_t as an integer; 0 = legacy default stream
 

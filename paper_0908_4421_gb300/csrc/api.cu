@@ -79,6 +79,7 @@ struct SellCopy {
     void* col = nullptr;
     int64_t entries = 0;
     std::vector<int64_t> host_cost;  // per slice, for warp partitions
+    std::vector<int64_t> host_off;   // per slice: first entry (equals slice_off on the device)
 };
 
 // Forward launch shape for one (copy, k_trials): grid, work units and their warp partition.
@@ -276,7 +277,8 @@ imrt_status validate_options(const imrt_options* o) {
     if (o->mode != IMRT_MODE_GRAPH && o->mode != IMRT_MODE_HOST) return set_error("unknown mode"), IMRT_EINVAL;
     if (o->trace < 0 || o->trace > 2) return set_error("trace must be 0, 1 or 2"), IMRT_EINVAL;
     if (o->polish_iter < 0) return set_error("polish_iter must be >= 0"), IMRT_EINVAL;
-    if (o->kernel_variant < 0 || o->kernel_variant > 1) return set_error("kernel_variant must be 0 or 1"), IMRT_EINVAL;
+    if (o->kernel_variant < 0 || o->kernel_variant > 2)
+        return set_error("kernel_variant must be 0, 1 or 2"), IMRT_EINVAL;
     if (!(o->timeout_ms >= 0.0)) return set_error("timeout_ms must be >= 0"), IMRT_EINVAL;
     return IMRT_OK;
 }
@@ -390,22 +392,94 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
         }
     }
     const int n_units = (int)us.size();
-    // longest first for the dynamic schedule (the order does not change any result)
-    std::vector<int32_t> ord(n_units);
-    for (int i = 0; i < n_units; ++i) ord[i] = i;
-    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return ucost[x] > ucost[y]; });
-    auto permute = [&](std::vector<int32_t>& v) {
-        std::vector<int32_t> t(v.size());
-        for (int i = 0; i < n_units; ++i) t[i] = v[ord[i]];
-        v.swap(t);
-    };
-    permute(us), permute(ug0), permute(ug1), permute(usplit), permute(upiece);
+    const int grid = out->grid;
     out->n_splits = (int)spieces.size();
     out->gstride = p->n_slices;
     FwdUnits& U = out->units;
+    U = FwdUnits{};
     U.n_units = n_units;
     U.n_splits = out->n_splits;
     U.gstride = out->gstride;
+    U.n_slices = p->n_slices;
+    std::vector<UnitRec> recs(n_units);
+    std::vector<int32_t> rec_slice(n_units);
+    std::vector<int32_t> cta_unit(grid + 1, 0), cta_slots(grid, 0);
+    auto make_rec = [&](int i, int32_t sid, int32_t slot) {
+        const int32_t gs = usplit[i];
+        return UnitRec{c.host_off[us[i]], us[i], ug0[i], ug1[i], sid, upiece[i], gs >= 0 ? spieces[gs] : 1,
+                       gs >= 0 ? sbase[gs] : 0, slot, {0, 0}};
+    };
+    bool local = variant == 0;
+    if (local) {
+        // CTA-local schedule: whole slices dealt to CTAs, longest first, each to the least-loaded
+        // CTA (ties: the lower index); every CTA's units longest first
+        std::vector<int32_t> sorder(p->n_slices);
+        for (int s = 0; s < p->n_slices; ++s) sorder[s] = s;
+        std::stable_sort(sorder.begin(), sorder.end(),
+                         [&](int x, int y) { return c.host_cost[x] > c.host_cost[y]; });
+        using Load = std::pair<int64_t, int32_t>;
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int b = 0; b < grid; ++b) heap.push(Load{0, b});
+        std::vector<int32_t> cta_of(p->n_slices), slot_of(p->n_slices);
+        for (int s : sorder) {
+            Load l = heap.top();
+            heap.pop();
+            cta_of[s] = l.second;
+            slot_of[s] = cta_slots[l.second]++;
+            heap.push(Load{l.first + c.host_cost[s], l.second});
+        }
+        std::vector<int32_t> uord(n_units);
+        for (int i = 0; i < n_units; ++i) uord[i] = i;
+        std::stable_sort(uord.begin(), uord.end(), [&](int x, int y) {
+            const int cx = cta_of[us[x]], cy = cta_of[us[y]];
+            return cx != cy ? cx < cy : ucost[x] > ucost[y];
+        });
+        std::vector<int32_t> lsid(std::max(out->n_splits, 1), -1), cta_splits(grid, 0);
+        for (int k = 0; k < n_units; ++k) {
+            const int i = uord[k];
+            const int b = cta_of[us[i]];
+            int32_t sid = -1;
+            if (usplit[i] >= 0) {
+                if (lsid[usplit[i]] < 0) lsid[usplit[i]] = cta_splits[b]++;
+                sid = lsid[usplit[i]];
+            }
+            recs[k] = make_rec(i, sid, slot_of[us[i]]);
+            rec_slice[k] = us[i];
+            cta_unit[b + 1] += 1;
+        }
+        for (int b = 0; b < grid; ++b) cta_unit[b + 1] += cta_unit[b];
+        for (int b = 0; b < grid; ++b) {
+            U.max_units = std::max(U.max_units, cta_unit[b + 1] - cta_unit[b]);
+            U.max_slots = std::max(U.max_slots, cta_slots[b]);
+            U.max_splits = std::max(U.max_splits, cta_splits[b]);
+        }
+        // the tables must fit beside the x / g staging area (else: the global schedule)
+        auto tables = [&](int kt) {
+            return (size_t)U.max_units * sizeof(UnitRec) + (size_t)U.max_slots * kt * 8 + (size_t)U.max_splits * 4;
+        };
+        auto align16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        const size_t need = align16(fwd_smem_bytes(p->n_pad, k_trials, c.precision)) + tables(k_trials);
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, out->fn));
+        if (need + fa.sharedSizeBytes + 1024 <= (size_t)max_smem) {
+            out->smem = need;
+            out->smem1 = align16(fwd_smem_bytes(p->n_pad, 1, c.precision)) + tables(1);
+        } else {
+            local = false;
+            U.max_units = U.max_slots = U.max_splits = 0;
+        }
+    }
+    if (!local) {
+        // global schedule: longest first over all units
+        std::vector<int32_t> ord(n_units);
+        for (int i = 0; i < n_units; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return ucost[x] > ucost[y]; });
+        for (int k = 0; k < n_units; ++k) {
+            recs[k] = make_rec(ord[k], usplit[ord[k]], 0);
+            rec_slice[k] = us[ord[k]];
+        }
+    }
+    U.local = local ? 1 : 0;
     auto upload = [&](const std::vector<int32_t>& h, const int32_t** dst) -> imrt_status {
         int32_t* d = nullptr;
         TRY(dalloc(p, &d, std::max<size_t>(h.size(), 1)));
@@ -414,22 +488,31 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
         *dst = d;
         return IMRT_OK;
     };
-    TRY(upload(us, &U.unit_slice));
-    TRY(upload(ug0, &U.unit_g0));
-    TRY(upload(ug1, &U.unit_g1));
-    TRY(upload(usplit, &U.unit_split));
-    TRY(upload(upiece, &U.unit_piece));
-    TRY(upload(spieces, &U.split_pieces));
-    TRY(upload(sbase, &U.split_base));
+    TRY(upload(rec_slice, &U.unit_slice));
+    TRY(upload(cta_unit, &U.cta_unit));
+    TRY(upload(cta_slots, &U.cta_slots));
+    {
+        void* d = nullptr;
+        TRY(dalloc_bytes(p, &d, sizeof(UnitRec) * std::max(n_units, 1)));
+        if (n_units)
+            CK(cudaMemcpyAsync(d, recs.data(), sizeof(UnitRec) * n_units, cudaMemcpyHostToDevice, stream_of(p)));
+        U.unit = static_cast<const UnitRec*>(d);
+    }
     TRY(dalloc(p, &U.partials, (size_t)std::max(parts, 1) * kSlice * k_trials));
     TRY(dalloc(p, &U.counters, std::max(out->n_splits, 1)));
     CK(cudaMemsetAsync(U.counters, 0, sizeof(int32_t) * std::max(out->n_splits, 1), stream_of(p)));
-    TRY(dalloc(p, &U.gpart, (size_t)k_trials * out->gstride));
-    U.n_slices = p->n_slices;
     U.n_groups = (p->n_slices + kGroupSlices - 1) / kGroupSlices;
-    TRY(dalloc(p, &U.gsum, (size_t)k_trials * std::max(U.n_groups, 1)));
-    TRY(dalloc(p, &U.gcount, std::max(U.n_groups, 1)));
-    CK(cudaMemsetAsync(U.gcount, 0, sizeof(int32_t) * std::max(U.n_groups, 1), stream_of(p)));
+    if (local) {
+        TRY(dalloc(p, &U.obj, (size_t)k_trials * grid));
+        U.n_obj = grid;
+    } else {
+        TRY(dalloc(p, &U.gpart, (size_t)k_trials * out->gstride));
+        TRY(dalloc(p, &U.gsum, (size_t)k_trials * std::max(U.n_groups, 1)));
+        TRY(dalloc(p, &U.gcount, std::max(U.n_groups, 1)));
+        CK(cudaMemsetAsync(U.gcount, 0, sizeof(int32_t) * std::max(U.n_groups, 1), stream_of(p)));
+        U.obj = U.gsum;
+        U.n_obj = U.n_groups;
+    }
     TRY(dalloc(p, &U.ticket, 1));
     TRY(dalloc(p, &U.next_unit, 1));
     CK(cudaMemsetAsync(U.ticket, 0, sizeof(int32_t), stream_of(p)));
@@ -515,7 +598,7 @@ imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, f
     a.r_dst = r_dst;
     void* args[] = {&a};
     CK(cudaLaunchKernel(sh->fn1, dim3(sh->grid), dim3(sh->block), args, sh->smem1, stream_of(p)));
-    if (G_out) CK(launch_g_objective(sh->units.gsum, sh->units.n_groups, G_out, stream_of(p)));
+    if (G_out) CK(launch_g_objective(sh->units.obj, sh->units.n_obj, G_out, stream_of(p)));
     return IMRT_OK;
 }
 
@@ -566,7 +649,13 @@ imrt_status build_sell(imrt_plan* p, SellCopy* c, int precision, const int64_t* 
     CK(cudaMemcpyAsync(sl.data(), c->slice_len, sizeof(int32_t) * p->n_slices, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     c->host_cost.resize(p->n_slices);
-    for (int i = 0; i < p->n_slices; ++i) c->host_cost[i] = (int64_t)sl[i] * kSlice * c->ge + 8 * kSlice;
+    c->host_off.resize(p->n_slices);
+    int64_t run = 0;
+    for (int i = 0; i < p->n_slices; ++i) {
+        c->host_cost[i] = (int64_t)sl[i] * kSlice * c->ge + 8 * kSlice;
+        c->host_off[i] = run;
+        run += (int64_t)sl[i] * kSlice * c->ge;
+    }
     TRY(dalloc_bytes(p, &c->val, (size_t)c->entries * elem_bytes(precision) + 64));
     TRY(dalloc_bytes(p, &c->col, (size_t)c->entries * col_bytes(precision) + 64));
     uint8_t* mask_out = precision == IMRT_FP32 ? p->mask : nullptr;
@@ -838,8 +927,8 @@ SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_in
     q.m = p->m;
     q.m_pad = p->m_pad;
     q.fwd_grid = sh.grid;
-    q.n_groups = sh.units.n_groups;
-    q.gsum = sh.units.gsum;
+    q.n_obj = sh.units.n_obj;
+    q.obj = sh.units.obj;
     q.timeout_ns = o.timeout_ms > 0.0 ? (unsigned long long)(o.timeout_ms * 1e6) : 0ull;
     q.tr_G = o.trace >= 1 ? p->tr_G : nullptr;
     q.tr_lam = o.trace >= 1 ? p->tr_lam : nullptr;
@@ -1579,6 +1668,8 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     if (get_shape(p, p->opt.precision, p->opt.k_trials, &sh) == IMRT_OK) {
         info->fwd_grid = sh->grid;
         info->fwd_block = sh->block;
+        info->fwd_schedule = sh->variant == 1 ? 1 : (sh->units.local ? 0 : 2);
+        info->fwd_units = sh->units.n_units;
     }
     info->bwd_grid = p->bwd_grid;
     info->bwd_block = kBwdThreads;

@@ -81,8 +81,8 @@ struct DevState {
 struct SolveParams {
     double eps, alpha, delta, lambda0, x1_scale;
     int32_t max_iter, max_bt, x_init, k_trials, trace, n, n_pad, m, m_pad;
-    int32_t fwd_grid, n_groups;  // forward grid; objective group sums per trial
-    const double* gsum;          // objective group sums of the forward shape in use
+    int32_t fwd_grid, n_obj;     // forward grid; objective partials per trial
+    const double* obj;           // objective partials of the forward shape in use
     unsigned long long timeout_ns;
     double* tr_G;
     double* tr_lam;
@@ -103,28 +103,52 @@ struct Vecs {
     int32_t n_pad, m_pad;
 };
 
-// Forward work units: a whole slice, or one piece (a range of groups) of a
-// heavy slice. Warps take units dynamically, longest first, from an integer
-// counter. Pieces of a split slice write partial row sums; the last piece to
-// finish (integer arrival counter) adds them in piece order and runs the
-// epilogue. Every slice writes its own objective partial, so results do not
-// depend on which warp ran which unit.
+// Forward work units: a whole slice, or one piece (a range of groups) of a heavy
+// slice. Two schedules share the records:
+//  * CTA-local (kernel_variant 0): the host deals whole slices to CTAs (longest
+//    first, to the least-loaded CTA); each CTA copies its records into shared
+//    memory and its warps take them, longest first, from a shared-memory counter.
+//    Pieces of a split slice all belong to one CTA; the last to finish (shared
+//    arrival counter) adds the partial row sums in piece order and runs the
+//    epilogue. Slice objective partials go to shared-memory slots that the CTA
+//    adds in slot order at its end: one objective partial per CTA.
+//  * global (kernel_variant 2, and the fallback when the CTA-local tables do not
+//    fit in shared memory): all warps take units from one device-wide counter;
+//    split pieces meet through device-scope counters, and slice partials are
+//    summed in fixed groups of kGroupSlices slices.
+// Every sum has a fixed order, so results never depend on which warp ran what.
+struct __align__(16) UnitRec {
+    int64_t off;     // first entry of the unit's slice
+    int32_t s;       // slice
+    int32_t g0, g1;  // groups [g0, g1) of the slice
+    int32_t sid;     // split id (CTA-local schedule: within the CTA), or -1 for a whole slice
+    int32_t piece;   // piece index within its split
+    int32_t np;      // pieces of the split
+    int32_t pbase;   // first partial row block of the split
+    int32_t slot;    // CTA-local schedule: the slice's objective slot within its CTA
+    int32_t pad[2];
+};
+static_assert(sizeof(UnitRec) == 48, "unit records are three 16-byte words");
+
 struct FwdUnits {
-    const int32_t* unit_slice;   // n_units, longest first
-    const int32_t* unit_g0;      // first group
-    const int32_t* unit_g1;      // one past the last group
-    const int32_t* unit_split;   // split id, or -1 for a whole slice
-    const int32_t* unit_piece;   // piece index within its split
-    const int32_t* split_pieces; // n_splits
-    const int32_t* split_base;   // n_splits: first partial row block of the split
+    const UnitRec* unit;         // n_units (CTA-local: grouped by CTA, each CTA's longest first)
+    const int32_t* unit_slice;   // n_units: the slice of each unit (bulk-copy variant)
+    const int32_t* cta_unit;     // CTA-local: grid + 1 offsets of each CTA's records
+    const int32_t* cta_slots;    // CTA-local: grid: objective slots of each CTA
+    const int32_t* split_pieces; // global: n_splits
+    const int32_t* split_base;   // global: n_splits: first partial row block of the split
     float* partials;             // (sum of pieces) * 32 * k_trials
-    int32_t* counters;           // n_splits arrival counters, left at 0
-    double* gpart;               // k_trials * gstride objective partials, one per slice
-    double* gsum;                // k_trials * n_groups sums of kGroupSlices consecutive slice partials
-    int32_t* gcount;             // n_groups arrival counters, left at 0
-    int32_t* next_unit;          // dynamic schedule counter, reset by the last CTA
+    int32_t* counters;           // global: n_splits arrival counters, left at 0
+    double* gpart;               // global: k_trials * gstride objective partials, one per slice
+    double* gsum;                // global: k_trials * n_groups sums of kGroupSlices slice partials
+    int32_t* gcount;             // global: n_groups arrival counters, left at 0
+    double* obj;                 // the objective partials the controller adds: k_trials * n_obj
+    int32_t* next_unit;          // global: dynamic schedule counter, reset by the last CTA
     int32_t* ticket;             // CTAs finished in the current launch
     int32_t n_units, n_splits, gstride, n_slices, n_groups;
+    int32_t n_obj;               // objective partials per trial (grid, or n_groups)
+    int32_t local;               // 1: CTA-local schedule
+    int32_t max_units, max_slots, max_splits;  // CTA-local: shared-memory table sizes
 };
 
 struct FwdArgs {

@@ -267,7 +267,9 @@ __device__ __forceinline__ void finish_loop(DevState& S, const SolveParams& P, i
 // Armijo controller (Sec. 2.2 steps 3-5, Eq. (5)); phase 0 follows the initial evaluation.
 // Runs on every thread of one CTA after all partials of the launch are visible. The state and
 // parameters are staged in shared memory so the decision is one short sequential section.
-__device__ void control_step(int phase, DevState* st, const SolveParams* sp, const Vecs& v, int grid) {
+template <int KT>
+__device__ void control_step(int phase, DevState* st, const SolveParams* sp, const Vecs& v, const FwdUnits& U,
+                             int n, int grid) {
     __shared__ DevState S;
     __shared__ SolveParams P;
     __shared__ double red[32][2 * kMaxTrials];
@@ -275,51 +277,63 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
     __shared__ float shf[32];
     __shared__ int acc_set;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
-    // the cancel flag lives in mapped host memory: its load is issued first and used last
+    const int nq = phase == 0 ? 1 : KT;  // step sizes this launch evaluated
+    const int W = U.n_obj;
+    const int B = blockDim.x;
+    // Every load the decision needs is issued before any is used, so the section costs one
+    // round trip: the cancel flag (mapped host memory), this thread's first objective group
+    // sum and step-length partial of each trial, its share of |g| (for ||g(x_1)||_inf), and
+    // its words of the state and parameters.
     int cancel_req = 0;
     if (tid == 0 && phase == 1) {
         const volatile int32_t* cf = sp->cancel;
         if (cf) cancel_req = *cf;
     }
+    double gs[KT], ds[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        gs[q] = (q < nq && tid < W) ? __ldcg(U.obj + (size_t)q * W + tid) : 0.0;
+        ds[q] = (phase == 1 && q < nq && tid < grid) ? __ldcg(v.dpart + (size_t)q * grid + tid) : 0.0;
+    }
+    float ga[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const int i = tid + h * B;
+        ga[h] = (phase == 1 && i < n) ? fabsf(__ldcg(v.g + i)) : 0.0f;
+    }
     cta_copy_in(&S, st);
     cta_copy_in(&P, sp);
-    __syncthreads();
-    const int KT = phase == 0 ? 1 : P.k_trials;
-    const int W = P.n_groups;
-    // all objective and step-length sums of the launch, fixed order per thread and per warp
+    // sizes beyond one element per thread (fixed order per thread)
+#pragma unroll
     for (int q = 0; q < KT; ++q) {
-        const double* g = P.gsum + (size_t)q * W;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int i = tid;
-        for (; i + 3 * (int)blockDim.x < W; i += 4 * blockDim.x) {
-            s0 += __ldcg(g + i);
-            s1 += __ldcg(g + i + blockDim.x);
-            s2 += __ldcg(g + i + 2 * blockDim.x);
-            s3 += __ldcg(g + i + 3 * blockDim.x);
-        }
-        for (; i < W; i += blockDim.x) s0 += __ldcg(g + i);
-        const double t = warp_sum((s0 + s1) + (s2 + s3));
-        if (lane == 0) red[wib][q] = t;
-        if (phase == 1) {
-            double d = 0.0;
-            for (int k = tid; k < grid; k += blockDim.x) d += __ldcg(v.dpart + (size_t)q * grid + k);
-            d = warp_sum(d);
-            if (lane == 0) red[wib][kMaxTrials + q] = d;
-        }
+        if (q >= nq) continue;
+        for (int i = tid + B; i < W; i += B) gs[q] += __ldcg(U.obj + (size_t)q * W + i);
+        if (phase == 1)
+            for (int k = tid + B; k < grid; k += B) ds[q] += __ldcg(v.dpart + (size_t)q * grid + k);
     }
     float ginf = 0.0f;
-    const bool want_g1 = phase == 1 && !S.g1_done;
-    if (want_g1) {
-        for (int i = tid; i < P.n; i += blockDim.x) ginf = fmaxf(ginf, fabsf(__ldcg(v.g + i)));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ginf = fmaxf(ginf, __shfl_xor_sync(0xffffffffu, ginf, o));
-        if (lane == 0) shf[wib] = ginf;
+    for (int h = 0; h < 8; ++h) ginf = fmaxf(ginf, ga[h]);
+    if (phase == 1)
+        for (int i = tid + 8 * B; i < n; i += B) ginf = fmaxf(ginf, fabsf(__ldcg(v.g + i)));
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const double t = warp_sum(gs[q]);
+        const double d = warp_sum(ds[q]);
+        if (lane == 0) {
+            red[wib][q] = t;
+            red[wib][kMaxTrials + q] = d;
+        }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ginf = fmaxf(ginf, __shfl_xor_sync(0xffffffffu, ginf, o));
+    if (lane == 0) shf[wib] = ginf;
     __syncthreads();
+    const bool want_g1 = phase == 1 && !S.g1_done;
     if (tid < 2 * kMaxTrials) {
         const int q = tid % kMaxTrials;
         double t = 0.0;
-        if (q < KT && (tid < kMaxTrials || phase == 1))
+        if (q < nq && (tid < kMaxTrials || phase == 1))
             for (int k = 0; k < nw; ++k) t += red[k][tid];
         sums[tid] = t;
     }
@@ -353,7 +367,7 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
             double lam = S.lambda;
             const int bt = S.bt;
             int status = S.status, stop = 0, accepted = -1;
-            for (int q = 0; q < KT && status == 0; ++q) {
+            for (int q = 0; q < nq && status == 0; ++q) {
                 if (bt + q > P.max_bt) {
                     status = IMRT_ELINESEARCH;
                     break;
@@ -395,10 +409,10 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
                 else if (rel < P.delta) stop = IMRT_STOP_REL;  // step 5
                 else if (S.iter >= P.max_iter) stop = IMRT_STOP_MAXITER;
             } else if (status == 0 && stop == 0) {
-                if (bt + KT - 1 >= P.max_bt) {
+                if (bt + nq - 1 >= P.max_bt) {
                     status = IMRT_ELINESEARCH;
                 } else {
-                    S.bt = bt + KT;
+                    S.bt = bt + nq;
                     S.lambda = lam;
                 }
             }
@@ -458,34 +472,49 @@ __device__ __forceinline__ void clear_group_counters(const FwdUnits& U) {
     for (int i = threadIdx.x; i < U.n_groups; i += blockDim.x) U.gcount[i] = 0;
 }
 
+// Where a unit's epilogue meets the other pieces of its slice and leaves the slice's
+// objective partials: the CTA-local schedule uses shared-memory counters and slots,
+// the global one device-scope counters and group sums.
+struct LocalTables {
+    int* cnt;       // shared: split arrival counters of this CTA
+    double* slots;  // shared: objective slots of this CTA (max_slots * k_trials)
+};
+
 // After a unit's dot products: a piece of a split slice publishes its partial row sums and
 // the last piece to arrive adds them in piece order; then, for complete rows, the penalty
-// epilogue writes z and r and the slice's objective partial.
-template <int KT>
+// epilogue writes z and r and the slice's objective partials.
+template <int KT, bool LOCAL>
 __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, int mode, float* const (&zq)[KT],
-                                              float* const (&rq)[KT], int s, int sid, int piece, int lane,
-                                              float (&acc)[KT]) {
+                                              float* const (&rq)[KT], const UnitRec& R, int lane,
+                                              const LocalTables& lt, float (&acc)[KT]) {
     const FwdUnits& U = a.u;
-    if (sid >= 0) {
-        float* part = U.partials + ((size_t)(U.split_base[sid] + piece) * kSlice + lane) * KT;
+    const int s = R.s;
+    if (R.sid >= 0) {
+        float* part = U.partials + ((size_t)(R.pbase + R.piece) * kSlice + lane) * KT;
 #pragma unroll
         for (int q = 0; q < KT; ++q) part[q] = acc[q];
-        __threadfence();
-        __syncwarp();
         int old = 0;
-        if (lane == 0) old = atomicAdd(&U.counters[sid], 1);
+        if constexpr (LOCAL) {
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) old = atomicAdd_block(&lt.cnt[R.sid], 1);
+        } else {
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) old = atomicAdd(&U.counters[R.sid], 1);
+        }
         old = __shfl_sync(0xffffffffu, old, 0);
-        const int P = U.split_pieces[sid];
-        if (old != P - 1) return;
-        __threadfence();
-        const float* base = U.partials + (size_t)U.split_base[sid] * kSlice * KT;
+        if (old != R.np - 1) return;
+        if constexpr (LOCAL) __threadfence_block();
+        else __threadfence();
+        const float* base = U.partials + (size_t)R.pbase * kSlice * KT;
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-        for (int k = 0; k < P; ++k) {
+        for (int k = 0; k < R.np; ++k) {
 #pragma unroll
             for (int q = 0; q < KT; ++q) acc[q] += __ldcg(base + ((size_t)k * kSlice + lane) * KT + q);
         }
-        if (lane == 0) U.counters[sid] = 0;
+        if (!LOCAL && lane == 0) U.counters[R.sid] = 0;
     }
     const int p = s * kSlice + lane;
     double Fq[KT];
@@ -508,7 +537,32 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
             }
         }
     }
-    publish_objective<KT>(U, s, lane, Fq);
+    if constexpr (LOCAL) {
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const double g = warp_sum(Fq[q]);
+            if (lane == 0) lt.slots[(size_t)R.slot * KT + q] = g;
+        }
+    } else {
+        publish_objective<KT>(U, s, lane, Fq);
+    }
+}
+
+// Loads one unit record (three 16-byte words) from shared or global memory.
+__device__ __forceinline__ UnitRec load_unit(const UnitRec* r, bool shared) {
+    UnitRec R;
+    const uint4* src = reinterpret_cast<const uint4*>(r);
+    uint4* dst = reinterpret_cast<uint4*>(&R);
+    if (shared) {
+        dst[0] = src[0];
+        dst[1] = src[1];
+        dst[2] = src[2];
+    } else {
+        dst[0] = __ldg(src);
+        dst[1] = __ldg(src + 1);
+        dst[2] = __ldg(src + 2);
+    }
+    return R;
 }
 
 // ---------------------------------------------------------------------------
@@ -517,47 +571,85 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
 template <class F, int KT>
 __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_forward(const FwdArgs a) {
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, bar_g, bar_r;
     __shared__ Terms T;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int n_pad = a.n_pad;
     DevState* st = a.st;
     const int mode = a.mode;
 
+    float* xs = smem;                  // n_pad * KT, trial-interleaved
+    float* gs = smem + (size_t)n_pad * KT;  // g (trial mode)
+    float* xr = gs + n_pad;            // raw x (trial mode, KT > 1)
+    const uint32_t bytes = (uint32_t)n_pad * 4u;
+
+    const FwdUnits& U = a.u;
+    // CTA-local schedule: this CTA's unit records, objective slots and split counters sit in
+    // shared memory after the x / g staging area
+    unsigned char* tab = reinterpret_cast<unsigned char*>(smem) +
+                         (((size_t)n_pad * 4u * (size_t)(KT + (KT > 1 ? 2 : 1)) + 15) & ~(size_t)15);
+    UnitRec* recs = reinterpret_cast<UnitRec*>(tab);
+    LocalTables lt;
+    lt.slots = reinterpret_cast<double*>(tab + (size_t)U.max_units * sizeof(UnitRec));
+    lt.cnt = reinterpret_cast<int*>(lt.slots + (size_t)U.max_slots * KT);
+    __shared__ int s_next, s_units, s_slots;
+
+    // g and the unit records do not depend on the solver state, so their copies start
+    // before the state is read
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init(&bar_g, 1);
+        mbar_init(&bar_r, 1);
+        fence_mbar_init();
+        if (mode == kFwdTrial) {
+            mbar_arrive_expect_tx(&bar_g, bytes);
+            bulk_g2s(gs, a.v.g, bytes, &bar_g);
+        }
+        s_next = 0;
+        if (U.local) {
+            const int c0 = U.cta_unit[blockIdx.x], c1 = U.cta_unit[blockIdx.x + 1];
+            s_units = c1 - c0;
+            s_slots = U.cta_slots[blockIdx.x];
+            const uint32_t rb = (uint32_t)(c1 - c0) * (uint32_t)sizeof(UnitRec);
+            mbar_arrive_expect_tx(&bar_r, rb);
+            if (rb) bulk_g2s(recs, U.unit + c0, rb, &bar_r);
+        } else {
+            s_units = 0;
+            s_slots = 0;
+            mbar_arrive_expect_tx(&bar_r, 0u);
+        }
+    }
+    if (U.local)
+        for (int i = tid; i < U.max_splits; i += kFwdThreads) lt.cnt[i] = 0;
     int cur = 0;
     double lam = 0.0, alpha = 2.0;
+    bool done = false;
     if (mode == kFwdTrial) {
-        if (st->done) return;
+        done = st->done != 0;
         cur = st->cur;
         lam = st->lambda;
         alpha = a.sp->alpha;
     }
-    const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)(mode == kFwdTrial ? cur : st->cur) * n_pad;
-
-    float* xs = smem;                  // n_pad * KT, trial-interleaved
-    float* gs = smem + (size_t)n_pad * KT;  // g (trial mode)
-    float* xr = gs + n_pad;            // raw x (trial mode, KT > 1)
-
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
     if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
-    __syncthreads();
-    const uint32_t bytes = (uint32_t)n_pad * 4u;
-    if (tid == 0) {
-        if (mode == kFwdTrial) {
-            mbar_arrive_expect_tx(&bar, 2u * bytes);
-            bulk_g2s(KT == 1 ? xs : xr, xsrc, bytes, &bar);
-            bulk_g2s(gs, a.v.g, bytes, &bar);
-        } else {
-            mbar_arrive_expect_tx(&bar, bytes);
-            bulk_g2s(xs, xsrc, bytes, &bar);
+    if (done) {  // the solve has ended (uniform over the grid): leave once the copies have landed
+        if (tid == 0) {
+            (void)mbar_wait_bounded(&bar_g, 0);
+            (void)mbar_wait_bounded(&bar_r, 0);
         }
+        return;
     }
-    // A bounded wait: on expiry the CTA flags a device error, skips its work, and still
+    const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)(mode == kFwdTrial ? cur : st->cur) * n_pad;
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, bytes);
+        bulk_g2s(mode == kFwdTrial && KT > 1 ? xr : xs, xsrc, bytes, &bar);
+    }
+    // Bounded waits: on expiry the CTA flags a device error, skips its work, and still
     // reports to the ticket so the controller runs and ends the solve.
-    const bool failed = __syncthreads_or(!mbar_wait_bounded(&bar, 0)) != 0;
+    bool bad = !mbar_wait_bounded(&bar, 0);
+    if (mode == kFwdTrial) bad = !mbar_wait_bounded(&bar_g, 0) || bad;
+    bad = !mbar_wait_bounded(&bar_r, 0) || bad;
+    const bool failed = __syncthreads_or(bad) != 0;
     if (failed && tid == 0) atomicExch(&st->status, (int)IMRT_ECUDA);
 
     float lamf[KT];
@@ -609,8 +701,7 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
         }
     }
 
-    // Rows: work units taken dynamically (longest first) from the schedule counter.
-    const FwdUnits& U = a.u;
+    // Rows: work units taken dynamically, longest first.
     float* zq[KT];
     float* rq[KT];
 #pragma unroll
@@ -624,24 +715,52 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
             rq[q] = a.r_dst ? a.r_dst : a.v.r + (size_t)st->cur * a.m_pad;
         }
     }
-    int u = U.n_units;
-    if (!failed) {
-        if (lane == 0) u = atomicAdd(U.next_unit, 1);
-        u = __shfl_sync(0xffffffffu, u, 0);
-    }
-    while (u < U.n_units) {
-        int u_next = 0;
-        if (lane == 0) u_next = atomicAdd(U.next_unit, 1);  // latency overlaps this unit
-        const int s = U.unit_slice[u];
-        const int sid = U.unit_split[u];
-        const int piece = U.unit_piece[u];
-        const int64_t off = a.slice_off[s];
-        float acc[KT];
+    if (U.local) {
+        // this CTA's units from the shared-memory counter
+        const int n_loc = s_units;
+        int u = n_loc;
+        if (!failed) {
+            if (lane == 0) u = atomicAdd_block(&s_next, 1);
+            u = __shfl_sync(0xffffffffu, u, 0);
+        }
+        while (u < n_loc) {
+            int u_next = 0;
+            if (lane == 0) u_next = atomicAdd_block(&s_next, 1);
+            const UnitRec R = load_unit(recs + u, true);
+            float acc[KT];
 #pragma unroll
-        for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-        slice_row_dot<F, KT>(a.val, a.col, off, U.unit_g0[u], U.unit_g1[u], lane, xs, acc);
-        unit_epilogue<KT>(a, T, mode, zq, rq, s, sid, piece, lane, acc);
-        u = __shfl_sync(0xffffffffu, u_next, 0);
+            for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+            slice_row_dot<F, KT>(a.val, a.col, R.off, R.g0, R.g1, lane, xs, acc);
+            unit_epilogue<KT, true>(a, T, mode, zq, rq, R, lane, lt, acc);
+            u = __shfl_sync(0xffffffffu, u_next, 0);
+        }
+        __syncthreads();
+        // the CTA's objective partial of each trial: its slots added in slot order
+        if (wib < KT) {
+            const int q = wib;
+            double t = 0.0;
+            for (int i = lane; i < s_slots; i += 32) t += lt.slots[(size_t)i * KT + q];
+            t = warp_sum(t);
+            if (lane == 0) U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : t;
+        }
+    } else {
+        // all units from the device-wide counter
+        int u = U.n_units;
+        if (!failed) {
+            if (lane == 0) u = atomicAdd(U.next_unit, 1);
+            u = __shfl_sync(0xffffffffu, u, 0);
+        }
+        while (u < U.n_units) {
+            int u_next = 0;
+            if (lane == 0) u_next = atomicAdd(U.next_unit, 1);  // latency overlaps this unit
+            const UnitRec R = load_unit(U.unit + u, false);
+            float acc[KT];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+            slice_row_dot<F, KT>(a.val, a.col, R.off, R.g0, R.g1, lane, xs, acc);
+            unit_epilogue<KT, false>(a, T, mode, zq, rq, R, lane, lt, acc);
+            u = __shfl_sync(0xffffffffu, u_next, 0);
+        }
     }
     // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
     __shared__ int is_last;
@@ -651,8 +770,8 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    clear_group_counters(U);
-    if (a.control) control_step(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, gridDim.x);
+    if (!U.local) clear_group_counters(U);
+    if (a.control) control_step<KT>(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, U, a.n, gridDim.x);
     if (tid == 0) {
         *U.next_unit = 0;
         *U.ticket = 0;
@@ -1001,7 +1120,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
     if (!is_last) return;
     __threadfence();
     clear_group_counters(U);
-    if (a.control) control_step(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, gridDim.x);
+    if (a.control) control_step<KT>(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, U, a.n, gridDim.x);
     if (tid == 0) {
         *U.next_unit = 0;
         *U.ticket = 0;

@@ -30,7 +30,7 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_full_size_eval(big, variant):
     case = big
     orc = oracle.get()
@@ -41,6 +41,7 @@ def test_full_size_eval(big, variant):
         info = plan.info()
     G_ref, z_ref, _, g_ref = orc.eval(case, x1.astype(np.float64), threads=threads)
     assert info["nnz"] == case.nnz and case.nnz > 50_000_000
+    assert info["fwd_schedule"] == variant  # the CTA-local tables fit at this size
     assert rel(z, z_ref) <= 1e-5
     assert abs(G - G_ref) <= 1e-5 * G_ref
     assert rel(g, g_ref) <= 1e-4
@@ -48,7 +49,7 @@ def test_full_size_eval(big, variant):
     assert np.all(np.abs(z - z_ref) <= 1e-5 * np.abs(z_ref) + 1e-6 * np.abs(z_ref).max())
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("k_trials", [1, 2])
 def test_full_size_iterations(big, k_trials, variant):
     case = big
@@ -66,3 +67,16 @@ def test_full_size_iterations(big, k_trials, variant):
         assert rel(orc.dose(case, xs[k].astype(np.float64), threads=threads),
                    orc.dose(case, ref.xs[k], threads=threads)) <= 1e-5
         assert abs(G[k] - ref.G[k]) <= 1e-5 * ref.G[k]
+
+
+def test_full_size_schedules_agree(big):
+    """The CTA-local and the device-wide schedules cut the same pieces: identical doses; the
+    objective differs only in the order its partials are added."""
+    case = big
+    x1 = oracle.get().initial_point(case).astype(np.float32)
+    out = {}
+    for variant in (0, 2):
+        with Plan.from_case(case, Options(kernel_variant=variant), device=True) as plan:
+            out[variant] = plan.eval(x1)
+    np.testing.assert_array_equal(out[0][1], out[2][1])
+    assert abs(out[0][0] - out[2][0]) <= 1e-12 * abs(out[2][0])

@@ -52,7 +52,7 @@ def orc():
     return oracle.get()
 
 
-VARIANTS = [0, 1]  # forward kernel: warp streaming, bulk-copy (TMA) pipeline
+VARIANTS = [0, 1, 2]  # forward kernel: CTA-local warp streaming, bulk-copy (TMA) pipeline, global warp streaming
 
 
 @pytest.mark.parametrize("variant", VARIANTS)

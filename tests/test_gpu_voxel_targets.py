@@ -25,7 +25,7 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("normalise", [False, True])
 def test_eval_random_with_voxel_targets(orc, variant, normalise):
     rng = np.random.Generator(np.random.PCG64(5))
