@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_0908_4421_gb300 import phantom  # noqa: E402
+from paper_0908_4421_gb300 import autotune, phantom  # noqa: E402
 
 DEFAULT_WORKLOAD = "prostate-192x160x96-2.5mm-9beam-2.5mm-beamlets"
 METRIC = "time-to-plan"
@@ -232,26 +232,17 @@ def main():
     info = plan.info()
     lam0 = info["lambda0_rule"]
 
-    # k_trials: evaluated step sizes per pass over D (identical results, fewer passes)
-    # tuning: forward kernel variant and k_trials (identical results; only speed differs)
+    # forward kernel variant and k_trials by the project autotuner (identical Armijo
+    # decisions for every candidate; only speed differs)
     kts = [args.k_trials] if args.k_trials else [1, 2]
-    variants = [args.variant] if args.variant >= 0 else [0, 1]
-    candidates = [(v, kt) for v in variants for kt in kts]
-    best_kt, best_variant, best_t = kts[0], variants[0], float("inf")
+    variants = [args.variant] if args.variant >= 0 else [0, 1, 2]
     tuned = {}
-    if len(candidates) > 1:
-        for v, kt in candidates:
-            plan.set_options(k_trials=kt, kernel_variant=v)
-            plan.solve()
-            ts = []
-            for _ in range(3):
-                t0 = time.perf_counter()
-                plan.solve()
-                ts.append(time.perf_counter() - t0)
-            tuned[f"v{v}k{kt}"] = statistics.median(ts)
-            if tuned[f"v{v}k{kt}"] < best_t:
-                best_kt, best_variant, best_t = kt, v, tuned[f"v{v}k{kt}"]
-    plan.set_options(k_trials=best_kt, kernel_variant=best_variant)
+    if len(kts) * len(variants) > 1:
+        tr = autotune.tune(plan, variants=variants, k_trials=kts, repeats=3, warmup=1)
+        best_kt, best_variant, tuned = tr.k_trials, tr.kernel_variant, tr.table
+    else:
+        best_kt, best_variant = kts[0], variants[0]
+        plan.set_options(k_trials=best_kt, kernel_variant=best_variant)
     info = plan.info()
 
     for _ in range(args.warmup):

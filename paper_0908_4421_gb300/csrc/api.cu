@@ -845,7 +845,7 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     if (s_star >= 0) {
         CK(launch_fill(p->x_stage, 1.0f, n, s));
         TRY(run_eval(p, kFwdEval, p->x_stage, p->z_stage, p->r_stage, nullptr));
-        CK(launch_sum_masked(p->z_stage, p->mask, s_star, p->m, p->dscratch, s));
+        CK(launch_sum_masked(p->z_stage, p->mask, s_star, p->m, p->dscratch, p->dscratch + 8, s));
         double sum = 0.0;
         CK(cudaMemcpyAsync(&sum, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -872,7 +872,7 @@ imrt_status alloc_vectors(imrt_plan* p) {
     TRY(dalloc(p, &p->z_stage, p->m_pad));
     TRY(dalloc(p, &p->r_stage, p->m_pad));
     TRY(dalloc(p, &p->zout_stage, std::max(p->m, 1)));
-    TRY(dalloc(p, &p->dscratch, 8));
+    TRY(dalloc(p, &p->dscratch, 8 + kSumParts));  // scalars, then the masked-sum partials
     TRY(dalloc(p, &p->terms_dev, 1));
     TRY(dalloc(p, &p->st, 1));
     TRY(dalloc(p, &p->sp, 1));
@@ -1417,7 +1417,7 @@ imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_
     if (p->s_star < 0 && nt > 0) {
         CK(launch_fill(p->x_stage, 1.0f, p->n, s));
         TRY(run_eval(p, kFwdEval, p->x_stage, p->z_stage, p->r_stage, nullptr));
-        CK(launch_sum_masked(p->z_stage, p->vtm_p, 0, p->m, p->dscratch, s));
+        CK(launch_sum_masked(p->z_stage, p->vtm_p, 0, p->m, p->dscratch, p->dscratch + 8, s));
         double sz = 0.0;
         CK(cudaMemcpyAsync(&sz, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));

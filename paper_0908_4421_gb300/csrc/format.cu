@@ -345,25 +345,34 @@ __global__ void k_fill(float* dst, float v, int32_t count) {
     if (i < count) dst[i] = v;
 }
 
+// Block-wide FP64 sum (fixed order: warp trees, then the warp totals in order). The warp
+// totals are added by one thread: FP64 arithmetic is scarce on this GPU, so no work is
+// replicated across the block.
 __device__ double block_sum_d(double v) {
     __shared__ double sh[32];
+    __shared__ double total;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+        total = t;
+    }
     __syncthreads();
-    return t;
+    return total;
 }
 
-__global__ void __launch_bounds__(1024) k_sum_masked(const float* __restrict__ z, const uint8_t* __restrict__ mask,
-                                                     int32_t bit, int32_t m, double* out) {
+// Masked sum of z over one structure: per-CTA partials over a fixed grid-stride partition,
+// then k_sum_doubles adds them in order.
+__global__ void __launch_bounds__(256) k_sum_masked_part(const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                                                         int32_t bit, int32_t m, double* __restrict__ part) {
     double s = 0.0;
-    for (int p = threadIdx.x; p < m; p += blockDim.x)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m; p += gridDim.x * blockDim.x)
         if ((mask[p] >> bit) & 1u) s += (double)z[p];
     s = block_sum_d(s);
-    if (threadIdx.x == 0) *out = s;
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // Power-iteration update: lambda = v . w, v = w / ||w||.
@@ -560,8 +569,9 @@ cudaError_t launch_fill(float* dst, float v, int32_t count, cudaStream_t stream)
 }
 
 cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, int32_t m, double* out,
-                              cudaStream_t stream) {
-    k_sum_masked<<<1, 1024, 0, stream>>>(z, mask, bit, m, out);
+                              double* scratch, cudaStream_t stream) {
+    k_sum_masked_part<<<kSumParts, 256, 0, stream>>>(z, mask, bit, m, scratch);
+    k_sum_doubles<<<1, 256, 0, stream>>>(scratch, kSumParts, out);
     return cudaGetLastError();
 }
 

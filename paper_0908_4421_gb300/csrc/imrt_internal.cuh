@@ -234,8 +234,9 @@ cudaError_t launch_mask_counts(const uint8_t* mask, int32_t m, int32_t* counts, 
 cudaError_t launch_unpermute(const float* zp, const int32_t* perm, int32_t m, float* z, cudaStream_t stream);
 cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* dst, cudaStream_t stream);
 cudaError_t launch_fill(float* dst, float v, int32_t count, cudaStream_t stream);
+constexpr int kSumParts = 256;  // CTAs (and partials) of the masked sum
 cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, int32_t m, double* out,
-                              cudaStream_t stream);
+                              double* scratch, cudaStream_t stream);
 cudaError_t launch_permute_in(const float* src, const uint8_t* src_mask, const int32_t* perm, int32_t m,
                               int32_t m_pad, float* dst, uint8_t* dst_mask, cudaStream_t stream);
 cudaError_t launch_power_update(float* v, const float* w, int32_t n, double* lam, cudaStream_t stream);

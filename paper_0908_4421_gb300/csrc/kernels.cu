@@ -316,10 +316,15 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
     for (int h = 0; h < 8; ++h) ginf = fmaxf(ginf, ga[h]);
     if (phase == 1)
         for (int i = tid + 8 * B; i < n; i += B) ginf = fmaxf(ginf, fabsf(__ldcg(v.g + i)));
+    // FP64 is scarce: only warps holding partials reduce them
+    const bool has_g = wib * 32 < W, has_d = phase == 1 && wib * 32 < grid;
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
-        const double t = warp_sum(gs[q]);
-        const double d = warp_sum(ds[q]);
+        double t = 0.0, d = 0.0;
+        if (q < nq) {
+            if (has_g) t = warp_sum(gs[q]);
+            if (has_d) d = warp_sum(ds[q]);
+        }
         if (lane == 0) {
             red[wib][q] = t;
             red[wib][kMaxTrials + q] = d;
