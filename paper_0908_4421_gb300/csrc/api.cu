@@ -558,6 +558,7 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.n_pad = p->n_pad;
     a.m_pad = p->m_pad;
     a.mode = mode;
+    a.cancel = p->cancel_dev;
     return a;
 }
 
@@ -602,10 +603,13 @@ imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, f
     return IMRT_OK;
 }
 
-imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision = IMRT_FP32) {
+imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision = IMRT_FP32,
+                          float* power_v = nullptr, double* power_lam = nullptr) {
     BwdArgs a = bwd_args(p, precision, 0);
     a.r_fixed = r;
     a.g = g;
+    a.pw_v = power_v;
+    a.pw_lam = power_lam;
     void* args[] = {&a};
     CK(cudaLaunchKernel(bwd_fixed_kernel(precision), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0, stream_of(p)));
     return IMRT_OK;
@@ -675,8 +679,7 @@ imrt_status ensure_lambda0_rule(imrt_plan* p) {
     CK(launch_fill(p->x_stage, (float)(1.0 / std::sqrt((double)p->n)), p->n, s));
     for (int it = 0; it < 50; ++it) {
         TRY(run_eval(p, kFwdPower, p->x_stage, p->z_stage, p->r_stage, nullptr));
-        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage));
-        CK(launch_power_update(p->x_stage, p->g_stage, p->n, p->dscratch, s));
+        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage, IMRT_FP32, p->x_stage, p->dscratch));
     }
     double lam = 0.0;
     CK(cudaMemcpyAsync(&lam, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));

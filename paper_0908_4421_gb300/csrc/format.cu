@@ -375,23 +375,6 @@ __global__ void __launch_bounds__(256) k_sum_masked_part(const float* __restrict
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// Power-iteration update: lambda = v . w, v = w / ||w||.
-__global__ void __launch_bounds__(1024) k_power_update(float* __restrict__ v, const float* __restrict__ w, int32_t n,
-                                                       double* lam) {
-    double vw = 0.0, ww = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        vw += (double)v[i] * (double)w[i];
-        ww += (double)w[i] * (double)w[i];
-    }
-    vw = block_sum_d(vw);
-    ww = block_sum_d(ww);
-    if (threadIdx.x == 0) *lam = vw;
-    if (ww > 0.0) {
-        const float inv = (float)(1.0 / sqrt(ww));
-        for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
-    }
-}
-
 __global__ void k_col_absmax(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                              const float* __restrict__ val, int32_t m, uint32_t* __restrict__ absmax_bits) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -572,11 +555,6 @@ cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, 
                               double* scratch, cudaStream_t stream) {
     k_sum_masked_part<<<kSumParts, 256, 0, stream>>>(z, mask, bit, m, scratch);
     k_sum_doubles<<<1, 256, 0, stream>>>(scratch, kSumParts, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_power_update(float* v, const float* w, int32_t n, double* lam, cudaStream_t stream) {
-    k_power_update<<<1, 1024, 0, stream>>>(v, w, n, lam);
     return cudaGetLastError();
 }
 

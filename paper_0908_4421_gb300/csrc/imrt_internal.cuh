@@ -169,6 +169,7 @@ struct FwdArgs {
     int32_t mode;        // FwdMode
     int32_t control;     // 1: the last CTA runs the Armijo controller (inside a solve)
     int32_t stages;      // bulk-copy kernel: ring stages per consumer warp
+    const volatile int32_t* cancel;  // mapped host flag: nonzero asks the solve to stop
     const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x
     float* z_dst;        // kFwdEval / kFwdPower; NULL => accepted set
     float* r_dst;
@@ -190,6 +191,8 @@ struct BwdArgs {
     DevState* st;
     const float* r_fixed;     // NULL => r of the accepted set
     float* g;
+    float* pw_v;              // step-size rule: power vector updated by the last CTA, or NULL
+    double* pw_lam;           // its Rayleigh quotient v . (D^T C D v)
     int32_t m_pad, guard;     // guard: skip unless st->need_grad
 };
 
@@ -239,7 +242,6 @@ cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, 
                               double* scratch, cudaStream_t stream);
 cudaError_t launch_permute_in(const float* src, const uint8_t* src_mask, const int32_t* perm, int32_t m,
                               int32_t m_pad, float* dst, uint8_t* dst_mask, cudaStream_t stream);
-cudaError_t launch_power_update(float* v, const float* w, int32_t n, double* lam, cudaStream_t stream);
 cudaError_t launch_col_absmax(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m,
                               int32_t n, uint32_t* absmax_bits, cudaStream_t stream);
 cudaError_t launch_scales(const uint32_t* absmax_bits, int32_t n, int32_t n_pad, float qmax, float* scale,

@@ -267,11 +267,20 @@ __device__ __forceinline__ void finish_loop(DevState& S, const SolveParams& P, i
 // Armijo controller (Sec. 2.2 steps 3-5, Eq. (5)); phase 0 follows the initial evaluation.
 // Runs on every thread of one CTA after all partials of the launch are visible. The state and
 // parameters are staged in shared memory so the decision is one short sequential section.
+// The state and parameters a forward launch's controller reads: every CTA stages them in
+// shared memory during its prologue (they do not change during the launch, except the
+// status word a failing CTA may set), so the controller's single round trip after the
+// ticket is the one for the launch's partial sums.
+struct CtlStage {
+    DevState S;
+    SolveParams P;
+};
+
 template <int KT>
-__device__ void control_step(int phase, DevState* st, const SolveParams* sp, const Vecs& v, const FwdUnits& U,
-                             int n, int grid) {
-    __shared__ DevState S;
-    __shared__ SolveParams P;
+__device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUnits& U, int n, int grid,
+                             CtlStage& cs, int cancel_req) {
+    DevState& S = cs.S;
+    const SolveParams& P = cs.P;
     __shared__ double red[32][2 * kMaxTrials];
     __shared__ double sums[2 * kMaxTrials];
     __shared__ float shf[32];
@@ -281,14 +290,10 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
     const int W = U.n_obj;
     const int B = blockDim.x;
     // Every load the decision needs is issued before any is used, so the section costs one
-    // round trip: the cancel flag (mapped host memory), this thread's first objective group
-    // sum and step-length partial of each trial, its share of |g| (for ||g(x_1)||_inf), and
-    // its words of the state and parameters.
-    int cancel_req = 0;
-    if (tid == 0 && phase == 1) {
-        const volatile int32_t* cf = sp->cancel;
-        if (cf) cancel_req = *cf;
-    }
+    // round trip: the status word, this thread's first objective partial and step-length
+    // partial of each trial, and its share of |g| (for ||g(x_1)||_inf).
+    int status_now = 0;
+    if (tid == 0) status_now = __ldcg(&st->status);
     double gs[KT], ds[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
@@ -301,8 +306,7 @@ __device__ void control_step(int phase, DevState* st, const SolveParams* sp, con
         const int i = tid + h * B;
         ga[h] = (phase == 1 && i < n) ? fabsf(__ldcg(v.g + i)) : 0.0f;
     }
-    cta_copy_in(&S, st);
-    cta_copy_in(&P, sp);
+    if (tid == 0) S.status = status_now;
     // sizes beyond one element per thread (fixed order per thread)
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
@@ -636,6 +640,15 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
         alpha = a.sp->alpha;
     }
     if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
+    // the controller's inputs (used only by the last CTA; the mapped cancel flag's latency
+    // is hidden behind the whole pass)
+    __shared__ CtlStage cs;
+    int cancel_req = 0;
+    if (a.control) {
+        cta_copy_in(&cs.S, st);
+        cta_copy_in(&cs.P, a.sp);
+        if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
+    }
     if (done) {  // the solve has ended (uniform over the grid): leave once the copies have landed
         if (tid == 0) {
             (void)mbar_wait_bounded(&bar_g, 0);
@@ -776,7 +789,7 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
     if (!is_last) return;
     __threadfence();
     if (!U.local) clear_group_counters(U);
-    if (a.control) control_step<KT>(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, U, a.n, gridDim.x);
+    if (a.control) control_step<KT>(mode == kFwdTrial ? 1 : 0, st, a.v, U, a.n, gridDim.x, cs, cancel_req);
     if (tid == 0) {
         *U.next_unit = 0;
         *U.ticket = 0;
@@ -889,6 +902,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
         fence_mbar_init();
     }
     if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
+    __shared__ CtlStage cs;
+    int cancel_req = 0;
+    if (a.control) {
+        cta_copy_in(&cs.S, st);
+        cta_copy_in(&cs.P, a.sp);
+        if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
+    }
     __syncthreads();
     const uint32_t bytes = (uint32_t)n_pad * 4u;
     if (tid == 0) {
@@ -1125,7 +1145,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
     if (!is_last) return;
     __threadfence();
     clear_group_counters(U);
-    if (a.control) control_step<KT>(mode == kFwdTrial ? 1 : 0, st, a.sp, a.v, U, a.n, gridDim.x);
+    if (a.control) control_step<KT>(mode == kFwdTrial ? 1 : 0, st, a.v, U, a.n, gridDim.x, cs, cancel_req);
     if (tid == 0) {
         *U.next_unit = 0;
         *U.ticket = 0;
@@ -1197,7 +1217,10 @@ __device__ __forceinline__ bool transposed_rows(const BwdArgs& a, const float* _
         idx = next_idx[buf];
     }
     __syncthreads();
-    if (tid == 0) is_last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
+    if (tid == 0) {
+        __threadfence();  // this CTA's g entries (written by this thread) before its ticket
+        is_last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
+    }
     __syncthreads();
     if (is_last && tid == 0) {
         *a.next_row = 0;
@@ -1291,7 +1314,10 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
         idx = nidx;
     }
     __syncthreads();
-    if (tid == 0) is_last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
+    if (tid == 0) {
+        __threadfence();  // this CTA's g entries (written by this thread) before its ticket
+        is_last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
+    }
     __syncthreads();
     if (is_last && tid == 0) {
         *a.next_row = 0;
@@ -1315,10 +1341,45 @@ __global__ void __launch_bounds__(kBwdThreads) k_transposed_cur(const BwdArgs a,
     if (a.guard && last && threadIdx.x == 0) st->grad_passes += 1;
 }
 
-// Outside the solve: r given explicitly.
+// One power-iteration step of the step-size rule on w = g (the last CTA, after every row):
+// lambda = v . w, then v = w / ||w|| (FP64 sums in a fixed order).
+__device__ void power_update(const BwdArgs& a) {
+    __shared__ double red[2][kBwdThreads / 32];
+    __shared__ double tot[2];
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    __threadfence();
+    double vw = 0.0, ww = 0.0;
+    for (int i = tid; i < a.n; i += blockDim.x) {
+        const double w = (double)__ldcg(a.g + i);
+        vw += (double)a.pw_v[i] * w;
+        ww += w * w;
+    }
+    vw = warp_sum(vw);
+    ww = warp_sum(ww);
+    if (lane == 0) {
+        red[0][wib] = vw;
+        red[1][wib] = ww;
+    }
+    __syncthreads();
+    if (tid < 2) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[tid][k];
+        tot[tid] = t;
+    }
+    __syncthreads();
+    if (tid == 0) *a.pw_lam = tot[0];
+    if (tot[1] > 0.0) {
+        const float inv = (float)(1.0 / sqrt(tot[1]));
+        for (int i = tid; i < a.n; i += blockDim.x) a.pw_v[i] = __ldcg(a.g + i) * inv;
+    }
+}
+
+// Outside the solve: r given explicitly (and, in the step-size rule, the power-iteration
+// update by the last CTA).
 template <int PREC>
-__global__ void __launch_bounds__(kBwdThreads) k_transposed(const BwdArgs a) {
-    transposed_any<PREC>(a, a.r_fixed);
+__global__ void __launch_bounds__(kBwdThreads, 4) k_transposed(const BwdArgs a) {
+    const bool last = transposed_any<PREC>(a, a.r_fixed);
+    if (last && a.pw_v) power_update(a);
 }
 
 // x_1 (Initialization of Sec. 2.2) and the solver state.
