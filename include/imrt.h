@@ -100,7 +100,9 @@ typedef struct {
     int32_t mode;           /* imrt_mode; default IMRT_MODE_GRAPH */
     int32_t profile;        /* 1: time every forward and transposed-product launch with CUDA events */
     int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
-    int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy; default 20 */
+    int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy
+                               (more when the reduced phase stops early: the polish gets the rest of
+                               max_iter); default 20 */
     int32_t kernel_variant; /* forward pass: 0 warp streaming with a CTA-local schedule (default; falls back
                                to 2 when a CTA's tables do not fit in shared memory), 1 bulk-copy (TMA)
                                pipeline, 2 warp streaming with one device-wide schedule */

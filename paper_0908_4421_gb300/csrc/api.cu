@@ -919,6 +919,8 @@ SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_in
     q.alpha = o.alpha;
     q.delta = o.delta;
     q.lambda0 = o.lambda0 > 0.0 ? o.lambda0 : p->lambda0_rule;
+    q.eps_over_lambda0 = q.eps / q.lambda0;
+    q.inv_alpha = 1.0 / q.alpha;
     q.x1_scale = p->x1_scale;
     q.max_iter = max_iter;
     q.max_bt = o.max_backtracks;
@@ -1028,8 +1030,26 @@ imrt_status launch_now(Launch& l, cudaStream_t s) {
     return IMRT_OK;
 }
 
-imrt_status add_node(Launch& l, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* out) {
+// programmatic: the node may start launching once every CTA of `dep` has called
+// pdl_launch_dependents (the kernels wait for `dep`'s completion before reading its results).
+imrt_status add_node(Launch& l, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* out, bool programmatic = false) {
     ArgPack a = pack_args(l, offsets_for(l));
+    if (programmatic && dep) {
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeKernel;
+        np.kernel.func = const_cast<void*>(l.fn);
+        np.kernel.gridDim = l.grid;
+        np.kernel.blockDim = l.block;
+        np.kernel.sharedMemBytes = (unsigned)l.smem;
+        np.kernel.kernelParams = a.ptrs.data();
+        np.kernel.extra = nullptr;
+        cudaGraphEdgeData ed{};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.to_port = 0;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        CK(cudaGraphAddNode(out, g, dep, &ed, 1, &np));
+        return IMRT_OK;
+    }
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void*>(l.fn);
     kp.gridDim = l.grid;
@@ -1046,6 +1066,13 @@ imrt_status add_node(Launch& l, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNo
 // Adds one plan's solve as a branch of `graph`:
 //   init -> eval -> while (cond) { bwd -> trial } -> bwd -> finish
 // (the controller runs in the last CTA of eval and trial and clears `cond`).
+#ifndef IMRT_WHILE_UNROLL
+#define IMRT_WHILE_UNROLL 8
+#endif
+#ifndef IMRT_PDL
+#define IMRT_PDL 1  // 1: programmatic edges between the kernel nodes of the loop body
+#endif
+
 imrt_status add_solve_branch(cudaGraph_t graph, PhaseKernels& K, cudaGraphConditionalHandle* cond) {
     CK(cudaGraphConditionalHandleCreate(cond, graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNode_t n_init, n_eval, n_loop, n_bwd_final, n_finish;
@@ -1057,10 +1084,18 @@ imrt_status add_solve_branch(cudaGraph_t graph, PhaseKernels& K, cudaGraphCondit
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     CK(cudaGraphAddNode(&n_loop, graph, &n_eval, nullptr, 1, &cp));
+    // The loop body holds IMRT_WHILE_UNROLL iterations (transposed pass, trial pass): each
+    // relaunch of the body costs the device scheduler a few microseconds. Passes after the
+    // controller has ended the solve return at once (the trial pass sees `done`, the
+    // transposed pass finds g current).
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t b_bwd, b_trial;
-    TRY(add_node(K.bwd, body, nullptr, &b_bwd));
-    TRY(add_node(K.trial, body, &b_bwd, &b_trial));
+    cudaGraphNode_t prev = nullptr;
+    for (int u = 0; u < IMRT_WHILE_UNROLL; ++u) {
+        cudaGraphNode_t b_bwd, b_trial;
+        TRY(add_node(K.bwd, body, u ? &prev : nullptr, &b_bwd, IMRT_PDL != 0));
+        TRY(add_node(K.trial, body, &b_bwd, &b_trial, IMRT_PDL != 0));
+        prev = b_trial;
+    }
     TRY(add_node(K.bwd, graph, &n_loop, &n_bwd_final));
     TRY(add_node(K.finish, graph, &n_bwd_final, &n_finish));
     return IMRT_OK;
@@ -1098,7 +1133,8 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
         CK(cudaGraphLaunch(sg->exec, s));
         CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        launches = 2 + 2 * (p->st_host->passes - 1) + 2;
+        const int trials = p->st_host->passes - 1;  // loop bodies hold IMRT_WHILE_UNROLL iterations
+        launches = 2 + 2 * IMRT_WHILE_UNROLL * ((trials + IMRT_WHILE_UNROLL - 1) / IMRT_WHILE_UNROLL) + 2;
     } else {
         TRY(launch_now(K.init, s));
         TRY(launch_now(K.eval, s));
@@ -1229,7 +1265,7 @@ imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vec
     CK(cudaStreamSynchronize(s));
     for (size_t i = 0; i < n; ++i) {
         const DevState& d = *plans[i]->st_host;
-        res[i].launches += 2 + 2 * (d.passes - 1) + 2;
+        res[i].launches += 2 + 2 * IMRT_WHILE_UNROLL * ((d.passes - 1 + IMRT_WHILE_UNROLL - 1) / IMRT_WHILE_UNROLL) + 2;
         res[i].passes += d.passes;
         res[i].grad_passes += d.grad_passes;
         plans[i]->cur = d.cur;
@@ -1461,7 +1497,10 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
                            cudaMemcpyDeviceToDevice, s));
         const int trace_saved = p->opt.trace;
         p->opt.trace = 0;
-        imrt_status ps = run_phase(p, IMRT_FP32, std::min(o.polish_iter, o.max_iter), 2, p->g_stage, res);
+        // the polish gets the iterations the reduced phase left (at least polish_iter): a
+        // reduced phase that stalls early hands the rest of the budget to the FP32 copy
+        const int budget = std::max(std::min(o.polish_iter, o.max_iter), o.max_iter - d.iter);
+        imrt_status ps = run_phase(p, IMRT_FP32, budget, 2, p->g_stage, res);
         p->opt.trace = trace_saved;
         TRY(ps);
         d = *p->st_host;
@@ -1541,7 +1580,7 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
             pp.push_back(p);
             pidx.push_back(i);
             pprec.push_back(IMRT_FP32);
-            piters.push_back(std::min(p->opt.polish_iter, p->opt.max_iter));
+            piters.push_back(std::max(std::min(p->opt.polish_iter, p->opt.max_iter), p->opt.max_iter - d.iter));
             pxinit.push_back(2);
             px0.push_back(p->g_stage);
         }

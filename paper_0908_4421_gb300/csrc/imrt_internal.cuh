@@ -57,7 +57,9 @@ struct Terms {
 struct DevState {
     double G;        // objective at the accepted x
     double lambda;   // first step size of the next trial batch
-    double rel;      // last relative change
+    double rel;      // last relative change (set by k_finish from dG and G)
+    double dG;       // |G_new - G_old| of the last accepted step
+    double eol;      // eps / lambda for the first step size of the next trial batch
     double g1_inf;   // ||g(x_1)||_inf
     double kkt;
     double G0;       // G(x_1)
@@ -80,6 +82,7 @@ struct DevState {
 // Solve parameters, device-resident, written by the host before each solve.
 struct SolveParams {
     double eps, alpha, delta, lambda0, x1_scale;
+    double eps_over_lambda0, inv_alpha;  // host-computed: the controller multiplies
     int32_t max_iter, max_bt, x_init, k_trials, trace, n, n_pad, m, m_pad;
     int32_t fwd_grid, n_obj;     // forward grid; objective partials per trial
     const double* obj;           // objective partials of the forward shape in use

@@ -195,13 +195,43 @@ __device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __res
 }
 
 // One row (one lane) of a slice: acc[q] += the row's entries in groups [g0, g1), in storage
-// order. Rounds of IMRT_FWD_UNROLL groups: all of a round's 128-bit loads are issued before
-// any is used, so each lane keeps UNROLL x (value + column) bytes in flight; the last round
-// is guarded per group (the guard is uniform across the warp).
+// order. Default: two register stages of IMRT_FWD_UNROLL / 2 groups; the 128-bit loads of the
+// next stage are issued before the current stage is used, so loads stay in flight while the
+// lane gathers x and accumulates. Otherwise: rounds of IMRT_FWD_UNROLL groups, all loads of
+// a round before any use. The last groups are guarded (the guard is uniform across the warp).
+#ifndef IMRT_FWD_PIPE
+#define IMRT_FWD_PIPE 1  // 1: software-pipelined rounds (the next round's loads before this round's use)
+#endif
 template <class F, int KT>
 __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, const void* __restrict__ col,
                                               int64_t off, int g0, int g1, int lane, const float* __restrict__ xs,
                                               float (&acc)[KT]) {
+#if IMRT_FWD_PIPE
+    // two register stages of U groups: while one stage is consumed the other is in flight
+    constexpr int U = (F::GE == 16 || KT >= 4) ? 2 : IMRT_FWD_UNROLL / 2;
+    GroupRegs a[U], b[U];
+    auto load = [&](GroupRegs(&r)[U], int k) {
+#pragma unroll
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) load_group<F>(val, col, off, k + h, lane, r[h]);
+    };
+    auto use = [&](const GroupRegs(&r)[U], int k) {
+#pragma unroll
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) fma_group<F, KT>(r[h], xs, acc);
+    };
+    int k = g0;
+    if (k < g1) load(a, k);
+    while (k < g1) {
+        if (k + U < g1) load(b, k + U);
+        use(a, k);
+        k += U;
+        if (k >= g1) break;
+        if (k + U < g1) load(a, k + U);
+        use(b, k);
+        k += U;
+    }
+#else
     // FP8 groups are 48 bytes and four or more trials need their accumulators: half the rounds
     constexpr int U = ((F::GE == 16 || KT >= 4) && IMRT_FWD_UNROLL > 4) ? IMRT_FWD_UNROLL / 2 : IMRT_FWD_UNROLL;
     for (int k = g0; k < g1; k += U) {
@@ -213,6 +243,7 @@ __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, cons
         for (int h = 0; h < U; ++h)
             if (k + h < g1) fma_group<F, KT>(r[h], xs, acc);
     }
+#endif
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -374,6 +405,7 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
             }
             const double G = S.G;
             double lam = S.lambda;
+            double eol = S.eol;  // eps / lam, kept by multiplication (no FP64 division here)
             const int bt = S.bt;
             int status = S.status, stop = 0, accepted = -1;
             for (int q = 0; q < nq && status == 0; ++q) {
@@ -390,16 +422,17 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
                     status = IMRT_ENUMERIC;
                     break;
                 }
-                if (Gt < G - (P.eps / lam) * d2) {  // Eq. (5), strict
+                if (Gt < G - eol * d2) {  // Eq. (5), strict
                     accepted = q;
                     break;
                 }
-                lam = lam / P.alpha;  // step 4
+                lam = lam * P.inv_alpha;  // step 4
+                eol = eol * P.alpha;
             }
             if (accepted >= 0) {
                 const double Gt = sums[accepted];
                 const int set = (S.cur + 1 + accepted) % kSets;
-                const double rel = Gt > 0.0 ? fabs(Gt - G) / Gt : 0.0;
+                const double dG = fabs(Gt - G);
                 const int k = S.iter;
                 if (P.tr_lam) P.tr_lam[k] = lam;
                 if (P.tr_bt) P.tr_bt[k] = bt + accepted;
@@ -407,15 +440,16 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
                 S.total_bt += bt + accepted;
                 S.cur = set;
                 S.G = Gt;
-                S.rel = rel;
+                S.dG = dG;
                 S.iter = k + 1;
                 S.lambda_acc = lam;
                 S.lambda = P.lambda0;  // step 2 of the next iteration
+                S.eol = P.eps_over_lambda0;
                 S.bt = 0;
                 S.need_grad = 1;
                 acc_set = set;
                 if (Gt == 0.0) stop = IMRT_STOP_EXACT;
-                else if (rel < P.delta) stop = IMRT_STOP_REL;  // step 5
+                else if (dG < P.delta * Gt) stop = IMRT_STOP_REL;  // step 5: |dG| / G < delta
                 else if (S.iter >= P.max_iter) stop = IMRT_STOP_MAXITER;
             } else if (status == 0 && stop == 0) {
                 if (bt + nq - 1 >= P.max_bt) {
@@ -423,6 +457,7 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
                 } else {
                     S.bt = bt + nq;
                     S.lambda = lam;
+                    S.eol = eol;
                 }
             }
             if (status == IMRT_ELINESEARCH) S.total_bt += P.max_bt;
@@ -472,7 +507,10 @@ __device__ __forceinline__ void publish_objective(const FwdUnits& U, int s, int 
     for (int q = 0; q < KT; ++q) {
         double v = lane < size ? __ldcg(U.gpart + (size_t)q * U.gstride + (size_t)grp * kGroupSlices + lane) : 0.0;
         v = warp_sum(v);
-        if (lane == 0) U.gsum[(size_t)q * U.n_groups + grp] = v;
+        if (lane == 0) {
+            U.gsum[(size_t)q * U.n_groups + grp] = v;
+            __threadfence();
+        }
     }
 }
 
@@ -603,17 +641,14 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
     lt.cnt = reinterpret_cast<int*>(lt.slots + (size_t)U.max_slots * KT);
     __shared__ int s_next, s_units, s_slots;
 
-    // g and the unit records do not depend on the solver state, so their copies start
-    // before the state is read
+    // The unit records are constant, so their copy starts first. Under a programmatic launch
+    // this prologue overlaps the transposed pass before it: everything up to pdl_wait reads
+    // only what the previous forward pass (complete by then) or the plan wrote; g comes after.
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_init(&bar_g, 1);
         mbar_init(&bar_r, 1);
         fence_mbar_init();
-        if (mode == kFwdTrial) {
-            mbar_arrive_expect_tx(&bar_g, bytes);
-            bulk_g2s(gs, a.v.g, bytes, &bar_g);
-        }
         s_next = 0;
         if (U.local) {
             const int c0 = U.cta_unit[blockIdx.x], c1 = U.cta_unit[blockIdx.x + 1];
@@ -640,20 +675,10 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
         alpha = a.sp->alpha;
     }
     if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
-    // the controller's inputs (used only by the last CTA; the mapped cancel flag's latency
-    // is hidden behind the whole pass)
     __shared__ CtlStage cs;
     int cancel_req = 0;
-    if (a.control) {
-        cta_copy_in(&cs.S, st);
-        cta_copy_in(&cs.P, a.sp);
-        if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
-    }
-    if (done) {  // the solve has ended (uniform over the grid): leave once the copies have landed
-        if (tid == 0) {
-            (void)mbar_wait_bounded(&bar_g, 0);
-            (void)mbar_wait_bounded(&bar_r, 0);
-        }
+    if (done) {  // the solve has ended (uniform over the grid): leave once the copy has landed
+        if (tid == 0) (void)mbar_wait_bounded(&bar_r, 0);
         return;
     }
     const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)(mode == kFwdTrial ? cur : st->cur) * n_pad;
@@ -661,6 +686,19 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, bytes);
         bulk_g2s(mode == kFwdTrial && KT > 1 ? xr : xs, xsrc, bytes, &bar);
+    }
+    pdl_wait();  // the transposed pass before this one (g, state) is complete
+    if (tid == 0 && mode == kFwdTrial) {
+        mbar_arrive_expect_tx(&bar_g, bytes);
+        bulk_g2s(gs, a.v.g, bytes, &bar_g);
+    }
+    pdl_launch_dependents();
+    // the controller's inputs, staged while the copies are in flight (used only by the last
+    // CTA; the mapped cancel flag's latency is hidden behind the whole pass)
+    if (a.control) {
+        cta_copy_in(&cs.S, st);
+        cta_copy_in(&cs.P, a.sp);
+        if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
     }
     // Bounded waits: on expiry the CTA flags a device error, skips its work, and still
     // reports to the ticket so the controller runs and ends the solve.
@@ -712,10 +750,14 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
                 d2[q] += e * e;
             }
         }
+        __threadfence();  // x_t is read by the controller's trace copy in this launch
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
             const double s = warp_sum(d2[q]);
-            if (lane == 0) a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = s;
+            if (lane == 0) {
+                a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = s;
+                __threadfence();
+            }
         }
     }
 
@@ -759,7 +801,10 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
             double t = 0.0;
             for (int i = lane; i < s_slots; i += 32) t += lt.slots[(size_t)i * KT + q];
             t = warp_sum(t);
-            if (lane == 0) U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : t;
+            if (lane == 0) {
+                U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : t;
+                __threadfence();
+            }
         }
     } else {
         // all units from the device-wide counter
@@ -781,8 +826,8 @@ __global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_f
         }
     }
     // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
+    // (every write the controller reads was fenced by its writer)
     __shared__ int is_last;
-    __threadfence();
     __syncthreads();
     if (tid == 0) is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
     __syncthreads();
@@ -878,6 +923,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
     const int n_pad = a.n_pad;
     DevState* st = a.st;
     const int mode = a.mode;
+    pdl_wait();  // the transposed pass before this one (g, state) is complete
+    pdl_launch_dependents();
 
     int cur = 0;
     double lam = 0.0, alpha = 2.0;
@@ -904,17 +951,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
     if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
     __shared__ CtlStage cs;
     int cancel_req = 0;
-    if (a.control) {
-        cta_copy_in(&cs.S, st);
-        cta_copy_in(&cs.P, a.sp);
-        if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
-    }
     __syncthreads();
     const uint32_t bytes = (uint32_t)n_pad * 4u;
     if (tid == 0) {
         mbar_arrive_expect_tx(&xbar, mode == kFwdTrial ? 2u * bytes : bytes);
         bulk_g2s(xstage, xsrc, bytes, &xbar);
         if (mode == kFwdTrial) bulk_g2s(gstage, a.v.g, bytes, &xbar);
+    }
+    if (a.control) {  // the controller's inputs, staged while the copies are in flight
+        cta_copy_in(&cs.S, st);
+        cta_copy_in(&cs.P, a.sp);
+        if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
     }
     const bool failed = __syncthreads_or(!mbar_wait_bounded(&xbar, 0)) != 0;
     float lamf[KT];
@@ -958,10 +1005,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
                 d2[q] += e * e;
             }
         }
+        __threadfence();  // x_t is read by the controller's trace copy in this launch
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
             const double sum = warp_sum(d2[q]);
-            if (lane == 0) a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = sum;
+            if (lane == 0) {
+                a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = sum;
+                __threadfence();
+            }
         }
     }
 
@@ -1137,8 +1188,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
         }
     }
     // count finished CTAs: the last one runs the controller inside a solve
+    // (every write the controller reads was fenced by its writer)
     __shared__ int is_last;
-    __threadfence();
     __syncthreads();
     if (tid == 0) is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
     __syncthreads();
@@ -1335,10 +1386,15 @@ __device__ __forceinline__ bool transposed_any(const BwdArgs& a, const float* __
 // Inside the solve: r of the accepted set, skipped when g is already current.
 template <int PREC>
 __global__ void __launch_bounds__(kBwdThreads) k_transposed_cur(const BwdArgs a, const float* __restrict__ r_sets) {
+    pdl_wait();  // the preceding forward pass (state, r) is complete
+    pdl_launch_dependents();
     DevState* st = a.st;
     if (a.guard && !st->need_grad) return;
     const bool last = transposed_any<PREC>(a, r_sets + (size_t)st->cur * a.m_pad);
-    if (a.guard && last && threadIdx.x == 0) st->grad_passes += 1;
+    if (a.guard && last && threadIdx.x == 0) {
+        st->grad_passes += 1;
+        st->need_grad = 0;  // g is current: a later pass in the same loop body skips
+    }
 }
 
 // One power-iteration step of the step-size rule on w = g (the last CTA, after every row):
@@ -1404,6 +1460,8 @@ __global__ void __launch_bounds__(kCtlThreads) k_init(DevState* st, const SolveP
         st->G = 0.0;
         st->lambda = sp->lambda0;
         st->rel = 0.0;
+        st->dG = 0.0;
+        st->eol = sp->eps_over_lambda0;
         st->g1_inf = 0.0;
         st->kkt = 0.0;
         st->G0 = 0.0;
@@ -1446,6 +1504,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_finish(DevState* st, const Solv
         }
         const double g1 = st->g1_inf > 1.0 ? st->g1_inf : 1.0;
         st->kkt = (double)t / g1;
+        st->rel = st->G > 0.0 ? st->dG / st->G : 0.0;  // relative change of the last accepted step
     }
 }
 

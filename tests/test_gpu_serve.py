@@ -63,3 +63,26 @@ def test_warm_start_keeps_patient_state(requests):
         ref = p.solve(x0=r1.x)
         np.testing.assert_array_equal(p.get_x(), r2.x)
     assert ref.objective == r2.objective
+
+
+@pytest.mark.parametrize("prec", [L.FP16, L.BF16])
+def test_served_mixed_precision_within_1e3_of_oracle(requests, prec):
+    """The serving form (reduced-precision D, FP32 polish, concurrent workers) against the FP64
+    oracle on the same requests and step size: relative objective error <= 1e-3."""
+    import oracle
+    from paper_0908_4421_gb300.serve import ReplanServer, poisson_stream
+    orc = oracle.get()
+    cases = requests[:3]
+    lam = []
+    for c in cases:
+        with Plan.from_case(c, Options()) as p:
+            lam.append(p.info()["lambda0_rule"])
+    srv = ReplanServer(workers=3, options=Options(precision=prec))
+    futs = poisson_stream(srv, cases, rate_hz=100.0, seed=5)
+    concurrent.futures.wait(futs)
+    srv.close()
+    for c, l0, f in zip(cases, lam, futs):
+        r = f.result()
+        ref = orc.solve(c, lambda0=l0, max_iter=200, trace=False)
+        assert r.status == 0
+        assert abs(r.objective - ref.objective) <= 1e-3 * ref.objective, (r.objective, ref.objective)
