@@ -619,7 +619,7 @@ imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision 
 imrt_status make_bwd_schedule(imrt_plan* p, const std::vector<int64_t>& len) {
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel(IMRT_FP32), kBwdThreads, 0));
-    per_sm = std::max(1, std::min(per_sm, 4));
+    per_sm = std::max(1, std::min(per_sm, kBwdPerSm));
     const int grid = (int)std::min<int64_t>((int64_t)p->sm_count * per_sm, std::max<int64_t>(1, p->n));
     std::vector<int32_t> order(p->n);
     for (int i = 0; i < p->n; ++i) order[i] = i;

@@ -26,7 +26,11 @@ constexpr int kMaxTrials = 8;     // Armijo step sizes per forward pass
 constexpr int kGroupSlices = 32;  // slices per objective group sum
 constexpr int kSets = kMaxTrials + 1;  // x/z/r buffer sets: accepted + trials
 constexpr int kFwdThreads = 512;
-constexpr int kBwdThreads = 512;
+#ifndef IMRT_BWD_THREADS
+#define IMRT_BWD_THREADS 256
+#endif
+constexpr int kBwdThreads = IMRT_BWD_THREADS;   // transposed-pass CTA size
+constexpr int kBwdPerSm = 2048 / kBwdThreads;   // resident transposed CTAs per SM (64 warps)
 constexpr int kCtlThreads = 256;
 constexpr int kTmaMaxConsumers = 8;   // bulk-copy forward kernel: 1 producer + up to 8 consumer warps
 constexpr int kTmaThreads = 32 * (1 + kTmaMaxConsumers);

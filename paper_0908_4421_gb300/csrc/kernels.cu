@@ -1283,32 +1283,6 @@ __device__ __forceinline__ bool transposed_rows(const BwdArgs& a, const float* _
 // Reduced-precision rows: groups of 8 entries, 16-bit voxel offsets inside segments of 65536
 // voxels; the row's segment boundaries are staged in shared memory.
 template <int PREC>
-__device__ __forceinline__ void load_q8(const void* val, int64_t e, float (&v)[8]) {
-    if constexpr (PREC == IMRT_FP8E4M3) {
-        const uint2 w = ld_stream_u2(reinterpret_cast<const uint2*>(static_cast<const uint8_t*>(val) + e));
-        const uint32_t ww[2] = {w.x, w.y};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float2 lo = e4m3x2f((uint16_t)(ww[h] & 0xffffu));
-            const float2 hi = e4m3x2f((uint16_t)(ww[h] >> 16));
-            v[4 * h + 0] = lo.x;
-            v[4 * h + 1] = lo.y;
-            v[4 * h + 2] = hi.x;
-            v[4 * h + 3] = hi.y;
-        }
-    } else {
-        const uint4 w = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + e));
-        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float2 f = PREC == IMRT_FP16 ? h2f(ww[h]) : b2f(ww[h]);
-            v[2 * h] = f.x;
-            v[2 * h + 1] = f.y;
-        }
-    }
-}
-
-template <int PREC>
 __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float* __restrict__ r) {
     __shared__ float red[kBwdThreads / 32];
     __shared__ int next_idx[2];
@@ -1329,15 +1303,49 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
         const int64_t r0 = b[0];
         const int G = (int)((b[H] - r0) >> 3);
         float acc0 = 0.0f, acc1 = 0.0f;
-        auto group = [&](int k, float& acc) {
+        // raw 16-byte words of a group and its voxel segment; values are converted at use, so
+        // both groups' loads are in flight before the first gather
+        struct Raw {
+            uint4 v, lw;
+            int h;
+        };
+        auto load = [&](int k, Raw& q) {
             const int64_t e = r0 + 8 * (int64_t)k;
             int h = 0;
             while (h + 1 < H && e >= b[h + 1]) ++h;
-            const float* rb = r + ((size_t)h << 16);
+            q.h = h;
+            if constexpr (PREC == IMRT_FP8E4M3) {
+                const uint2 w = ld_stream_u2(reinterpret_cast<const uint2*>(static_cast<const uint8_t*>(a.val) + e));
+                q.v = make_uint4(w.x, w.y, 0u, 0u);
+            } else {
+                q.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(a.val) + e));
+            }
+            q.lw = ld_stream(reinterpret_cast<const uint4*>(a.lo + e));
+        };
+        auto use = [&](const Raw& q, float& acc) {
+            const float* rb = r + ((size_t)q.h << 16);
             float v[8];
-            load_q8<PREC>(a.val, e, v);
-            const uint4 lw = ld_stream(reinterpret_cast<const uint4*>(a.lo + e));
-            const uint32_t l4[4] = {lw.x, lw.y, lw.z, lw.w};
+            if constexpr (PREC == IMRT_FP8E4M3) {
+                const uint32_t ww[2] = {q.v.x, q.v.y};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 lo = e4m3x2f((uint16_t)(ww[h] & 0xffffu));
+                    const float2 hi = e4m3x2f((uint16_t)(ww[h] >> 16));
+                    v[4 * h + 0] = lo.x;
+                    v[4 * h + 1] = lo.y;
+                    v[4 * h + 2] = hi.x;
+                    v[4 * h + 3] = hi.y;
+                }
+            } else {
+                const uint32_t ww[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float2 f = PREC == IMRT_FP16 ? h2f(ww[h]) : b2f(ww[h]);
+                    v[2 * h] = f.x;
+                    v[2 * h + 1] = f.y;
+                }
+            }
+            const uint32_t l4[4] = {q.lw.x, q.lw.y, q.lw.z, q.lw.w};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 acc = fmaf(v[2 * t], __ldg(rb + (l4[t] & 0xffffu)), acc);
@@ -1346,10 +1354,17 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
         };
         int k = tid;
         for (; k + kBwdThreads < G; k += 2 * kBwdThreads) {
-            group(k, acc0);
-            group(k + kBwdThreads, acc1);
+            Raw q0, q1;
+            load(k, q0);
+            load(k + kBwdThreads, q1);
+            use(q0, acc0);
+            use(q1, acc1);
         }
-        if (k < G) group(k, acc0);
+        if (k < G) {
+            Raw q0;
+            load(k, q0);
+            use(q0, acc0);
+        }
         const float acc = warp_sum(acc0 + acc1);
         if (lane == 0) red[wib] = acc;
         __syncthreads();  // next_idx[buf ^ 1] is visible after this barrier
@@ -1385,7 +1400,7 @@ __device__ __forceinline__ bool transposed_any(const BwdArgs& a, const float* __
 
 // Inside the solve: r of the accepted set, skipped when g is already current.
 template <int PREC>
-__global__ void __launch_bounds__(kBwdThreads) k_transposed_cur(const BwdArgs a, const float* __restrict__ r_sets) {
+__global__ void __launch_bounds__(kBwdThreads, kBwdPerSm) k_transposed_cur(const BwdArgs a, const float* __restrict__ r_sets) {
     pdl_wait();  // the preceding forward pass (state, r) is complete
     pdl_launch_dependents();
     DevState* st = a.st;
@@ -1433,7 +1448,7 @@ __device__ void power_update(const BwdArgs& a) {
 // Outside the solve: r given explicitly (and, in the step-size rule, the power-iteration
 // update by the last CTA).
 template <int PREC>
-__global__ void __launch_bounds__(kBwdThreads, 4) k_transposed(const BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, kBwdPerSm) k_transposed(const BwdArgs a) {
     const bool last = transposed_any<PREC>(a, a.r_fixed);
     if (last && a.pw_v) power_update(a);
 }
