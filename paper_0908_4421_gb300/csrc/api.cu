@@ -67,11 +67,11 @@ bool is_device_ptr(const void* p) {
 }
 
 size_t elem_bytes(int precision) { return precision == IMRT_FP32 ? 4 : precision == IMRT_FP8E4M3 ? 1 : 2; }
-size_t col_bytes(int precision) { return precision == IMRT_FP32 ? 4 : 2; }
 
 // One voxel-major SELL copy of D at a given storage precision.
 struct SellCopy {
     int precision = -1;
+    int fmt = -1;  // format id: the precision, or kFmtF32C16 (FP32 values, 16-bit beamlet indices)
     int ge = 4;
     int64_t* slice_off = nullptr;  // n_slices + 1
     int32_t* slice_len = nullptr;  // n_slices
@@ -295,12 +295,12 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
     CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     out->variant = variant;
     if (variant == 1) {
-        out->fn = fwd_tma_kernel(c.precision, k_trials);
-        out->fn1 = fwd_tma_kernel(c.precision, 1);
+        out->fn = fwd_tma_kernel(c.fmt, k_trials);
+        out->fn1 = fwd_tma_kernel(c.fmt, 1);
         if (!out->fn) return set_error("no forward kernel for k_trials %d", k_trials), IMRT_EINVAL;
         cudaFuncAttributes fa;
         CK(cudaFuncGetAttributes(&fa, out->fn));
-        const size_t sb = (size_t)fwd_tma_stage_bytes(c.precision);
+        const size_t sb = (size_t)fwd_tma_stage_bytes(c.fmt);
         const size_t xs = ((size_t)p->n_pad * k_trials * 4 + 127) & ~(size_t)127;
         const size_t xs1 = ((size_t)p->n_pad * 4 + 127) & ~(size_t)127;
         const size_t avail = (size_t)max_smem - fa.sharedSizeBytes - 1024;
@@ -329,8 +329,8 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
         CK(cudaFuncSetAttribute(out->fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 max_smem - (int)fa1.sharedSizeBytes));
     } else {
-        out->fn = fwd_kernel(c.precision, k_trials);
-        out->fn1 = fwd_kernel(c.precision, 1);
+        out->fn = fwd_kernel(c.fmt, k_trials);
+        out->fn1 = fwd_kernel(c.fmt, 1);
         if (!out->fn) return set_error("no forward kernel for k_trials %d", k_trials), IMRT_EINVAL;
         const size_t smem = fwd_smem_bytes(p->n_pad, k_trials, c.precision);
         if (smem + 4096 > (size_t)max_smem)
@@ -640,7 +640,9 @@ imrt_status make_bwd_schedule(imrt_plan* p, const std::vector<int64_t>& len) {
 imrt_status build_sell(imrt_plan* p, SellCopy* c, int precision, const int64_t* row_ptr, const int32_t* col,
                        const float* val, const int32_t* len, const uint8_t* mask_in, cudaStream_t s) {
     c->precision = precision;
-    c->ge = fwd_group_entries(precision);
+    // FP32 values with 16-bit beamlet indices whenever the beamlets fit (6 bytes per entry)
+    c->fmt = precision == IMRT_FP32 && p->n <= 65536 ? kFmtF32C16 : precision;
+    c->ge = fwd_group_entries(c->fmt);
     TRY(dalloc(p, &c->slice_len, p->n_slices));
     TRY(dalloc(p, &c->slice_off, p->n_slices + 1));
     Temp tent;
@@ -661,11 +663,11 @@ imrt_status build_sell(imrt_plan* p, SellCopy* c, int precision, const int64_t* 
         run += (int64_t)sl[i] * kSlice * c->ge;
     }
     TRY(dalloc_bytes(p, &c->val, (size_t)c->entries * elem_bytes(precision) + 64));
-    TRY(dalloc_bytes(p, &c->col, (size_t)c->entries * col_bytes(precision) + 64));
+    TRY(dalloc_bytes(p, &c->col, (size_t)c->entries * (c->fmt == IMRT_FP32 ? 4 : 2) + 64));
     uint8_t* mask_out = precision == IMRT_FP32 ? p->mask : nullptr;
     Temp tmask;
     if (!mask_out) TRY(talloc(tmask, &mask_out, p->m_pad));
-    CK(launch_sell_fill(precision, row_ptr, col, val, p->perm, mask_in, p->m, p->m_pad, c->slice_off, c->slice_len,
+    CK(launch_sell_fill(c->fmt, row_ptr, col, val, p->perm, mask_in, p->m, p->m_pad, c->slice_off, c->slice_len,
                         precision == IMRT_FP32 ? nullptr : p->inv_scale, c->val, c->col, mask_out, s));
     CK(cudaStreamSynchronize(s));
     return IMRT_OK;
@@ -1698,7 +1700,7 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     const SellCopy& c = copy_of(p, p->opt.precision);
     info->sell_entries = c.entries;
     info->t_entries = p->opt.precision == IMRT_FP32 ? p->t_entries : p->tq_entries;
-    const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = (int64_t)col_bytes(p->opt.precision);
+    const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = c.fmt == IMRT_FP32 ? 4 : 2;
     // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes, mask read)
     info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 9;
     info->bwd_bytes = p->opt.precision == IMRT_FP32

@@ -145,14 +145,15 @@ __device__ __forceinline__ void store_val(void* dst, int64_t k, float v) {
     }
 }
 
-template <int PREC>
+template <int PREC, bool C16>
 __device__ __forceinline__ void store_col(void* dst, int64_t k, int32_t c) {
-    if constexpr (PREC == IMRT_FP32) static_cast<int32_t*>(dst)[k] = c;
+    if constexpr (PREC == IMRT_FP32 && !C16) static_cast<int32_t*>(dst)[k] = c;
     else static_cast<uint16_t*>(dst)[k] = (uint16_t)c;
 }
 
-// One thread per permuted row: writes the row into its lane of the slice layout.
-template <int PREC, int GE>
+// One thread per permuted row: writes the row into its lane of the slice layout
+// (C16: 16-bit beamlet indices with FP32 values).
+template <int PREC, int GE, bool C16 = false>
 __global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const float* __restrict__ val, const int32_t* __restrict__ perm,
                             const uint8_t* __restrict__ mask_in, int32_t m, int32_t m_pad,
@@ -172,10 +173,10 @@ __global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* 
             const int c = col[a + e];
             const float v = inv_scale ? val[a + e] * inv_scale[c] : val[a + e];
             store_val<PREC>(sval, dst, v);
-            store_col<PREC>(scol, dst, c);
+            store_col<PREC, C16>(scol, dst, c);
         } else {
             store_val<PREC>(sval, dst, 0.0f);
-            store_col<PREC>(scol, dst, 0);
+            store_col<PREC, C16>(scol, dst, 0);
         }
     }
     mask_out[p] = j >= 0 ? mask_in[j] : (uint8_t)0;
@@ -439,12 +440,17 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t count, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_sell_fill(int precision, const int64_t* row_ptr, const int32_t* col, const float* val,
+cudaError_t launch_sell_fill(int fmt, const int64_t* row_ptr, const int32_t* col, const float* val,
                              const int32_t* perm, const uint8_t* mask_in, int32_t m, int32_t m_pad,
                              const int64_t* slice_off, const int32_t* slice_len, const float* inv_scale,
                              void* sval, void* scol, uint8_t* mask_out, cudaStream_t stream) {
     const int g = blocks_for(m_pad, 128);
-    switch (precision) {
+    switch (fmt) {
+        case kFmtF32C16:
+            k_sell_fill<IMRT_FP32, 8, true><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad,
+                                                                   slice_off, slice_len, nullptr, sval, scol,
+                                                                   mask_out);
+            break;
         case IMRT_FP32:
             k_sell_fill<IMRT_FP32, 4><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
                                                              slice_len, nullptr, sval, scol, mask_out);

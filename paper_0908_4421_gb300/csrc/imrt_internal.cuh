@@ -24,7 +24,10 @@ constexpr int kSigma = 1024;      // sorting window (rows)
 constexpr int kMaxStruct = 8;
 constexpr int kMaxTrials = 8;     // Armijo step sizes per forward pass
 constexpr int kGroupSlices = 32;  // slices per objective group sum
-constexpr int kSets = kMaxTrials + 1;  // x/z/r buffer sets: accepted + trials
+constexpr int kSets = kMaxTrials + 1;
+// SELL copy format ids: the imrt_precision values, and FP32 values with 16-bit beamlet
+// indices (6 bytes per stored entry instead of 8; plans with n <= 65536 beamlets)
+constexpr int kFmtF32C16 = 100;  // x/z/r buffer sets: accepted + trials
 constexpr int kFwdThreads = 512;
 #ifndef IMRT_BWD_THREADS
 #define IMRT_BWD_THREADS 256
@@ -207,15 +210,15 @@ struct BwdArgs {
 void set_last_error_message(const char* msg);
 
 // Kernel launchers / function pointers (kernels.cu).
-const void* fwd_kernel(int precision, int k_trials);
-const void* fwd_tma_kernel(int precision, int k_trials);
-int fwd_tma_stage_bytes(int precision);
+const void* fwd_kernel(int fmt, int k_trials);
+const void* fwd_tma_kernel(int fmt, int k_trials);
+int fwd_tma_stage_bytes(int fmt);
 const void* bwd_kernel(int precision);
 const void* bwd_fixed_kernel(int precision);
 const void* init_kernel();
 const void* finish_kernel();
 size_t fwd_smem_bytes(int n_pad, int k_trials, int precision);
-int fwd_group_entries(int precision);
+int fwd_group_entries(int fmt);
 
 // Setup kernels (format.cu), all on `stream`.
 cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
@@ -224,7 +227,7 @@ cudaError_t launch_sigma_sort(const int32_t* len, int32_t m, int32_t m_pad, int3
 cudaError_t launch_slice_sizes(const int32_t* len, const int32_t* perm, int32_t m, int32_t n_slices, int ge,
                                int32_t* slice_len, int64_t* slice_entries, cudaStream_t stream);
 cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t stream);
-cudaError_t launch_sell_fill(int precision, const int64_t* row_ptr, const int32_t* col, const float* val,
+cudaError_t launch_sell_fill(int fmt, const int64_t* row_ptr, const int32_t* col, const float* val,
                              const int32_t* perm, const uint8_t* mask_in, int32_t m, int32_t m_pad,
                              const int64_t* slice_off, const int32_t* slice_len, const float* inv_scale,
                              void* sval, void* scol, uint8_t* mask_out, cudaStream_t stream);

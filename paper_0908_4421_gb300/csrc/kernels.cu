@@ -34,6 +34,9 @@ namespace imrt {
 #ifndef IMRT_FWD_MINB1
 #define IMRT_FWD_MINB1 1  // resident CTAs per SM the single-trial instance is built for
 #endif
+#ifndef IMRT_FWD_MINB_Q
+#define IMRT_FWD_MINB_Q 1  // resident CTAs per SM for the 16-bit formats (1 or 2)
+#endif
 #ifndef IMRT_FWD_UNROLL
 #define IMRT_FWD_UNROLL 8  // groups in flight per lane (FP8: half as many, each is 48 bytes)
 #endif
@@ -93,17 +96,23 @@ __device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T, uint32_t t
 // Storage formats of the voxel-major copy. GE = entries per 16-byte value load.
 // ---------------------------------------------------------------------------
 // VB / CB: bytes of values / column indices per lane and group.
+// SELL copy formats. KIND: 0 FP32 values / int32 columns, 1 FP32 values / 16-bit columns,
+// 2 FP16 / 16-bit, 3 BF16 / 16-bit, 4 FP8-e4m3 / 16-bit. GE entries per lane and group;
+// VB / CB bytes of values / columns per lane and group.
 struct FmtF32 {
-    static constexpr int GE = 4, VB = 16, CB = 16;
+    static constexpr int GE = 4, VB = 16, CB = 16, KIND = 0;
+};
+struct FmtF32C16 {
+    static constexpr int GE = 8, VB = 32, CB = 16, KIND = 1;
 };
 struct FmtF16 {
-    static constexpr int GE = 8, VB = 16, CB = 16;
+    static constexpr int GE = 8, VB = 16, CB = 16, KIND = 2;
 };
 struct FmtBF16 {
-    static constexpr int GE = 8, VB = 16, CB = 16;
+    static constexpr int GE = 8, VB = 16, CB = 16, KIND = 3;
 };
 struct FmtF8 {
-    static constexpr int GE = 16, VB = 16, CB = 32;
+    static constexpr int GE = 16, VB = 16, CB = 32, KIND = 4;
 };
 
 // acc[q] += v * xs[c * KT + q] for one entry (x_t of all trials interleaved in shared memory).
@@ -151,9 +160,14 @@ struct GroupRegs {
 template <class F>
 __device__ __forceinline__ void load_group(const void* __restrict__ val, const void* __restrict__ col, int64_t off,
                                            int k, int lane, GroupRegs& g) {
-    if constexpr (F::GE == 4) {
+    if constexpr (F::KIND == 0) {
         g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 32 + lane);
         g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const int32_t*>(col) + off) + (size_t)k * 32 + lane);
+    } else if constexpr (F::KIND == 1) {  // 8 FP32 values (two words), 8 16-bit columns
+        const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 64 + 2 * lane;
+        g.v = ld_stream(vp);
+        g.c1 = ld_stream(vp + 1);
+        g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane);
     } else if constexpr (F::GE == 8) {
         g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + off) + (size_t)k * 32 + lane);
         g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane);
@@ -170,9 +184,16 @@ template <class F, int KT>
 __device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __restrict__ xs, float (&acc)[KT]) {
     const uint32_t vv[4] = {g.v.x, g.v.y, g.v.z, g.v.w};
     const uint32_t cc[4] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w};
-    if constexpr (F::GE == 4) {
+    if constexpr (F::KIND == 0) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) fma_entry<KT>(__uint_as_float(vv[h]), (int)cc[h], xs, acc);
+    } else if constexpr (F::KIND == 1) {
+        const uint32_t v8[8] = {g.v.x, g.v.y, g.v.z, g.v.w, g.c1.x, g.c1.y, g.c1.z, g.c1.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            fma_entry<KT>(__uint_as_float(v8[2 * h]), (int)(cc[h] & 0xffffu), xs, acc);
+            fma_entry<KT>(__uint_as_float(v8[2 * h + 1]), (int)(cc[h] >> 16), xs, acc);
+        }
     } else if constexpr (F::GE == 8) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -208,7 +229,10 @@ __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, cons
                                               float (&acc)[KT]) {
 #if IMRT_FWD_PIPE
     // two register stages of U groups: while one stage is consumed the other is in flight
-    constexpr int U = (F::GE == 16 || KT >= 4) ? 2 : IMRT_FWD_UNROLL / 2;
+    constexpr bool q16 = F::KIND == 2 || F::KIND == 3;
+    constexpr int U = (F::KIND == 4 || KT >= 4 || (q16 && IMRT_FWD_MINB_Q > 1)) ? 2
+                      : F::KIND == 1                                              ? 3
+                                                                                  : IMRT_FWD_UNROLL / 2;
     GroupRegs a[U], b[U];
     auto load = [&](GroupRegs(&r)[U], int k) {
 #pragma unroll
@@ -233,7 +257,8 @@ __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, cons
     }
 #else
     // FP8 groups are 48 bytes and four or more trials need their accumulators: half the rounds
-    constexpr int U = ((F::GE == 16 || KT >= 4) && IMRT_FWD_UNROLL > 4) ? IMRT_FWD_UNROLL / 2 : IMRT_FWD_UNROLL;
+    constexpr int U = ((F::KIND == 4 || F::KIND == 1 || KT >= 4) && IMRT_FWD_UNROLL > 4) ? IMRT_FWD_UNROLL / 2
+                                                                                       : IMRT_FWD_UNROLL;
     for (int k = g0; k < g1; k += U) {
         GroupRegs r[U];
 #pragma unroll
@@ -616,7 +641,9 @@ __device__ __forceinline__ UnitRec load_unit(const UnitRec* r, bool shared) {
 // Forward pass (fused step + dose + penalty + objective partials).
 // ---------------------------------------------------------------------------
 template <class F, int KT>
-__global__ void __launch_bounds__(kFwdThreads, KT <= 2 ? IMRT_FWD_MINB1 : 1) k_forward(const FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads,
+                                  KT <= 2 ? ((F::KIND == 2 || F::KIND == 3) ? IMRT_FWD_MINB_Q : IMRT_FWD_MINB1) : 1)
+    k_forward(const FwdArgs a) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar, bar_g, bar_r;
     __shared__ Terms T;
@@ -873,7 +900,17 @@ __device__ __forceinline__ void staged_dot(const unsigned char* __restrict__ sta
     const unsigned char* cbase = stage + kTmaStageGroups * kSlice * F::VB;
     for (int k = 0; k < ng; ++k) {
         const uint4 vw = *reinterpret_cast<const uint4*>(vbase + ((size_t)k * kSlice + lane) * F::VB);
-        if constexpr (F::GE == 4) {
+        if constexpr (F::KIND == 1) {
+            const uint4 vw1 = *reinterpret_cast<const uint4*>(vbase + ((size_t)k * kSlice + lane) * F::VB + 16);
+            const uint4 cw = *reinterpret_cast<const uint4*>(cbase + ((size_t)k * kSlice + lane) * F::CB);
+            const uint32_t v8[8] = {vw.x, vw.y, vw.z, vw.w, vw1.x, vw1.y, vw1.z, vw1.w};
+            const uint32_t cc[4] = {cw.x, cw.y, cw.z, cw.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                fma_entry<KT>(__uint_as_float(v8[2 * h]), (int)(cc[h] & 0xffffu), xs, acc);
+                fma_entry<KT>(__uint_as_float(v8[2 * h + 1]), (int)(cc[h] >> 16), xs, acc);
+            }
+        } else if constexpr (F::GE == 4) {
             const int4 cw = *reinterpret_cast<const int4*>(cbase + ((size_t)k * kSlice + lane) * F::CB);
             fma_entry<KT>(__uint_as_float(vw.x), cw.x, xs, acc);
             fma_entry<KT>(__uint_as_float(vw.y), cw.y, xs, acc);
@@ -1537,9 +1574,10 @@ static const void* fwd_for_kt(int kt) {
     }
 }
 
-const void* fwd_kernel(int precision, int k_trials) {
-    switch (precision) {
+const void* fwd_kernel(int fmt, int k_trials) {
+    switch (fmt) {
         case IMRT_FP32: return fwd_for_kt<FmtF32>(k_trials);
+        case kFmtF32C16: return fwd_for_kt<FmtF32C16>(k_trials);
         case IMRT_FP16: return fwd_for_kt<FmtF16>(k_trials);
         case IMRT_BF16: return fwd_for_kt<FmtBF16>(k_trials);
         case IMRT_FP8E4M3: return fwd_for_kt<FmtF8>(k_trials);
@@ -1558,9 +1596,10 @@ static const void* fwd_tma_for_kt(int kt) {
     }
 }
 
-const void* fwd_tma_kernel(int precision, int k_trials) {
-    switch (precision) {
+const void* fwd_tma_kernel(int fmt, int k_trials) {
+    switch (fmt) {
         case IMRT_FP32: return fwd_tma_for_kt<FmtF32>(k_trials);
+        case kFmtF32C16: return fwd_tma_for_kt<FmtF32C16>(k_trials);
         case IMRT_FP16: return fwd_tma_for_kt<FmtF16>(k_trials);
         case IMRT_BF16: return fwd_tma_for_kt<FmtBF16>(k_trials);
         case IMRT_FP8E4M3: return fwd_tma_for_kt<FmtF8>(k_trials);
@@ -1568,9 +1607,10 @@ const void* fwd_tma_kernel(int precision, int k_trials) {
     }
 }
 
-int fwd_tma_stage_bytes(int precision) {
-    switch (precision) {
+int fwd_tma_stage_bytes(int fmt) {
+    switch (fmt) {
         case IMRT_FP32: return tma_stage_bytes<FmtF32>();
+        case kFmtF32C16: return tma_stage_bytes<FmtF32C16>();
         case IMRT_FP16: return tma_stage_bytes<FmtF16>();
         case IMRT_BF16: return tma_stage_bytes<FmtBF16>();
         default: return tma_stage_bytes<FmtF8>();
@@ -1600,9 +1640,10 @@ const void* bwd_fixed_kernel(int precision) {
 const void* init_kernel() { return (const void*)k_init; }
 const void* finish_kernel() { return (const void*)k_finish; }
 
-int fwd_group_entries(int precision) {
-    switch (precision) {
+int fwd_group_entries(int fmt) {
+    switch (fmt) {
         case IMRT_FP32: return FmtF32::GE;
+        case kFmtF32C16: return FmtF32C16::GE;
         case IMRT_FP16: return FmtF16::GE;
         case IMRT_BF16: return FmtBF16::GE;
         default: return FmtF8::GE;
