@@ -160,6 +160,7 @@ struct imrt_plan {
     int64_t* t_off = nullptr;
     float* t_val = nullptr;
     void* t_valq = nullptr;            // reduced-precision beamlet-major values
+    float* t_vals = nullptr;           // FP32 values of the segmented beamlet-major copy
     uint16_t* t_lo = nullptr;          // their 16-bit voxel offsets
     int64_t* t_seg = nullptr;          // n * H + 1 segment starts
     int32_t t_H = 0;
@@ -562,10 +563,16 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     return a;
 }
 
+// Transposed-pass format of a precision: the reduced formats, FP32 in the segmented layout
+// (kFmtF32C16) when the plan keeps one, else FP32 with int32 voxel indices.
+int bwd_fmt(const imrt_plan* p, int precision) {
+    return precision != IMRT_FP32 ? precision : (p->t_H > 0 ? kFmtF32C16 : IMRT_FP32);
+}
+
 BwdArgs bwd_args(imrt_plan* p, int precision, int guard) {
     BwdArgs a{};
     a.t_off = p->t_off;
-    a.val = precision == IMRT_FP32 ? (const void*)p->t_val : p->t_valq;
+    a.val = precision != IMRT_FP32 ? p->t_valq : (p->t_H > 0 ? (const void*)p->t_vals : (const void*)p->t_val);
     a.row = p->t_row;
     a.order = p->bwd_order;
     a.next_row = p->bwd_next;
@@ -611,14 +618,15 @@ imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision 
     a.pw_v = power_v;
     a.pw_lam = power_lam;
     void* args[] = {&a};
-    CK(cudaLaunchKernel(bwd_fixed_kernel(precision), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0, stream_of(p)));
+    CK(cudaLaunchKernel(bwd_fixed_kernel(bwd_fmt(p, precision)), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0,
+                        stream_of(p)));
     return IMRT_OK;
 }
 
 // Transposed-pass schedule: a persistent grid whose CTAs take beamlet rows longest first.
 imrt_status make_bwd_schedule(imrt_plan* p, const std::vector<int64_t>& len) {
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel(IMRT_FP32), kBwdThreads, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel(bwd_fmt(p, IMRT_FP32)), kBwdThreads, 0));
     per_sm = std::max(1, std::min(per_sm, kBwdPerSm));
     const int grid = (int)std::min<int64_t>((int64_t)p->sm_count * per_sm, std::max<int64_t>(1, p->n));
     std::vector<int32_t> order(p->n);
@@ -785,13 +793,24 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     std::vector<int64_t> hlen(n);
     CK(cudaMemcpyAsync(hlen.data(), col_len, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    TRY(dalloc(p, &p->t_val, p->t_entries + 4));
-    TRY(dalloc(p, &p->t_row, p->t_entries + 4));
+    // Plans with at most 16 segments of 65536 voxels keep segmented beamlet-major copies (16-bit
+    // voxel offsets: 6 bytes per FP32 entry); the int32-index copy is then only the source
+    // of the segmented ones and is freed with the build's temporaries.
+    const int H = (int)((p->m_pad + 65535) / 65536);
+    const bool segmented = H <= 16;
+    if (!segmented && p->opt.precision != IMRT_FP32)
+        return set_error("reduced precision supports at most 1048576 voxels"), IMRT_EUNSUPPORTED;
+    Temp tval_src, trow_src;
+    if (segmented) {
+        TRY(talloc(tval_src, &p->t_val, p->t_entries + 4));
+        TRY(talloc(trow_src, &p->t_row, p->t_entries + 4));
+    } else {
+        TRY(dalloc(p, &p->t_val, p->t_entries + 4));
+        TRY(dalloc(p, &p->t_row, p->t_entries + 4));
+    }
     CK(launch_transpose_fill(row_ptr, col, val, p->perm, p->m_pad, n, chunk_rows, counts, col_len, p->t_off,
                              p->t_val, p->t_row, s));
-    if (p->opt.precision != IMRT_FP32) {
-        const int H = (int)((p->m_pad + 65535) / 65536);
-        if (H > 16) return set_error("reduced precision supports at most 1048576 voxels"), IMRT_EUNSUPPORTED;
+    if (segmented) {
         p->t_H = H;
         Temp tsl;
         int64_t* seg_len;
@@ -801,13 +820,19 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
         CK(launch_scan_i64(seg_len, p->t_seg, (int64_t)n * H, s));
         CK(cudaMemcpyAsync(&p->tq_entries, p->t_seg + (size_t)n * H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        TRY(dalloc_bytes(p, &p->t_valq, (size_t)p->tq_entries * elem_bytes(p->opt.precision) + 64));
         TRY(dalloc(p, &p->t_lo, (size_t)p->tq_entries + 32));
-        CK(launch_tq_fill(p->opt.precision, p->t_off, p->t_row, p->t_val, col_len, n, H, p->t_seg, p->inv_scale,
-                          p->t_valq, p->t_lo, s));
+        TRY(dalloc(p, &p->t_vals, (size_t)p->tq_entries + 16));
+        CK(launch_tq_fill(IMRT_FP32, p->t_off, p->t_row, p->t_val, col_len, n, H, p->t_seg, nullptr, p->t_vals,
+                          p->t_lo, s));
+        if (p->opt.precision != IMRT_FP32) {
+            TRY(dalloc_bytes(p, &p->t_valq, (size_t)p->tq_entries * elem_bytes(p->opt.precision) + 64));
+            CK(launch_tq_fill(p->opt.precision, p->t_off, p->t_row, p->t_val, col_len, n, H, p->t_seg, p->inv_scale,
+                              p->t_valq, p->t_lo, s));
+        }
         CK(cudaStreamSynchronize(s));
     }
     TRY(make_bwd_schedule(p, hlen));
+    if (segmented) p->t_val = nullptr, p->t_row = nullptr;  // freed with the temporaries below
     // --- structures and term coefficients (Eq. (1): c = w / |V_s|) ----------
     Temp tcnt;
     int32_t* scount;
@@ -997,7 +1022,7 @@ imrt_status phase_kernels(imrt_plan* p, int precision, int k_trials, PhaseKernel
     ea.control = 1;
     K->eval = make_launch(sh->fn1, sh->grid, sh->block, sh->smem1, ea);
     BwdCurArgs ba{bwd_args(p, precision, 1), p->v.r};
-    K->bwd = make_launch(bwd_kernel(precision), p->bwd_grid, kBwdThreads, 0, ba);
+    K->bwd = make_launch(bwd_kernel(bwd_fmt(p, precision)), p->bwd_grid, kBwdThreads, 0, ba);
     FwdArgs ta = fwd_args(p, c, *sh, kFwdTrial);
     ta.control = 1;
     K->trial = make_launch(sh->fn, sh->grid, sh->block, sh->smem, ta);
@@ -1023,6 +1048,7 @@ std::vector<size_t> offsets_for(const Launch& l) {
         return {offsetof(InitArgs, st), offsetof(InitArgs, sp), offsetof(InitArgs, v)};
     for (int prec = 0; prec <= IMRT_FP8E4M3; ++prec)
         if (l.fn == bwd_kernel(prec)) return {offsetof(BwdCurArgs, a), offsetof(BwdCurArgs, r_sets)};
+    if (l.fn == bwd_kernel(kFmtF32C16)) return {offsetof(BwdCurArgs, a), offsetof(BwdCurArgs, r_sets)};
     return {0};
 }
 
@@ -1699,11 +1725,11 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     info->nnz = p->nnz;
     const SellCopy& c = copy_of(p, p->opt.precision);
     info->sell_entries = c.entries;
-    info->t_entries = p->opt.precision == IMRT_FP32 ? p->t_entries : p->tq_entries;
+    info->t_entries = p->t_H > 0 ? p->tq_entries : p->t_entries;
     const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = c.fmt == IMRT_FP32 ? 4 : 2;
     // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes, mask read)
     info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 9;
-    info->bwd_bytes = p->opt.precision == IMRT_FP32
+    info->bwd_bytes = p->t_H == 0
                           ? p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4
                           : p->nnz * (vb + 2) + ((int64_t)p->n * p->t_H + 1) * 8 + (int64_t)p->m * 4 +
                                 (int64_t)p->n * 4;

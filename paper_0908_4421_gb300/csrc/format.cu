@@ -286,7 +286,7 @@ __global__ void k_tq_fill(const int64_t* __restrict__ t_off, const int32_t* __re
     const int i = blockIdx.x;
     if (i >= n) return;
     const int64_t a = t_off[i], b = a + col_len[i];
-    const float s = inv_scale[i];
+    const float s = inv_scale ? inv_scale[i] : 1.0f;
     for (int h = 0; h < H; ++h) {
         const int64_t lo_b = lower_bound_row(t_row, a, b, h << 16);
         const int64_t hi_b = h + 1 < H ? lower_bound_row(t_row, a, b, (h + 1) << 16) : b;
@@ -515,6 +515,9 @@ cudaError_t launch_tq_fill(int precision, const int64_t* t_off, const int32_t* t
                            const int64_t* col_len, int32_t n, int32_t H, const int64_t* seg, const float* inv_scale,
                            void* q_val, uint16_t* q_lo, cudaStream_t stream) {
     switch (precision) {
+        case IMRT_FP32:  // unscaled FP32 values in the segmented layout
+            k_tq_fill<IMRT_FP32><<<n, 256, 0, stream>>>(t_off, t_row, t_val, col_len, n, H, seg, nullptr, q_val, q_lo);
+            break;
         case IMRT_FP16:
             k_tq_fill<IMRT_FP16><<<n, 256, 0, stream>>>(t_off, t_row, t_val, col_len, n, H, seg, inv_scale, q_val, q_lo);
             break;

@@ -213,8 +213,8 @@ void set_last_error_message(const char* msg);
 const void* fwd_kernel(int fmt, int k_trials);
 const void* fwd_tma_kernel(int fmt, int k_trials);
 int fwd_tma_stage_bytes(int fmt);
-const void* bwd_kernel(int precision);
-const void* bwd_fixed_kernel(int precision);
+const void* bwd_kernel(int fmt);        // fmt: a precision, or kFmtF32C16 (segmented FP32)
+const void* bwd_fixed_kernel(int fmt);
 const void* init_kernel();
 const void* finish_kernel();
 size_t fwd_smem_bytes(int n_pad, int k_trials, int precision);

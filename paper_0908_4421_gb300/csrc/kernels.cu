@@ -1343,7 +1343,7 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
         // raw 16-byte words of a group and its voxel segment; values are converted at use, so
         // both groups' loads are in flight before the first gather
         struct Raw {
-            uint4 v, lw;
+            uint4 v, v2, lw;  // v2: values 4..7 of an FP32 group
             int h;
         };
         auto load = [&](int k, Raw& q) {
@@ -1354,6 +1354,10 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
             if constexpr (PREC == IMRT_FP8E4M3) {
                 const uint2 w = ld_stream_u2(reinterpret_cast<const uint2*>(static_cast<const uint8_t*>(a.val) + e));
                 q.v = make_uint4(w.x, w.y, 0u, 0u);
+            } else if constexpr (PREC == kFmtF32C16) {
+                const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const float*>(a.val) + e);
+                q.v = ld_stream(vp);
+                q.v2 = ld_stream(vp + 1);
             } else {
                 q.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(a.val) + e));
             }
@@ -1362,7 +1366,11 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
         auto use = [&](const Raw& q, float& acc) {
             const float* rb = r + ((size_t)q.h << 16);
             float v[8];
-            if constexpr (PREC == IMRT_FP8E4M3) {
+            if constexpr (PREC == kFmtF32C16) {
+                const uint32_t ww[8] = {q.v.x, q.v.y, q.v.z, q.v.w, q.v2.x, q.v2.y, q.v2.z, q.v2.w};
+#pragma unroll
+                for (int h = 0; h < 8; ++h) v[h] = __uint_as_float(ww[h]);
+            } else if constexpr (PREC == IMRT_FP8E4M3) {
                 const uint32_t ww[2] = {q.v.x, q.v.y};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -1410,7 +1418,7 @@ __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float*
         if (wib == 0) {
             float t = lane < kBwdThreads / 32 ? red[lane] : 0.0f;
             t = warp_sum(t);
-            if (lane == 0) a.g[i] = t * a.scale[i];
+            if (lane == 0) a.g[i] = a.scale ? t * a.scale[i] : t;
         }
         __syncthreads();
         buf ^= 1;
@@ -1617,9 +1625,10 @@ int fwd_tma_stage_bytes(int fmt) {
     }
 }
 
-const void* bwd_kernel(int precision) {
-    switch (precision) {
+const void* bwd_kernel(int fmt) {
+    switch (fmt) {
         case IMRT_FP32: return (const void*)k_transposed_cur<IMRT_FP32>;
+        case kFmtF32C16: return (const void*)k_transposed_cur<kFmtF32C16>;
         case IMRT_FP16: return (const void*)k_transposed_cur<IMRT_FP16>;
         case IMRT_BF16: return (const void*)k_transposed_cur<IMRT_BF16>;
         case IMRT_FP8E4M3: return (const void*)k_transposed_cur<IMRT_FP8E4M3>;
@@ -1627,9 +1636,10 @@ const void* bwd_kernel(int precision) {
     }
 }
 
-const void* bwd_fixed_kernel(int precision) {
-    switch (precision) {
+const void* bwd_fixed_kernel(int fmt) {
+    switch (fmt) {
         case IMRT_FP32: return (const void*)k_transposed<IMRT_FP32>;
+        case kFmtF32C16: return (const void*)k_transposed<kFmtF32C16>;
         case IMRT_FP16: return (const void*)k_transposed<IMRT_FP16>;
         case IMRT_BF16: return (const void*)k_transposed<IMRT_BF16>;
         case IMRT_FP8E4M3: return (const void*)k_transposed<IMRT_FP8E4M3>;
