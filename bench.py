@@ -50,7 +50,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "imrt_internal.cuh", "ptx.cuh"):
+    for f in ("kernels.cu", "imrt_internal.cuh", "ptx.cuh", "format.cu", "api.cu"):  # kernels, layouts, schedule
         with open(os.path.join(ROOT, "paper_0908_4421_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -386,7 +386,7 @@ def main():
                    "kernel_variant": best_variant,
                    "tuned_s": {k: round(v, 5) for k, v in tuned.items()}, "max_iter": args.max_iter, "delta": 1e-6,
                    "lambda0": f"rule 8/L = {lam0:.6g}",
-                   "l2": f"inputs larger than L2: D held twice, {(info['sell_entries'] + info['t_entries']) * 8 / 1e9:.2f} GB > 129 MB",
+                   "l2": f"inputs larger than L2: one forward and one transposed pass read {(info['fwd_bytes'] + info['bwd_bytes']) / 1e9:.2f} GB > 129 MB",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "traffic": traffic, "kernel": dominant,

@@ -286,19 +286,27 @@ __global__ void k_tq_fill(const int64_t* __restrict__ t_off, const int32_t* __re
     const int i = blockIdx.x;
     if (i >= n) return;
     const int64_t a = t_off[i], b = a + col_len[i];
+    const int64_t r0 = seg[(int64_t)i * H];
     const float s = inv_scale ? inv_scale[i] : 1.0f;
     for (int h = 0; h < H; ++h) {
         const int64_t lo_b = lower_bound_row(t_row, a, b, h << 16);
         const int64_t hi_b = h + 1 < H ? lower_bound_row(t_row, a, b, (h + 1) << 16) : b;
         const int64_t dst0 = seg[(int64_t)i * H + h], dst1 = seg[(int64_t)i * H + h + 1];
         for (int64_t k = dst0 + threadIdx.x; k < dst1; k += blockDim.x) {
+            // k is the entry's place in the sorted run; it is stored at its transposed place
+            // inside the piece of its 256-entry block that lies in this run (all multiples of 8)
+            const int64_t blk = r0 + ((k - r0) & ~(int64_t)(kTqBlock - 1));
+            const int64_t ps = blk > dst0 ? blk : dst0;
+            const int64_t pe = blk + kTqBlock < dst1 ? blk + kTqBlock : dst1;
+            const int sg = (int)((pe - ps) >> 3), u = (int)(k - ps);
+            const int64_t d = ps + 8 * (u % sg) + u / sg;
             const int64_t src = lo_b + (k - dst0);
             if (src < hi_b) {
-                store_val<PREC>(q_val, k, t_val[src] * s);
-                q_lo[k] = (uint16_t)(t_row[src] & 0xffff);
+                store_val<PREC>(q_val, d, t_val[src] * s);
+                q_lo[d] = (uint16_t)(t_row[src] & 0xffff);
             } else {
-                store_val<PREC>(q_val, k, 0.0f);
-                q_lo[k] = 0;
+                store_val<PREC>(q_val, d, 0.0f);
+                q_lo[d] = 0;
             }
         }
     }

@@ -34,6 +34,11 @@ constexpr int kFwdThreads = 512;
 #endif
 constexpr int kBwdThreads = IMRT_BWD_THREADS;   // transposed-pass CTA size
 constexpr int kBwdPerSm = 2048 / kBwdThreads;   // resident transposed CTAs per SM (64 warps)
+// Segmented beamlet-major copies: a row is cut into blocks of 256 entries (one warp's 32
+// groups of 8); the piece of a block inside one segment run, sg groups, is stored
+// transposed, so group l holds the run's entries l, l + sg, ..., l + 7 sg and the t-th
+// entries of a warp's groups are sg consecutive voxels of the row.
+constexpr int kTqBlock = 256;
 constexpr int kCtlThreads = 256;
 constexpr int kTmaMaxConsumers = 8;   // bulk-copy forward kernel: 1 producer + up to 8 consumer warps
 constexpr int kTmaThreads = 32 * (1 + kTmaMaxConsumers);
@@ -193,7 +198,8 @@ struct BwdArgs {
     int32_t* next_row;        // schedule counter, reset by the last CTA
     int32_t* ticket;          // CTAs finished in the current launch
     int32_t n;
-    // reduced precision: 16-bit voxel indices in segments of 65536 voxels
+    // segmented copies: 16-bit voxel indices in segments of 65536 voxels, stored in the
+    // transposed block order of kTqBlock
     const int64_t* seg;       // n * H + 1 entry offsets (row i, segment h at i * H + h)
     const uint16_t* lo;       // voxel index & 0xffff
     int32_t H;

@@ -1317,10 +1317,13 @@ __device__ __forceinline__ bool transposed_rows(const BwdArgs& a, const float* _
     return is_last;
 }
 
-// Reduced-precision rows: groups of 8 entries, 16-bit voxel offsets inside segments of 65536
-// voxels; the row's segment boundaries are staged in shared memory.
+// Segmented rows: groups of 8 entries, 16-bit voxel offsets inside segments of 65536 voxels;
+// the row's segment boundaries are staged in shared memory. Group k goes to lane k % 32, so a
+// warp takes one kTqBlock block of the row, and the block's transposed order makes each of
+// its 8 gather instructions read consecutive voxels (few L1 lines) instead of every 8th.
 template <int PREC>
 __device__ __forceinline__ bool transposed_rows_q(const BwdArgs& a, const float* __restrict__ r) {
+    static_assert(kTqBlock == 8 * 32 && kBwdThreads % 32 == 0, "a warp's groups form one block");
     __shared__ float red[kBwdThreads / 32];
     __shared__ int next_idx[2];
     __shared__ int64_t sb[2][17];
