@@ -547,6 +547,7 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.u = sh.units;
     a.stages = sh.stages;
     a.mask = p->mask;
+    a.r_index = p->perm;
     a.scale = c.precision == IMRT_FP32 ? nullptr : p->scale;
     a.vt = p->vt_on ? p->vt_p : nullptr;
     a.vtm = p->vt_on ? p->vtm_p : nullptr;
@@ -779,7 +780,7 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     }
     // --- beamlet-major copy -------------------------------------------------
     const int chunk_rows = 512;
-    const int n_chunks = (p->m_pad + chunk_rows - 1) / chunk_rows;
+    const int n_chunks = (p->m + chunk_rows - 1) / chunk_rows;
     Temp tcounts, tcl, tpad;
     int32_t* counts;
     int64_t* col_len;
@@ -788,7 +789,7 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     TRY(talloc(tcl, &col_len, n));
     TRY(talloc(tpad, &padded, n));
     TRY(dalloc(p, &p->t_off, n + 1));
-    CK(launch_transpose_plan(row_ptr, col, p->perm, p->m_pad, n, chunk_rows, counts, col_len, padded, p->t_off, s));
+    CK(launch_transpose_plan(row_ptr, col, p->m, n, chunk_rows, counts, col_len, padded, p->t_off, s));
     CK(cudaMemcpyAsync(&p->t_entries, p->t_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     std::vector<int64_t> hlen(n);
     CK(cudaMemcpyAsync(hlen.data(), col_len, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
@@ -808,8 +809,8 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
         TRY(dalloc(p, &p->t_val, p->t_entries + 4));
         TRY(dalloc(p, &p->t_row, p->t_entries + 4));
     }
-    CK(launch_transpose_fill(row_ptr, col, val, p->perm, p->m_pad, n, chunk_rows, counts, col_len, p->t_off,
-                             p->t_val, p->t_row, s));
+    CK(launch_transpose_fill(row_ptr, col, val, p->m, n, chunk_rows, counts, col_len, p->t_off, p->t_val,
+                             p->t_row, s));
     if (segmented) {
         p->t_H = H;
         Temp tsl;
@@ -1727,8 +1728,9 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     info->sell_entries = c.entries;
     info->t_entries = p->t_H > 0 ? p->tq_entries : p->t_entries;
     const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = c.fmt == IMRT_FP32 ? 4 : 2;
-    // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes, mask read)
-    info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 9;
+    // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes; mask and
+    // r-order reads)
+    info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 13;
     info->bwd_bytes = p->t_H == 0
                           ? p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4
                           : p->nnz * (vb + 2) + ((int64_t)p->n * p->t_H + 1) * 8 + (int64_t)p->m * 4 +

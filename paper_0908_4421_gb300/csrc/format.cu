@@ -183,16 +183,13 @@ __global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* 
 }
 
 // Transposition, pass 1: per chunk of permuted rows, how many entries each beamlet gets.
-__global__ void k_t_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                          const int32_t* __restrict__ perm, int32_t m_pad, int32_t n, int32_t chunk_rows,
-                          int32_t* __restrict__ counts) {
+__global__ void k_t_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int32_t m,
+                          int32_t n, int32_t chunk_rows, int32_t* __restrict__ counts) {
     extern __shared__ int32_t hist[];
     for (int c = threadIdx.x; c < n; c += blockDim.x) hist[c] = 0;
     __syncthreads();
-    const int p0 = blockIdx.x * chunk_rows, p1 = min(m_pad, p0 + chunk_rows);
-    for (int p = p0; p < p1; ++p) {
-        const int j = perm[p];
-        if (j < 0) continue;
+    const int j0 = blockIdx.x * chunk_rows, j1 = min(m, j0 + chunk_rows);
+    for (int j = j0; j < j1; ++j) {
         for (int64_t k = row_ptr[j] + threadIdx.x; k < row_ptr[j + 1]; k += blockDim.x) atomicAdd(&hist[col[k]], 1);
     }
     __syncthreads();
@@ -218,25 +215,23 @@ __global__ void k_t_colscan(int32_t* __restrict__ counts, int32_t n_chunks, int3
 // receives voxels in ascending (permuted) index; within one voxel row the
 // columns are distinct, so the per-beamlet cursors need no atomics.
 __global__ void k_t_scatter(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                            const float* __restrict__ val, const int32_t* __restrict__ perm, int32_t m_pad,
-                            int32_t n, int32_t chunk_rows, const int32_t* __restrict__ counts,
-                            const int64_t* __restrict__ t_off, float* __restrict__ t_val,
-                            int32_t* __restrict__ t_row) {
+                            const float* __restrict__ val, int32_t m, int32_t n, int32_t chunk_rows,
+                            const int32_t* __restrict__ counts, const int64_t* __restrict__ t_off,
+                            float* __restrict__ t_val, int32_t* __restrict__ t_row) {
     extern __shared__ int32_t cursor[];
     for (int c = threadIdx.x; c < n; c += blockDim.x) cursor[c] = counts[(size_t)blockIdx.x * n + c];
     __syncthreads();
-    const int p0 = blockIdx.x * chunk_rows, p1 = min(m_pad, p0 + chunk_rows);
-    for (int p = p0; p < p1; ++p) {
-        const int j = perm[p];
-        if (j >= 0) {
-            for (int64_t k = row_ptr[j] + threadIdx.x; k < row_ptr[j + 1]; k += blockDim.x) {
-                const int c = col[k];
-                const int pos = cursor[c];
-                cursor[c] = pos + 1;
-                const int64_t dst = t_off[c] + pos;
-                t_val[dst] = val[k];
-                t_row[dst] = p;
-            }
+    // the caller's voxel order: it keeps a beamlet's voxels close together in r, which the
+    // transposed pass gathers (the SELL permutation scatters them inside each sorting window)
+    const int j0 = blockIdx.x * chunk_rows, j1 = min(m, j0 + chunk_rows);
+    for (int j = j0; j < j1; ++j) {
+        for (int64_t k = row_ptr[j] + threadIdx.x; k < row_ptr[j + 1]; k += blockDim.x) {
+            const int c = col[k];
+            const int pos = cursor[c];
+            cursor[c] = pos + 1;
+            const int64_t dst = t_off[c] + pos;
+            t_val[dst] = val[k];
+            t_row[dst] = j;
         }
         __syncthreads();
     }
@@ -482,33 +477,31 @@ cudaError_t launch_sell_fill(int fmt, const int64_t* row_ptr, const int32_t* col
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, const int32_t* perm, int32_t m_pad,
-                                  int32_t n, int32_t chunk_rows, int32_t* counts, int64_t* col_len, int64_t* padded,
+cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, int32_t m, int32_t n,
+                                  int32_t chunk_rows, int32_t* counts, int64_t* col_len, int64_t* padded,
                                   int64_t* t_off, cudaStream_t stream) {
-    const int n_chunks = (m_pad + chunk_rows - 1) / chunk_rows;
+    const int n_chunks = (m + chunk_rows - 1) / chunk_rows;
     const size_t smem = (size_t)n * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = set_max_dynamic_smem(k_t_count);
         if (e != cudaSuccess) return e;
     }
-    k_t_count<<<n_chunks, 256, smem, stream>>>(row_ptr, col, perm, m_pad, n, chunk_rows, counts);
+    k_t_count<<<n_chunks, 256, smem, stream>>>(row_ptr, col, m, n, chunk_rows, counts);
     k_t_colscan<<<blocks_for(n, 256), 256, 0, stream>>>(counts, n_chunks, n, col_len, padded);
     k_scan_i64<<<1, 1024, 0, stream>>>(padded, t_off, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* perm,
-                                  int32_t m_pad, int32_t n, int32_t chunk_rows, const int32_t* counts,
-                                  const int64_t* col_len, const int64_t* t_off, float* t_val, int32_t* t_row,
-                                  cudaStream_t stream) {
-    const int n_chunks = (m_pad + chunk_rows - 1) / chunk_rows;
+cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m,
+                                  int32_t n, int32_t chunk_rows, const int32_t* counts, const int64_t* col_len,
+                                  const int64_t* t_off, float* t_val, int32_t* t_row, cudaStream_t stream) {
+    const int n_chunks = (m + chunk_rows - 1) / chunk_rows;
     const size_t smem = (size_t)n * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = set_max_dynamic_smem(k_t_scatter);
         if (e != cudaSuccess) return e;
     }
-    k_t_scatter<<<n_chunks, 256, smem, stream>>>(row_ptr, col, val, perm, m_pad, n, chunk_rows, counts, t_off, t_val,
-                                                 t_row);
+    k_t_scatter<<<n_chunks, 256, smem, stream>>>(row_ptr, col, val, m, n, chunk_rows, counts, t_off, t_val, t_row);
     k_t_pad<<<blocks_for(n, 256), 256, 0, stream>>>(col_len, t_off, n, t_val, t_row);
     return cudaGetLastError();
 }

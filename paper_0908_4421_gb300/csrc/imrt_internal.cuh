@@ -173,6 +173,8 @@ struct FwdArgs {
     const void* col;
     FwdUnits u;
     const uint8_t* mask;         // m_pad, permuted order
+    const int32_t* r_index;      // m_pad: the caller's index of permuted voxel p; r is stored in
+                                 // the caller's voxel order, which the beamlet-major copies use
     const float* scale;          // n_pad per-beamlet value scale, or NULL (FP32)
     const float* vt;             // m_pad per-voxel target dose T_j (permuted), or NULL
     const uint8_t* vtm;          // m_pad: 1 => voxel in V_T
@@ -193,7 +195,7 @@ struct FwdArgs {
 struct BwdArgs {
     const int64_t* t_off;     // n + 1 (entries, padded rows)
     const void* val;
-    const int32_t* row;       // permuted voxel indices
+    const int32_t* row;       // voxel indices in the caller's order (ascending per row)
     const int32_t* order;     // beamlet rows, longest first (dynamic schedule)
     int32_t* next_row;        // schedule counter, reset by the last CTA
     int32_t* ticket;          // CTAs finished in the current launch
@@ -237,13 +239,12 @@ cudaError_t launch_sell_fill(int fmt, const int64_t* row_ptr, const int32_t* col
                              const int32_t* perm, const uint8_t* mask_in, int32_t m, int32_t m_pad,
                              const int64_t* slice_off, const int32_t* slice_len, const float* inv_scale,
                              void* sval, void* scol, uint8_t* mask_out, cudaStream_t stream);
-cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, const int32_t* perm, int32_t m_pad,
-                                  int32_t n, int32_t chunk_rows, int32_t* counts, int64_t* col_len, int64_t* padded,
+cudaError_t launch_transpose_plan(const int64_t* row_ptr, const int32_t* col, int32_t m, int32_t n,
+                                  int32_t chunk_rows, int32_t* counts, int64_t* col_len, int64_t* padded,
                                   int64_t* t_off, cudaStream_t stream);
-cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* perm,
-                                  int32_t m_pad, int32_t n, int32_t chunk_rows, const int32_t* counts,
-                                  const int64_t* col_len, const int64_t* t_off, float* t_val, int32_t* t_row,
-                                  cudaStream_t stream);
+cudaError_t launch_transpose_fill(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m,
+                                  int32_t n, int32_t chunk_rows, const int32_t* counts, const int64_t* col_len,
+                                  const int64_t* t_off, float* t_val, int32_t* t_row, cudaStream_t stream);
 cudaError_t launch_tq_count(const int64_t* t_off, const int32_t* t_row, const int64_t* col_len, int32_t n, int32_t H,
                             int64_t* seg_len, cudaStream_t stream);
 cudaError_t launch_tq_fill(int precision, const int64_t* t_off, const int32_t* t_row, const float* t_val,

@@ -596,16 +596,17 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
         const uint32_t bits = a.mask[p];
         const float tj = a.vt ? a.vt[p] : 0.0f;
         const uint32_t tg = a.vt ? a.vtm[p] : 0u;
+        const int ro = a.r_index[p];
         if (mode == kFwdPower) {
             zq[0][p] = acc[0];
-            rq[0][p] = cdiag(bits, T, tg) * acc[0];
+            rq[0][ro] = cdiag(bits, T, tg) * acc[0];
         } else {
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
                 float rj;
                 penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
                 zq[q][p] = acc[q];
-                rq[q][p] = rj;
+                rq[q][ro] = rj;
             }
         }
     }
@@ -1208,16 +1209,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
             if (p < a.m) {
                 const float tj = a.vt ? a.vt[p] : 0.0f;
                 const uint32_t tg = a.vt ? a.vtm[p] : 0u;
+                const int ro = a.r_index[p];
                 if (mode == kFwdPower) {
                     zq[0][p] = acc[0];
-                    rq[0][p] = cdiag(bits, T, tg) * acc[0];
+                    rq[0][ro] = cdiag(bits, T, tg) * acc[0];
                 } else {
 #pragma unroll
                     for (int q = 0; q < KT; ++q) {
                         float rj;
                         penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
                         zq[q][p] = acc[q];
-                        rq[q][p] = rj;
+                        rq[q][ro] = rj;
                     }
                 }
             }
