@@ -36,6 +36,7 @@
 #ifndef IMRT_H
 #define IMRT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -277,6 +278,14 @@ imrt_status imrt_eval_csr_noalloc(const imrt_csr* D, const uint8_t* structures, 
 
 /* Frees the plan and all its device memory. NULL-safe. */
 void plan_destroy(imrt_plan* plan);
+
+/* Device memory of plans comes from one stream-ordered pool per device that the library
+ * owns and that keeps freed memory for later plans, so creating plans one after another
+ * maps no new memory. This hands the cached memory of the current device's pool back to
+ * the system down to keep_bytes (0: all that no live plan holds). Live plans are not
+ * affected. Returns IMRT_ECUDA if no device is usable or the device has no library pool
+ * (plans then allocate from the device's default pool). */
+imrt_status imrt_trim_memory(size_t keep_bytes);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* imrt_last_error(void);

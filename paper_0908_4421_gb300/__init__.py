@@ -8,5 +8,5 @@ sm_103a CUDA kernels behind a C ABI (include/imrt.h, libimrt.so).
 Importing the package does not load the CUDA library; creating a Plan does,
 and fails loudly if libimrt.so has not been built.
 """
-from .api import Options, Plan, Result, solve_batch, version  # noqa: F401
+from .api import Options, Plan, Result, solve_batch, trim_memory, version  # noqa: F401
 from . import _lib  # noqa: F401

@@ -24,7 +24,8 @@ MODE_GRAPH, MODE_HOST = 0, 1
 # Every symbol include/imrt.h declares.
 EXPORTS = ("imrt_default_options", "plan_create", "plan_set_options", "plan_solve", "plan_dose", "plan_eval",
            "plan_get_x", "plan_get_trace", "plan_info", "plan_cancel", "plan_destroy", "imrt_last_error",
-           "imrt_version", "imrt_eval_csr_noalloc", "plan_solve_batch", "plan_set_voxel_targets")
+           "imrt_version", "imrt_eval_csr_noalloc", "plan_solve_batch", "plan_set_voxel_targets",
+           "imrt_trim_memory")
 
 
 class imrt_csr(ctypes.Structure):
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.imrt_last_error.argtypes = []
     lib.imrt_version.restype = ctypes.c_char_p
     lib.imrt_version.argtypes = []
+    lib.imrt_trim_memory.restype = ctypes.c_int
+    lib.imrt_trim_memory.argtypes = [ctypes.c_size_t]
     lib.imrt_eval_csr_noalloc.restype = ctypes.c_int
     lib.imrt_eval_csr_noalloc.argtypes = [P(imrt_csr), vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
     _lib = lib

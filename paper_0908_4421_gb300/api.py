@@ -221,6 +221,12 @@ def version() -> str:
     return L.load().imrt_version().decode()
 
 
+def trim_memory(keep_bytes: int = 0) -> None:
+    """Hands the device memory the library keeps cached for later plans (current device) back
+    to the system, down to `keep_bytes`."""
+    L.check(L.load().imrt_trim_memory(int(keep_bytes)))
+
+
 def solve_batch(plans, x0s=None, stream: int = 0, raise_on_error: bool = True):
     """plan_solve_batch: all plans in one CUDA-graph launch (one branch per plan)."""
     lib = L.load()

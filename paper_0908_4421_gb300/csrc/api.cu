@@ -215,6 +215,45 @@ namespace {
 
 cudaStream_t stream_of(const imrt_plan* p) { return static_cast<cudaStream_t>(p->opt.stream); }
 
+// Device memory comes from one stream-ordered pool per device that the library owns. The
+// pool keeps freed memory for later plans (no release threshold) instead of handing it back
+// at every synchronisation, which made each plan_create map its buffers afresh;
+// imrt_trim_memory() hands it back. NULL if the pool cannot be made (cudaMallocAsync's
+// default pool is used then).
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+cudaError_t g_pool_error[kMaxDevices] = {};  // why a device has no library pool
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (g_pool_error[dev] != cudaSuccess) return nullptr;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        uint64_t keep = UINT64_MAX;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (pool) cudaMemPoolDestroy(pool);
+            g_pool_error[dev] = e;
+            return nullptr;
+        }
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t pool_malloc(void** ptr, size_t bytes, int dev, cudaStream_t s) {
+    cudaMemPool_t pool = device_pool(dev);
+    return pool ? cudaMallocFromPoolAsync(ptr, bytes, pool, s) : cudaMallocAsync(ptr, bytes, s);
+}
+
 template <class T>
 imrt_status dalloc(imrt_plan* p, T** out, size_t count) {
     *out = nullptr;
@@ -222,7 +261,7 @@ imrt_status dalloc(imrt_plan* p, T** out, size_t count) {
     void* ptr = nullptr;
     // stream-ordered: plan creation and destruction never synchronise the whole device,
     // so plans on other streams keep running (the serving loop relies on this)
-    cudaError_t e = cudaMallocAsync(&ptr, count * sizeof(T), stream_of(p));
+    cudaError_t e = pool_malloc(&ptr, count * sizeof(T), p->device, stream_of(p));
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMallocAsync of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
@@ -256,7 +295,9 @@ template <class T>
 imrt_status talloc(Temp& t, T** out, size_t count) {
     if (count == 0) count = 1;
     t.stream = g_temp_stream;
-    cudaError_t e = cudaMallocAsync(&t.ptr, count * sizeof(T), t.stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = pool_malloc(&t.ptr, count * sizeof(T), dev, t.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("temporary cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
@@ -584,7 +625,6 @@ BwdArgs bwd_args(imrt_plan* p, int precision, int guard) {
     a.H = p->t_H;
     a.scale = precision == IMRT_FP32 ? nullptr : p->scale;
     a.st = p->st;
-    a.r_fixed = nullptr;
     a.g = p->v.g;
     a.m_pad = p->m_pad;
     a.guard = guard;
@@ -614,13 +654,16 @@ imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, f
 imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision = IMRT_FP32,
                           float* power_v = nullptr, double* power_lam = nullptr) {
     BwdArgs a = bwd_args(p, precision, 0);
-    a.r_fixed = r;
+    a.m_pad = 0;  // the kernel reads r_sets + cur * m_pad = r
     a.g = g;
     a.pw_v = power_v;
     a.pw_lam = power_lam;
-    void* args[] = {&a};
+    const float* r_sets = r;
+    void* args[] = {&a, &r_sets};
     CK(cudaLaunchKernel(bwd_fixed_kernel(bwd_fmt(p, precision)), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0,
                         stream_of(p)));
+    void* pargs[] = {&a};
+    if (power_v) CK(cudaLaunchKernel(power_step_kernel(), dim3(1), dim3(kBwdThreads), pargs, 0, stream_of(p)));
     return IMRT_OK;
 }
 
@@ -779,7 +822,8 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
         TRY(build_sell(p, &p->sellq, p->opt.precision, row_ptr, col, val, len, mask_in, s));
     }
     // --- beamlet-major copy -------------------------------------------------
-    const int chunk_rows = 512;
+    int chunk_rows = kTChunkRows;
+    while ((int64_t)((p->m + chunk_rows - 1) / chunk_rows) * n * 4 > kTCountBytes && chunk_rows < p->m) chunk_rows *= 2;
     const int n_chunks = (p->m + chunk_rows - 1) / chunk_rows;
     Temp tcounts, tcl, tpad;
     int32_t* counts;
@@ -1333,6 +1377,25 @@ void imrt_default_options(imrt_options* o) {
 }
 
 const char* imrt_last_error(void) { return g_error.c_str(); }
+
+imrt_status imrt_trim_memory(size_t keep_bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error("no CUDA device: %s", cudaGetErrorString(e)), IMRT_ECUDA;
+    }
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool)
+        return set_error("no library memory pool on device %d: %s", dev, cudaGetErrorString(g_pool_error[dev])),
+               IMRT_ECUDA;
+    e = cudaMemPoolTrimTo(pool, keep_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error("cudaMemPoolTrimTo failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;
+    }
+    return IMRT_OK;
+}
 
 const char* imrt_version(void) { return "imrt-gb300 1.0 sm_103a"; }
 

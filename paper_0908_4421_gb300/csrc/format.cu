@@ -151,46 +151,58 @@ __device__ __forceinline__ void store_col(void* dst, int64_t k, int32_t c) {
     else static_cast<uint16_t*>(dst)[k] = (uint16_t)c;
 }
 
-// One thread per permuted row: writes the row into its lane of the slice layout
-// (C16: 16-bit beamlet indices with FP32 values).
+// One CTA per slice: thread o of the slice writes stored position o (group o / (32 GE), lane
+// (o / GE) % 32, place o % GE), so the writes are coalesced and a long row is spread over
+// the CTA instead of being walked by one thread (C16: 16-bit beamlet indices with FP32 values).
 template <int PREC, int GE, bool C16 = false>
-__global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                            const float* __restrict__ val, const int32_t* __restrict__ perm,
-                            const uint8_t* __restrict__ mask_in, int32_t m, int32_t m_pad,
-                            const int64_t* __restrict__ slice_off, const int32_t* __restrict__ slice_len,
-                            const float* __restrict__ inv_scale, void* sval, void* scol, uint8_t* mask_out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m_pad) return;
-    const int s = p / kSlice, lane = p % kSlice;
-    const int j = p < m ? perm[p] : -1;
-    const int64_t a = j >= 0 ? row_ptr[j] : 0;
-    const int len = j >= 0 ? (int)(row_ptr[j + 1] - a) : 0;
-    const int total = slice_len[s] * GE;
+__global__ void __launch_bounds__(256) k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                                   const float* __restrict__ val, const int32_t* __restrict__ perm,
+                                                   const uint8_t* __restrict__ mask_in, int32_t m, int32_t m_pad,
+                                                   const int64_t* __restrict__ slice_off,
+                                                   const int32_t* __restrict__ slice_len,
+                                                   const float* __restrict__ inv_scale, void* sval, void* scol,
+                                                   uint8_t* mask_out) {
+    __shared__ int64_t ra[kSlice];
+    __shared__ int32_t rl[kSlice];
+    const int s = blockIdx.x;
+    if (threadIdx.x < kSlice) {
+        const int p = s * kSlice + threadIdx.x;
+        const int j = p < m ? perm[p] : -1;
+        const int64_t a = j >= 0 ? row_ptr[j] : 0;
+        ra[threadIdx.x] = a;
+        rl[threadIdx.x] = j >= 0 ? (int)(row_ptr[j + 1] - a) : 0;
+        if (p < m_pad) mask_out[p] = j >= 0 ? mask_in[j] : (uint8_t)0;
+    }
+    __syncthreads();
     const int64_t base = slice_off[s];
-    for (int e = 0; e < total; ++e) {
-        const int64_t dst = base + ((int64_t)(e / GE) * kSlice + lane) * GE + (e % GE);
-        if (e < len) {
-            const int c = col[a + e];
-            const float v = inv_scale ? val[a + e] * inv_scale[c] : val[a + e];
-            store_val<PREC>(sval, dst, v);
-            store_col<PREC, C16>(scol, dst, c);
+    const int64_t total = (int64_t)slice_len[s] * GE * kSlice;
+    for (int64_t o = threadIdx.x; o < total; o += blockDim.x) {
+        const int within = (int)(o % (kSlice * GE));
+        const int lane = within / GE;
+        const int e = (int)(o / (kSlice * GE)) * GE + within % GE;
+        if (e < rl[lane]) {
+            const int64_t k = ra[lane] + e;
+            const int c = col[k];
+            const float v = inv_scale ? val[k] * inv_scale[c] : val[k];
+            store_val<PREC>(sval, base + o, v);
+            store_col<PREC, C16>(scol, base + o, c);
         } else {
-            store_val<PREC>(sval, dst, 0.0f);
-            store_col<PREC, C16>(scol, dst, 0);
+            store_val<PREC>(sval, base + o, 0.0f);
+            store_col<PREC, C16>(scol, base + o, 0);
         }
     }
-    mask_out[p] = j >= 0 ? mask_in[j] : (uint8_t)0;
 }
 
-// Transposition, pass 1: per chunk of permuted rows, how many entries each beamlet gets.
+// Transposition, pass 1: per chunk of voxel rows, how many entries each beamlet gets.
 __global__ void k_t_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int32_t m,
                           int32_t n, int32_t chunk_rows, int32_t* __restrict__ counts) {
     extern __shared__ int32_t hist[];
     for (int c = threadIdx.x; c < n; c += blockDim.x) hist[c] = 0;
     __syncthreads();
     const int j0 = blockIdx.x * chunk_rows, j1 = min(m, j0 + chunk_rows);
-    for (int j = j0; j < j1; ++j) {
-        for (int64_t k = row_ptr[j] + threadIdx.x; k < row_ptr[j + 1]; k += blockDim.x) atomicAdd(&hist[col[k]], 1);
+    if (j0 < j1) {  // the chunk's rows are consecutive, so their entries are one range
+        const int64_t k1 = row_ptr[j1];
+        for (int64_t k = row_ptr[j0] + threadIdx.x; k < k1; k += blockDim.x) atomicAdd(&hist[col[k]], 1);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += blockDim.x) counts[(size_t)blockIdx.x * n + c] = hist[c];
@@ -202,17 +214,22 @@ __global__ void k_t_colscan(int32_t* __restrict__ counts, int32_t n_chunks, int3
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     int64_t run = 0;
-    for (int ch = 0; ch < n_chunks; ++ch) {
-        const int v = counts[(size_t)ch * n + c];
-        counts[(size_t)ch * n + c] = (int32_t)run;
-        run += v;
+    for (int ch0 = 0; ch0 < n_chunks; ch0 += 8) {  // eight loads in flight per step
+        int v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = ch0 + t < n_chunks ? counts[(size_t)(ch0 + t) * n + c] : 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (ch0 + t < n_chunks) counts[(size_t)(ch0 + t) * n + c] = (int32_t)run;
+            run += v[t];
+        }
     }
     col_len[c] = run;
     padded[c] = (run + 3) & ~(int64_t)3;
 }
 
 // Pass 3: scatter. Rows of a chunk are visited in order, so each beamlet row
-// receives voxels in ascending (permuted) index; within one voxel row the
+// receives voxels in ascending (caller) index; within one voxel row the
 // columns are distinct, so the per-beamlet cursors need no atomics.
 __global__ void k_t_scatter(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const float* __restrict__ val, int32_t m, int32_t n, int32_t chunk_rows,
@@ -447,27 +464,27 @@ cudaError_t launch_sell_fill(int fmt, const int64_t* row_ptr, const int32_t* col
                              const int32_t* perm, const uint8_t* mask_in, int32_t m, int32_t m_pad,
                              const int64_t* slice_off, const int32_t* slice_len, const float* inv_scale,
                              void* sval, void* scol, uint8_t* mask_out, cudaStream_t stream) {
-    const int g = blocks_for(m_pad, 128);
+    const int g = m_pad / kSlice;  // one CTA per slice (m_pad is a whole number of slices)
     switch (fmt) {
         case kFmtF32C16:
-            k_sell_fill<IMRT_FP32, 8, true><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad,
+            k_sell_fill<IMRT_FP32, 8, true><<<g, 256, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad,
                                                                    slice_off, slice_len, nullptr, sval, scol,
                                                                    mask_out);
             break;
         case IMRT_FP32:
-            k_sell_fill<IMRT_FP32, 4><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
+            k_sell_fill<IMRT_FP32, 4><<<g, 256, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
                                                              slice_len, nullptr, sval, scol, mask_out);
             break;
         case IMRT_FP16:
-            k_sell_fill<IMRT_FP16, 8><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
+            k_sell_fill<IMRT_FP16, 8><<<g, 256, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
                                                              slice_len, inv_scale, sval, scol, mask_out);
             break;
         case IMRT_BF16:
-            k_sell_fill<IMRT_BF16, 8><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
+            k_sell_fill<IMRT_BF16, 8><<<g, 256, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad, slice_off,
                                                              slice_len, inv_scale, sval, scol, mask_out);
             break;
         case IMRT_FP8E4M3:
-            k_sell_fill<IMRT_FP8E4M3, 16><<<g, 128, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad,
+            k_sell_fill<IMRT_FP8E4M3, 16><<<g, 256, 0, stream>>>(row_ptr, col, val, perm, mask_in, m, m_pad,
                                                                  slice_off, slice_len, inv_scale, sval, scol,
                                                                  mask_out);
             break;

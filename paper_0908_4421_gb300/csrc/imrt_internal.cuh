@@ -39,6 +39,10 @@ constexpr int kBwdPerSm = 2048 / kBwdThreads;   // resident transposed CTAs per 
 // transposed, so group l holds the run's entries l, l + sg, ..., l + 7 sg and the t-th
 // entries of a warp's groups are sg consecutive voxels of the row.
 constexpr int kTqBlock = 256;
+// Beamlet-major build: voxel rows per counting-sort chunk (doubled while the chunk x beamlet
+// count table would exceed kTCountBytes).
+constexpr int kTChunkRows = 512;
+constexpr int64_t kTCountBytes = 256ll << 20;
 constexpr int kCtlThreads = 256;
 constexpr int kTmaMaxConsumers = 8;   // bulk-copy forward kernel: 1 producer + up to 8 consumer warps
 constexpr int kTmaThreads = 32 * (1 + kTmaMaxConsumers);
@@ -207,11 +211,10 @@ struct BwdArgs {
     int32_t H;
     const float* scale;       // n_pad or NULL
     DevState* st;
-    const float* r_fixed;     // NULL => r of the accepted set
     float* g;
     float* pw_v;              // step-size rule: power vector updated by the last CTA, or NULL
     double* pw_lam;           // its Rayleigh quotient v . (D^T C D v)
-    int32_t m_pad, guard;     // guard: skip unless st->need_grad
+    int32_t m_pad, guard;     // r = r_sets + cur * m_pad (0: a fixed r); guard: skip unless st->need_grad
 };
 
 // Sets the message imrt_last_error() returns on this thread (api.cu).
@@ -222,7 +225,8 @@ const void* fwd_kernel(int fmt, int k_trials);
 const void* fwd_tma_kernel(int fmt, int k_trials);
 int fwd_tma_stage_bytes(int fmt);
 const void* bwd_kernel(int fmt);        // fmt: a precision, or kFmtF32C16 (segmented FP32)
-const void* bwd_fixed_kernel(int fmt);
+const void* bwd_fixed_kernel(int fmt);  // the same kernel, launched with a fixed r (m_pad 0)
+const void* power_step_kernel();    // one CTA of kBwdThreads: the power-iteration update
 const void* init_kernel();
 const void* finish_kernel();
 size_t fwd_smem_bytes(int n_pad, int k_trials, int precision);

@@ -9,7 +9,7 @@
 //                Sec. 2.1), and in the epilogue evaluates the penalties of
 //                Eq. (1) per voxel: r_j = dF_j/dz_j and FP64 per-warp partials
 //                of G (Eq. (2)).
-//   k_transposed Sec. 2.3 "gradient calculation": g = D^T r (Eq. (3)-(4)) over
+//   k_transposed_cur Sec. 2.3 "gradient calculation": g = D^T r (Eq. (3)-(4)) over
 //                the beamlet-major copy, one CTA per beamlet row at a time,
 //                deterministic shuffle + shared-memory reduction, no atomics.
 //   controller   Sec. 2.2 steps 3-5 and Eq. (5), run by the last CTA of each
@@ -1448,7 +1448,8 @@ __device__ __forceinline__ bool transposed_any(const BwdArgs& a, const float* __
     else return transposed_rows_q<PREC>(a, r);
 }
 
-// Inside the solve: r of the accepted set, skipped when g is already current.
+// Inside the solve: r of the accepted set, skipped when g is already current. Outside the
+// solve (guard 0) the same kernel takes a fixed r: r_sets = r with m_pad = 0.
 template <int PREC>
 __global__ void __launch_bounds__(kBwdThreads, kBwdPerSm) k_transposed_cur(const BwdArgs a, const float* __restrict__ r_sets) {
     pdl_wait();  // the preceding forward pass (state, r) is complete
@@ -1462,7 +1463,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdPerSm) k_transposed_cur(const
     }
 }
 
-// One power-iteration step of the step-size rule on w = g (the last CTA, after every row):
+// One power-iteration step of the step-size rule on w = g (after every row):
 // lambda = v . w, then v = w / ||w|| (FP64 sums in a fixed order).
 __device__ void power_update(const BwdArgs& a) {
     __shared__ double red[2][kBwdThreads / 32];
@@ -1495,13 +1496,9 @@ __device__ void power_update(const BwdArgs& a) {
     }
 }
 
-// Outside the solve: r given explicitly (and, in the step-size rule, the power-iteration
-// update by the last CTA).
-template <int PREC>
-__global__ void __launch_bounds__(kBwdThreads, kBwdPerSm) k_transposed(const BwdArgs a) {
-    const bool last = transposed_any<PREC>(a, a.r_fixed);
-    if (last && a.pw_v) power_update(a);
-}
+// The step-size rule's power-iteration update after a fixed-r pass, in one CTA (kept out of
+// the pass: its FP64 registers would spill the pass's row loop at 32 registers a thread).
+__global__ void __launch_bounds__(kBwdThreads) k_power_step(const BwdArgs a) { power_update(a); }
 
 // x_1 (Initialization of Sec. 2.2) and the solver state.
 __global__ void __launch_bounds__(kCtlThreads) k_init(DevState* st, const SolveParams* sp, Vecs v) {
@@ -1641,16 +1638,9 @@ const void* bwd_kernel(int fmt) {
     }
 }
 
-const void* bwd_fixed_kernel(int fmt) {
-    switch (fmt) {
-        case IMRT_FP32: return (const void*)k_transposed<IMRT_FP32>;
-        case kFmtF32C16: return (const void*)k_transposed<kFmtF32C16>;
-        case IMRT_FP16: return (const void*)k_transposed<IMRT_FP16>;
-        case IMRT_BF16: return (const void*)k_transposed<IMRT_BF16>;
-        case IMRT_FP8E4M3: return (const void*)k_transposed<IMRT_FP8E4M3>;
-        default: return nullptr;
-    }
-}
+const void* power_step_kernel() { return (const void*)k_power_step; }
+
+const void* bwd_fixed_kernel(int fmt) { return bwd_kernel(fmt); }
 
 const void* init_kernel() { return (const void*)k_init; }
 const void* finish_kernel() { return (const void*)k_finish; }
