@@ -49,10 +49,14 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Fingerprint of the kernel, layout and schedule sources; comments and blank lines do not
+    count, so a profile stays valid across edits that cannot change the code."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "imrt_internal.cuh", "ptx.cuh", "format.cu", "api.cu"):  # kernels, layouts, schedule
-        with open(os.path.join(ROOT, "paper_0908_4421_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in ("kernels.cu", "imrt_internal.cuh", "ptx.cuh", "format.cu", "api.cu"):
+        with open(os.path.join(ROOT, "paper_0908_4421_gb300", "csrc", f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
@@ -133,12 +137,13 @@ def pinned(a: np.ndarray):
     return t.numpy(), t
 
 
-def cpu_oracle_sample(case, lambda0: float, iterations_full: int, budget_s: float = 20.0):
+def cpu_oracle_sample(case, lambda0: float, iterations_full: int, budget_s: float = 20.0, threads: int = 0):
     """Times the FP64 oracle on the full workload for a bounded number of iterations and scales it
-    to `iterations_full` iterations. Returns (estimated seconds, details)."""
+    to `iterations_full` iterations (all host cores unless `threads`). Returns (estimated seconds,
+    details)."""
     import oracle
     orc = oracle.get()
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     r1 = orc.solve(case, lambda0=lambda0, max_iter=1, threads=threads, trace=False)
     t_one = time.perf_counter() - t0
@@ -293,7 +298,7 @@ def main():
         fwd_avg_s * res.passes + bwd_avg_s * res.grad_passes, 1e-12) / 1e9
 
     # end to end through the C ABI with host buffers: create from pinned host CSR, solve, read x and z back
-    e2e_times = []
+    e2e_times, create_times = [], []
     h_rp, t_rp = pinned(case.row_ptr)
     h_col, t_col = pinned(case.col)
     h_val, t_val = pinned(case.val)
@@ -310,13 +315,16 @@ def main():
         t0 = time.perf_counter()
         with Plan(h_rp, h_col, h_val, h_mask, case.thresholds, case.weights, m=case.m, n=case.n,
                   options=e2e_opts) as p2:
+            dc = time.perf_counter() - t0  # plan_create returns once the plan is built
             r2 = p2.solve()
             p2.get_x(x_out)
             p2.dose(x_out, z_out)
         dt = time.perf_counter() - t0
         if i > 0:  # the first one also pays one-time CUDA module loading
             e2e_times.append(dt)
+            create_times.append(dc)
     e2e_s = max_over_ranks(statistics.mean(e2e_times)) if e2e_times else None
+    create_s = max_over_ranks(statistics.mean(create_times)) if create_times else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -325,6 +333,11 @@ def main():
                "sample": f"FP64 oracle, {det['iterations_timed']} iterations of the full workload "
                          f"({det['seconds_timed']} s), per-iteration time scaled to the GPU's "
                          f"{res.iterations} iterations plus set-up"}
+        # one core: the analogue of a sequential CPU implementation
+        est1, det1 = cpu_oracle_sample(case, lam0, res.iterations, budget_s=args.cpu_budget_s / 3, threads=1)
+        cpu["single_thread"] = {"value": est1, "unit": UNIT, "cores": 1,
+                                "sample": f"{det1['iterations_timed']} iterations ({det1['seconds_timed']} s), "
+                                          f"scaled the same way"}
 
     # the reduced-precision forms (FP16 / BF16 / FP8-e4m3 storage, FP32 accumulation, FP64
     # objective and Armijo test, FP32 polish): time-to-plan, bandwidth, errors vs the FP64 oracle
@@ -404,7 +417,7 @@ def main():
         "forms": forms,
         "e2e": None if e2e_s is None else {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "includes": "plan_create from pinned host CSR (copy, layouts, step-size rule), plan_solve, "
-                            "plan_get_x and plan_dose to host"},
+                            "plan_get_x and plan_dose to host", "plan_create_s": create_s},
         "gpu_launches": int(res.launches) * args.steps,
         "clocks": clocks.summary(),
     }

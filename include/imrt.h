@@ -282,8 +282,9 @@ void plan_destroy(imrt_plan* plan);
 /* Device memory of plans comes from one stream-ordered pool per device that the library
  * owns and that keeps freed memory for later plans, so creating plans one after another
  * maps no new memory. This hands the cached memory of the current device's pool back to
- * the system down to keep_bytes (0: all that no live plan holds). Live plans are not
- * affected. Returns IMRT_ECUDA if no device is usable or the device has no library pool
+ * the system down to keep_bytes (0: all that no live plan holds). It synchronises the
+ * device first, so that memory of plans destroyed on any stream is included. Live plans
+ * are not affected. Returns IMRT_ECUDA if no device is usable or the device has no library pool
  * (plans then allocate from the device's default pool). */
 imrt_status imrt_trim_memory(size_t keep_bytes);
 

@@ -636,7 +636,7 @@ const SellCopy& copy_of(const imrt_plan* p, int precision) {
 }
 
 // Stand-alone evaluation of the forward kernel (no step) with the copy of D at `precision`:
-// z, r (permuted) and the objective partials (summed into *G_out when given).
+// z (permuted), r (caller's voxel order) and the objective partials (summed into *G_out when given).
 imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, float* r_dst, double* G_out,
                      int precision = IMRT_FP32) {
     FwdShape* sh = nullptr;
@@ -1389,7 +1389,9 @@ imrt_status imrt_trim_memory(size_t keep_bytes) {
     if (!pool)
         return set_error("no library memory pool on device %d: %s", dev, cudaGetErrorString(g_pool_error[dev])),
                IMRT_ECUDA;
-    e = cudaMemPoolTrimTo(pool, keep_bytes);
+    // frees still pending in stream order keep their memory in the pool: complete them first
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, keep_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error("cudaMemPoolTrimTo failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;

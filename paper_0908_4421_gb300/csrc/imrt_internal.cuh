@@ -7,11 +7,13 @@
 //   L groups stores, for group k and lane l, GE consecutive entries of row
 //   (32 s + l) at entry offset slice_off[s] + (32 k + l) * GE, so one warp-wide
 //   16-byte load per array reads 512 contiguous bytes. Padding entries hold
-//   value 0 and column 0. All per-voxel vectors (z, r, mask) live in this
-//   permuted order; the ABI un-permutes on the way out.
+//   value 0 and column 0. The per-voxel vectors z and mask live in this
+//   permuted order (the ABI un-permutes on the way out); r is stored in the
+//   caller's voxel order, which the beamlet-major copies index.
 //   Beamlet-major copy of D: one row per beamlet, voxel indices in the
-//   permuted order (ascending), each row padded to a multiple of 4 entries so
-//   every row starts 16-byte aligned.
+//   caller's order (ascending), each row padded to a multiple of 4 entries so
+//   every row starts 16-byte aligned; the segmented copies cut from it are
+//   described at kTqBlock.
 #pragma once
 
 #include <cuda_runtime.h>
