@@ -589,6 +589,16 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.stages = sh.stages;
     a.mask = p->mask;
     a.r_index = p->perm;
+    if (p->t_H > 0 && p->bwd_order) {
+        a.nx_order = p->bwd_order;
+        a.nx_seg = p->t_seg;
+        a.nx_val = c.precision != IMRT_FP32 ? (const void*)p->t_valq : (const void*)p->t_vals;
+        a.nx_lo = p->t_lo;
+        a.nx_H = p->t_H;
+        a.nx_n = p->n;
+        a.nx_vb = (int32_t)elem_bytes(c.precision);
+        a.nx_per_cta = (p->bwd_grid + sh.grid - 1) / std::max(sh.grid, 1);
+    }
     a.scale = c.precision == IMRT_FP32 ? nullptr : p->scale;
     a.vt = p->vt_on ? p->vt_p : nullptr;
     a.vtm = p->vt_on ? p->vtm_p : nullptr;

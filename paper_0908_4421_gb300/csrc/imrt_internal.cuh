@@ -196,6 +196,13 @@ struct FwdArgs {
     const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x
     float* z_dst;        // kFwdEval / kFwdPower; NULL => accepted set
     float* r_dst;
+    // the transposed pass that follows (segmented copies), for an L2 prefetch of its first rows
+    // at the end of this pass; nx_order NULL: none
+    const int32_t* nx_order;
+    const int64_t* nx_seg;
+    const void* nx_val;
+    const uint16_t* nx_lo;
+    int32_t nx_H, nx_n, nx_vb, nx_per_cta;
 };
 
 struct BwdArgs {

@@ -220,6 +220,9 @@ __device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __res
 // next stage are issued before the current stage is used, so loads stay in flight while the
 // lane gathers x and accumulates. Otherwise: rounds of IMRT_FWD_UNROLL groups, all loads of
 // a round before any use. The last groups are guarded (the guard is uniform across the warp).
+#ifndef IMRT_BWD_PREFETCH_KB
+#define IMRT_BWD_PREFETCH_KB 64  // forward tail: L2 prefetch (KB per row) of the next transposed pass's first rows
+#endif
 #ifndef IMRT_FWD_PIPE
 #define IMRT_FWD_PIPE 1  // 1: software-pipelined rounds (the next round's loads before this round's use)
 #endif
@@ -853,6 +856,21 @@ __global__ void __launch_bounds__(kFwdThreads,
             u = __shfl_sync(0xffffffffu, u_next, 0);
         }
     }
+#if IMRT_BWD_PREFETCH_KB > 0
+    // this warp is done with D: hint the start of one first-wave row of the transposed pass
+    // that follows into L2, while the other warps and CTAs finish (D is constant)
+    if (a.nx_order && lane == 0 && wib < a.nx_per_cta) {
+        const int idx = (int)blockIdx.x * a.nx_per_cta + wib;
+        if (idx < a.nx_n) {
+            const int i = a.nx_order[idx];
+            const int64_t e0 = a.nx_seg[(int64_t)i * a.nx_H], e1 = a.nx_seg[(int64_t)i * a.nx_H + a.nx_H];
+            const int64_t cap = ((int64_t)IMRT_BWD_PREFETCH_KB * 1024 / (a.nx_vb + 2)) & ~(int64_t)7;
+            const int64_t n_e = e1 - e0 < cap ? e1 - e0 : cap;
+            prefetch_l2(static_cast<const char*>(a.nx_val) + e0 * a.nx_vb, n_e * a.nx_vb);
+            prefetch_l2(a.nx_lo + e0, n_e * 2);
+        }
+    }
+#endif
     // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
     // (every write the controller reads was fenced by its writer)
     __shared__ int is_last;

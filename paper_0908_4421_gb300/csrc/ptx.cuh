@@ -70,6 +70,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // programmatically has completed and its writes are visible (at once when the launch has no
 // such dependency); `pdl_launch_dependents` lets the next grid start launching.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// A hint that brings [p, p + bytes) into L2; there is no completion to wait for. The bulk
+// prefetch needs a 16-byte aligned start and a multiple of 16 bytes, so the start is rounded
+// up and the length down (a hint may skip a few bytes; FP8 rows start on 8-byte boundaries).
+// Issued in 16 KB pieces.
+__device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p), a16 = (a + 15) & ~(uintptr_t)15;
+    bytes -= (int64_t)(a16 - a);
+    const char* c = reinterpret_cast<const char*>(a16);
+    for (int64_t o = 0; o + 16 <= bytes; o += 16384) {
+        const uint32_t b = (uint32_t)((bytes - o < 16384 ? bytes - o : 16384) & ~(int64_t)15);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(b) : "memory");
+    }
+}
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
