@@ -229,11 +229,11 @@ cudaMemPool_t device_pool(int dev) {
     if (dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(g_pool_mu);
     if (!g_pool[dev]) {
+        if (g_pool_error[dev] != cudaSuccess) return nullptr;  // creation failed before
         cudaMemPoolProps props{};
         props.allocType = cudaMemAllocationTypePinned;
         props.location.type = cudaMemLocationTypeDevice;
         props.location.id = dev;
-        if (g_pool_error[dev] != cudaSuccess) return nullptr;
         cudaMemPool_t pool = nullptr;
         cudaError_t e = cudaMemPoolCreate(&pool, &props);
         uint64_t keep = UINT64_MAX;
@@ -1401,7 +1401,11 @@ imrt_status imrt_trim_memory(size_t keep_bytes) {
                IMRT_ECUDA;
     // frees still pending in stream order keep their memory in the pool: complete them first
     e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, keep_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error("cudaDeviceSynchronize before trimming failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;
+    }
+    e = cudaMemPoolTrimTo(pool, keep_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error("cudaMemPoolTrimTo failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;

@@ -9,9 +9,11 @@
 //                Sec. 2.1), and in the epilogue evaluates the penalties of
 //                Eq. (1) per voxel: r_j = dF_j/dz_j and FP64 per-warp partials
 //                of G (Eq. (2)).
-//   k_transposed_cur Sec. 2.3 "gradient calculation": g = D^T r (Eq. (3)-(4)) over
-//                the beamlet-major copy, one CTA per beamlet row at a time,
-//                deterministic shuffle + shared-memory reduction, no atomics.
+//   k_transposed_cur  Sec. 2.3 "gradient calculation": g = D^T r (Eq. (3)-(4))
+//                over the beamlet-major copy, one CTA per beamlet row at a time,
+//                deterministic shuffle + shared-memory reduction, no atomics
+//                (inside solves, and with a fixed r for the step-size rule).
+//   k_power_step the step-size rule's power-iteration update (one CTA).
 //   controller   Sec. 2.2 steps 3-5 and Eq. (5), run by the last CTA of each
 //                forward launch inside a solve: FP64 reduction of the partials
 //                in a fixed order, the Armijo acceptance test, lambda / alpha,
@@ -39,6 +41,9 @@ namespace imrt {
 #endif
 #ifndef IMRT_FWD_UNROLL
 #define IMRT_FWD_UNROLL 8  // groups in flight per lane (FP8: half as many, each is 48 bytes)
+#endif
+#ifndef IMRT_BWD_PREFETCH_KB
+#define IMRT_BWD_PREFETCH_KB 64  // forward tail: L2 prefetch (KB per row) of the next transposed pass's first rows
 #endif
 
 // ---------------------------------------------------------------------------
@@ -220,9 +225,6 @@ __device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __res
 // next stage are issued before the current stage is used, so loads stay in flight while the
 // lane gathers x and accumulates. Otherwise: rounds of IMRT_FWD_UNROLL groups, all loads of
 // a round before any use. The last groups are guarded (the guard is uniform across the warp).
-#ifndef IMRT_BWD_PREFETCH_KB
-#define IMRT_BWD_PREFETCH_KB 64  // forward tail: L2 prefetch (KB per row) of the next transposed pass's first rows
-#endif
 #ifndef IMRT_FWD_PIPE
 #define IMRT_FWD_PIPE 1  // 1: software-pipelined rounds (the next round's loads before this round's use)
 #endif
