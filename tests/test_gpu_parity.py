@@ -288,6 +288,31 @@ def test_reduced_precision_eval(orc, tiny, prec, dose_tol, obj_tol, variant):
     assert np.linalg.norm(g - g_ref) <= 2 * dose_tol * np.linalg.norm(S)
 
 
+@pytest.fixture(scope="module")
+def multi_segment(orc):
+    case = phantom.random_case(6, m=200_000, n=50, density=0.01, n_structures=3, empty_rows=1000, long_rows=3)
+    x = np.random.Generator(np.random.PCG64(11)).uniform(0, 2, case.n).astype(np.float32)
+    return case, x, orc.eval(case, x.astype(np.float64))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("prec,dose_tol,obj_tol", [(L.FP32, DOSE_RTOL, OBJ_RTOL)] + REDUCED)
+def test_multi_segment_eval(multi_segment, prec, dose_tol, obj_tol, variant):
+    """200,000 voxels: the beamlet-major copies hold four segments of 65,536 voxels, so segment
+    runs cut the 256-entry blocks of the transposed order into pieces; ragged and empty rows.
+    The gradient against the FP64 oracle, entry by entry for FP32."""
+    case, x, (G_ref, z_ref, r_ref, g_ref) = multi_segment
+    with Plan.from_case(case, Options(precision=prec, kernel_variant=variant)) as plan:
+        G, z, g = plan.eval(x)
+    assert rel(z, z_ref) <= dose_tol
+    assert abs(G - G_ref) <= obj_tol * abs(G_ref)
+    if prec == L.FP32:
+        np.testing.assert_allclose(g, g_ref, rtol=1e-4, atol=1e-5 * np.abs(g_ref).max())
+    else:
+        S = gradient_scale(case, z_ref, r_ref)
+        assert np.linalg.norm(g - g_ref) <= 2 * dose_tol * np.linalg.norm(S)
+
+
 @pytest.mark.parametrize("prec,obj_tol", [(L.FP16, 1e-3), (L.BF16, 1e-3), (L.FP8E4M3, 1e-2)])
 def test_reduced_precision_solve_with_polish(orc, tiny, prec, obj_tol):
     """Reduced-precision iterations, then the last polish_iter iterations on the FP32 copy:
