@@ -589,7 +589,10 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.stages = sh.stages;
     a.mask = p->mask;
     a.r_index = p->perm;
-    if (p->t_H > 0 && p->bwd_order) {
+    // the next transposed pass's L2 prefetch pays only when its copy of D is far larger than L2
+    // could hold anyway (small plans stay L2-resident, and the prefetch would delay the ticket)
+    const int64_t tq_bytes = p->tq_entries * ((int64_t)elem_bytes(c.precision) + 2);
+    if (p->t_H > 0 && p->bwd_order && tq_bytes > kPrefetchMinBytes) {
         a.nx_order = p->bwd_order;
         a.nx_seg = p->t_seg;
         a.nx_val = c.precision != IMRT_FP32 ? (const void*)p->t_valq : (const void*)p->t_vals;

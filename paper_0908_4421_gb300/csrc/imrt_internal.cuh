@@ -41,6 +41,7 @@ constexpr int kBwdPerSm = 2048 / kBwdThreads;   // resident transposed CTAs per 
 // transposed, so group l holds the run's entries l, l + sg, ..., l + 7 sg and the t-th
 // entries of a warp's groups are sg consecutive voxels of the row.
 constexpr int kTqBlock = 256;
+constexpr int64_t kPrefetchMinBytes = 64ll << 20;  // beamlet-major copies above this get the L2 prefetch
 // Beamlet-major build: voxel rows per counting-sort chunk (doubled while the chunk x beamlet
 // count table would exceed kTCountBytes).
 constexpr int kTChunkRows = 512;
