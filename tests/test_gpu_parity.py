@@ -313,6 +313,31 @@ def test_multi_segment_eval(multi_segment, prec, dose_tol, obj_tol, variant):
         assert np.linalg.norm(g - g_ref) <= 2 * dose_tol * np.linalg.norm(S)
 
 
+@pytest.fixture(scope="module")
+def many_segments(orc):
+    case = phantom.random_case(8, m=1_100_000, n=24, density=0.002, n_structures=2, empty_rows=1000)
+    x = np.random.Generator(np.random.PCG64(12)).uniform(0, 2, case.n).astype(np.float32)
+    return case, x, orc.eval(case, x.astype(np.float64))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_more_than_16_segments(many_segments, variant):
+    """1,100,000 voxels (17 segments of 65,536): the plan keeps the int32-index beamlet-major
+    copy and its transposed loop; z, G and g against the FP64 oracle, g entry by entry."""
+    case, x, (G_ref, z_ref, r_ref, g_ref) = many_segments
+    with Plan.from_case(case, Options(kernel_variant=variant)) as plan:
+        G, z, g = plan.eval(x)
+    assert rel(z, z_ref) <= DOSE_RTOL
+    assert abs(G - G_ref) <= OBJ_RTOL * abs(G_ref)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-4, atol=1e-5 * np.abs(g_ref).max())
+
+
+def test_reduced_precision_refuses_more_than_16_segments(many_segments):
+    case = many_segments[0]
+    with pytest.raises(L.ImrtError, match="at most 1048576 voxels"):
+        Plan.from_case(case, Options(precision=L.FP16))
+
+
 @pytest.mark.parametrize("prec,obj_tol", [(L.FP16, 1e-3), (L.BF16, 1e-3), (L.FP8E4M3, 1e-2)])
 def test_reduced_precision_solve_with_polish(orc, tiny, prec, obj_tol):
     """Reduced-precision iterations, then the last polish_iter iterations on the FP32 copy:
