@@ -165,7 +165,9 @@ void imrt_default_options(imrt_options* opt);
  *   out         receives the plan; NULL on failure.
  * The caller may free every input when this returns.
  * Errors: IMRT_EINVAL (bad sizes or CSR structure, bad options),
- * IMRT_EUNSUPPORTED (n above the shared-memory limit), IMRT_ENOMEM, IMRT_ECUDA.
+ * IMRT_EUNSUPPORTED (size limits: the forward pass stages x, and g in a solve, in shared
+ * memory, about 8 * n * k_trials bytes, so n is limited to about 28,000 beamlets at
+ * k_trials = 1; reduced precision needs m <= 1,048,576 voxels), IMRT_ENOMEM, IMRT_ECUDA.
  */
 imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
                         const float* thresholds, const float* weights, const imrt_options* opt,
