@@ -404,7 +404,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "traffic": traffic, "kernel": dominant,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "algorithmic_bytes_per_launch": dom_bytes},
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     **({"traffic_note": "the forward pass's DRAM bytes include its L2 prefetch of the first "
+                                         "rows of the transposed pass that follows (up to 64 KB a row of the "
+                                         "first wave)"} if dominant == "k_forward" and traffic else {})},
         "kernels": {"k_forward": {"avg_ms": fwd_avg_s * 1e3, "gbs": fwd_gbs, "bytes": fwd_bytes,
                                   "launches_timed": fwd_n},
                     "k_transposed": {"avg_ms": bwd_avg_s * 1e3, "gbs": bwd_gbs, "bytes": bwd_bytes,
