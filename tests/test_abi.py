@@ -59,3 +59,13 @@ def test_struct_layouts_match_header(tmp_path):
         for f, _ in st._fields_:
             expect.append(f"{st.__name__} {f} {getattr(st, f).offset}")
     assert [l for l in out if l] == expect
+
+
+def test_every_declaration_is_documented():
+    """Each function the header declares is preceded by its comment (arguments, layout,
+    ownership and errors are stated there)."""
+    text = open(os.path.join(ROOT, "include", "imrt.h")).read()
+    decls = list(re.finditer(r"^(?:imrt_status|void|const char\*|int32_t)\s+(\w+)\s*\(", text, re.M))
+    assert {m.group(1) for m in decls} == declared_functions()
+    undocumented = [m.group(1) for m in decls if not text[:m.start()].rstrip().endswith("*/")]
+    assert not undocumented, undocumented
