@@ -39,3 +39,19 @@ def test_profiled_traffic_only_for_the_current_source(tmp_path, monkeypatch):
     assert bench.profiled_traffic("k_forward", "w") == 12345
     prof.write_text("source_sha256_16: 0123456789abcdef\ntraffic_bytes_per_launch: 12345\n")
     assert bench.profiled_traffic("k_forward", "w") is None  # stale
+
+
+def test_clock_summary_reports_throttle_reasons():
+    """nvidia-smi rows (clocks, power, event-reason flags): median SM clock, max clock, and every
+    reason seen Active; malformed lines are skipped."""
+    cs = bench.ClockSampler(0)
+    cs.lines = ["2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+                "1980, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+                "2010, 2070, 1400.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+                "[N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbage", ""]
+    s = cs.summary()
+    assert (s["samples"], s["sm_mhz"], s["sm_max_mhz"]) == (3, 2010.0, 2070.0)
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"],
+                                               "samples": 0}
