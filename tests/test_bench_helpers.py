@@ -55,3 +55,14 @@ def test_clock_summary_reports_throttle_reasons():
     assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"],
                                                "samples": 0}
+
+
+def test_cpu_oracle_sample_scales_a_bounded_sample():
+    """The CPU baseline times a few oracle iterations and scales them to the full count."""
+    from paper_0908_4421_gb300 import phantom
+    import oracle
+    case = phantom.make_case(phantom.TINY_5MM_5BEAM)
+    lam0 = oracle.get().lambda0_rule(case, threads=1)
+    est, det = bench.cpu_oracle_sample(case, lam0, iterations_full=200, budget_s=0.5, threads=1)
+    assert det["cores"] == 1 and det["iterations_timed"] >= 2
+    assert est == det["setup_s"] + det["per_iteration_s"] * 200 and est > 0
