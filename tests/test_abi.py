@@ -69,3 +69,26 @@ def test_every_declaration_is_documented():
     assert {m.group(1) for m in decls} == declared_functions()
     undocumented = [m.group(1) for m in decls if not text[:m.start()].rstrip().endswith("*/")]
     assert not undocumented, undocumented
+
+
+def test_python_options_mirror_the_c_defaults_and_fields():
+    """Options (Python) and imrt_options (C) have the same fields and the same defaults, and
+    Result covers every field of imrt_result."""
+    import dataclasses
+
+    from paper_0908_4421_gb300.api import Options, Result
+    lib = _lib.load(cuda_build.build())
+    c = _lib.imrt_options()
+    lib.imrt_default_options(ctypes.byref(c))
+    c_fields = {name for name, _ in _lib.imrt_options._fields_}
+    py = Options()
+    assert {f.name for f in dataclasses.fields(Options)} == c_fields
+    for f in dataclasses.fields(Options):  # a NULL pointer (the stream) reads back as None
+        assert getattr(py, f.name) == (getattr(c, f.name) or 0), f.name
+    custom = Options(eps=0.25, alpha=3.0, lambda0=0.5, delta=1e-3, max_iter=7, max_backtracks=9, x_init=2,
+                     precision=_lib.FP16, k_trials=4, mode=_lib.MODE_HOST, profile=1, trace=2, polish_iter=5,
+                     kernel_variant=2, timeout_ms=12.5, stream=1234)
+    back = custom.to_c()
+    for f in dataclasses.fields(Options):
+        assert getattr(back, f.name) == getattr(custom, f.name), f.name
+    assert {f.name for f in dataclasses.fields(Result)} == {name for name, _ in _lib.imrt_result._fields_}
