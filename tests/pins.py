@@ -375,3 +375,65 @@ def pin_sufficient_decrease(orc, case=None):
         case = phantom.random_case(12, m=60, n=10, density=0.5, n_structures=2)
     lam0 = 16 * orc.lambda0_rule(case)
     pin_invariants(orc, case, lambda0=lam0, max_iter=30, eps=0.45)
+
+
+def pin_kkt_hand(orc):
+    """The KKT residual ||x - max(0, x - g)||_inf / max(1, ||g(x_1)||_inf) at a given x_1, worked by hand.
+
+    D = I, one structure with T_under = T_over = 2 and weights 3 on its 3 voxels: c = 1, G = sum (x - 2)^2,
+    g = 2 (x - 2). With max_iter = 0 the solve stops at x_1 = (0, 1, 5): g = (-4, -2, 6), the projected
+    step residuals are |0 - 4| = 4, |1 - 3| = 2 and |5 - 0| = 5, and ||g(x_1)||_inf = 6, so KKT = 5 / 6.
+    """
+    from oracle import STOP_MAXITER
+    case = _case_from_dense(np.eye(3), np.ones(3, np.uint8), [(2.0, 2.0)], [(3.0, 3.0)])
+    res = orc.solve(case, lambda0=0.1, x_init=2, x0=np.array([0.0, 1.0, 5.0]), max_iter=0)
+    assert res.status == 0 and res.stop_reason == STOP_MAXITER and res.iterations == 0
+    assert abs(res.kkt - 5.0 / 6.0) <= 1e-15, res.kkt
+    # below the unit floor of the denominator: x_1 = (1.5, 2, 2.25), g = (-1, 0, 0.5), residuals 1, 0, 0.5
+    res = orc.solve(case, lambda0=0.1, x_init=2, x0=np.array([1.5, 2.0, 2.25]), max_iter=0)
+    assert abs(res.kkt - 1.0) <= 1e-15, res.kkt
+
+
+def pin_kkt_dense(orc, seed=14):
+    """The reported KKT residual at a non-converged iterate equals the definition evaluated with the
+    test-side dense gradient at the returned x and at x_1."""
+    case = phantom.random_case(seed, m=70, n=9, density=0.5, n_structures=3)
+    x1 = orc.initial_point(case, 0)
+    g1 = dense_objective(case, x1)[1]
+    for iters in (1, 4):
+        res = orc.solve(case, lambda0=orc.lambda0_rule(case), delta=0.0, max_iter=iters)
+        assert res.status == 0 and res.iterations == iters
+        g = dense_objective(case, res.x)[1]
+        kkt = float(np.max(np.abs(res.x - np.maximum(0.0, res.x - g)))) / max(1.0, float(np.max(np.abs(g1))))
+        assert kkt > 1e-3, kkt  # far from stationary: the pin has something to check
+        assert abs(res.kkt - kkt) <= 1e-12 * kkt, (res.kkt, kkt)
+
+
+def pin_stop_rule(orc):
+    """Step 5's relative-change test on a case whose objective sequence is known in closed form.
+
+    One beamlet reaches two voxels (D = [1; 1]) with exact-fit targets 1.5 and 2.5 (one structure each,
+    unit weights): G(x) = 2 (x - 2)^2 + 1/2 and g = 4 (x - 2). The step lambda = 1/8 halves e = x - 2 and
+    satisfies Eq. (5) at once (decrease 1.5 e^2 against (eps / lambda) e^2 / 4), so from x_1 = 2 + 1024
+    the accepted step k leaves e_k = 2^(10 - k) behind and changes G by 1.5 e_k^2 to
+    G_(k+1) = 1/2 + e_k^2 / 2. With delta = 0.5 the rule |dG| / G_new < delta first holds at e^2 = 1/16
+    (0.176), after 13 accepted steps; |dG| / G_old (0.15 at e^2 = 1/4) or |dG| alone (0.375) would stop
+    one step earlier.
+    """
+    from oracle import STOP_REL
+    case = _case_from_dense(np.ones((2, 1)), np.array([1, 2], np.uint8), [(1.5, 1.5), (2.5, 2.5)],
+                            [(1.0, 1.0), (1.0, 1.0)])
+    res = orc.solve(case, lambda0=0.125, x_init=2, x0=np.array([1026.0]), delta=0.5, max_iter=100)
+    assert res.status == 0 and res.stop_reason == STOP_REL, (res.status, res.stop_reason)
+    assert res.iterations == 13, res.iterations
+    assert res.backtracks == 0
+    e = 1024.0 / 2.0 ** np.arange(14)
+    np.testing.assert_array_equal(res.G, 0.5 + 2.0 * e ** 2)
+    assert abs(res.rel_change - (1.5 / 16.0) / (0.5 + 0.5 / 16.0)) <= 1e-15  # the last step, e^2 = 1/16
+    np.testing.assert_array_equal(res.x, [2.0 + e[13]])
+    # a delta below every relative change runs to the iteration cap instead
+    res2 = orc.solve(case, lambda0=0.125, x_init=2, x0=np.array([1026.0]), delta=1e-300, max_iter=20)
+    assert res2.stop_reason != STOP_REL and res2.iterations == 20
+
+
+ALL_PINS = ALL_PINS + ("pin_kkt_hand", "pin_kkt_dense", "pin_stop_rule")

@@ -28,6 +28,10 @@ MUTANTS = {
     "voxel_target_under_sign": ("d -= 2.0 * vcu * e;", "d += 2.0 * vcu * e;"),
     "voxel_target_no_normalise": ("*co = P->m > 0 ? P->vt_wo / (P->vt_normalise ? (double)P->m : 1.0) : 0.0;",
                                   "*co = P->m > 0 ? P->vt_wo : 0.0;"),
+    "kkt_zero": ("return worst / (g1_inf > 1.0 ? g1_inf : 1.0);", "return 0.0 * worst * g1_inf;"),
+    "kkt_no_projection": ("double e = fabs(x[i] - p);", "double e = fabs(g[i]);"),
+    "rel_denominator": ("rel = Gt > 0.0 ? fabs(Gt - G) / Gt : 0.0;", "rel = G > 0.0 ? fabs(Gt - G) / G : 0.0;"),
+    "rel_absolute": ("rel = Gt > 0.0 ? fabs(Gt - G) / Gt : 0.0;", "rel = fabs(Gt - G);"),
 }
 
 
