@@ -66,7 +66,8 @@ typedef enum {
 } imrt_stop;
 
 typedef enum {
-    IMRT_FP32 = 0,    /* FP32 values, int32 indices (the paper's CSR precision, Sec. 3.2) */
+    IMRT_FP32 = 0,    /* FP32 values from int32 input indices (the paper's CSR precision, Sec. 3.2); stored
+                         with 16-bit beamlet indices when n <= 65,536 */
     IMRT_FP16 = 1,    /* FP16 values scaled per beamlet (FP32 scale), 16-bit beamlet indices */
     IMRT_BF16 = 2,    /* BF16 values scaled per beamlet */
     IMRT_FP8E4M3 = 3  /* FP8 e4m3 values scaled per beamlet */
@@ -216,7 +217,7 @@ imrt_status plan_solve(imrt_plan* plan, const float* x0, imrt_result* res);
 imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float* const* x0s, imrt_result* results,
                              void* stream);
 
-/* z = D x (Sec. 2.1) with the FP32 copy of D./* z = D x (Sec. 2.1) with the FP32 copy of D. x: n (host or device), NULL => the plan's current x.
+/* z = D x (Sec. 2.1) with the FP32 copy of D. x: n (host or device), NULL => the plan's current x.
    z_out: m (host or device). */
 imrt_status plan_dose(imrt_plan* plan, const float* x, float* z_out);
 
@@ -253,26 +254,34 @@ imrt_status plan_cancel(imrt_plan* plan);
 /*
  * Dose and objective at x straight from a device CSR, without allocating any
  * memory. The paper has no counterpart: this entry point serves callers that
- * cannot allocate device memory when they evaluate a plan, such as code that is
- * capturing a stream into a CUDA graph (cudaMalloc is not allowed during a
- * global-mode capture), treatment-delivery controllers whose device memory is
- * reserved once at start-up, or host frameworks that own every allocation. It
- * calls no cudaMalloc, cudaFree or allocating library routine; its scratch is a
- * file-scope device array of about 129 KiB that every GPU loading the library
- * holds until the process exits.
- *   D           voxel-major CSR, device pointers (D->on_device must be 1);
- *               m <= 16,777,216 voxels, else IMRT_EUNSUPPORTED.
+ * cannot allocate device memory when they evaluate a plan, such as
+ * treatment-delivery controllers whose device memory is reserved once at start-up
+ * and may not grow, host frameworks that give the library a fixed budget and own
+ * every allocation, or processes in which another component holds nearly all of
+ * the device's memory. It calls no cudaMalloc, cudaFree or allocating library
+ * routine; its scratch is a file-scope device array of about 129 KiB that every
+ * GPU loading the library holds until the process exits.
+ *   D           voxel-major CSR, device pointers of the current device
+ *               (D->on_device must be 1); m <= 16,777,216 voxels, else
+ *               IMRT_EUNSUPPORTED.
  *   structures  m bytes, device: bit s set => voxel in structure s.
- *   n_structures, thresholds, weights: as for plan_create (host arrays).
+ *   n_structures, thresholds, weights: as for plan_create (host arrays; weights
+ *               finite and >= 0, thresholds finite or NaN).
  *   x           n beamlet intensities, device.
  *   z_out       m floats, device, in the caller's row order; NULL to skip.
  *   G_out       the FP64 objective, host.
- *   stream      cudaStream_t; the call returns after its work finished.
+ *   stream      cudaStream_t. The call waits for its stream and copies G into
+ *               G_out before it returns.
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call clears the parts of the scratch that must start at zero. All calls
- * on one device share the scratch: calls whose work overlaps on the GPU (other
- * streams or host threads) race and must be serialised by the caller.
+ * (cudaGetSymbolAddress). Every call clears the parts of the scratch that must
+ * start at zero. All calls on one device share the scratch: calls whose work
+ * overlaps on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.
+ * Errors: IMRT_EINVAL for NULL or host pointers, pointers of another device, bad
+ * weights or thresholds, and a malformed CSR (row_ptr[0] != 0, row_ptr[m] != nnz,
+ * decreasing offsets, beamlet indices outside [0, n)); the kernel reads nothing
+ * outside the arrays, skipping such rows and entries, and z_out and G are then
+ * not meaningful. IMRT_EUNSUPPORTED beyond the size limit, IMRT_ECUDA.
  */
 imrt_status imrt_eval_csr_noalloc(const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
                                   const float* thresholds, const float* weights, const float* x, float* z_out,

@@ -1,26 +1,30 @@
 // Allocation-free evaluation of the dose and the objective from a caller's device CSR.
 //
 // Some callers cannot allocate device memory at the moment they need an evaluation:
-// code that is capturing a stream into a CUDA graph (cudaMalloc is not allowed while a
-// global-mode capture is active), controllers in a treatment-delivery loop whose device
-// memory is reserved once at start-up and may not grow afterwards, and host frameworks
-// that give this library a fixed device budget and own every allocation themselves.
-// For them, imrt_eval_csr_noalloc keeps its scratch (per-block objective partials,
-// structure voxel counts, a completion counter and the final objective) in one
-// file-scope __device__ array instead of asking the runtime for memory. The caller
-// passes the inputs and the output buffers.
+// controllers in a treatment-delivery loop whose device memory is reserved once at
+// start-up and may not grow afterwards, host frameworks that give this library a fixed
+// device budget and own every allocation themselves, and processes in which another
+// component already holds nearly all of the device's memory. For them,
+// imrt_eval_csr_noalloc keeps its scratch (per-block objective partials, structure voxel
+// counts, a completion counter, an input-error flag and the final objective) in one
+// file-scope __device__ array instead of asking the runtime for memory. The caller passes
+// the inputs and the output buffers.
 //
 // The array is created when the library is loaded and every GPU that loads the library
 // holds it (about 129 KiB) until the process exits. All calls on a device share it and
 // it keeps the last call's contents: each call clears the parts that must start at zero,
 // and calls whose work overlaps on the GPU (different streams, or different host
-// threads) race on it and must be serialised by the caller.
+// threads) race on it and must be serialised by the caller. Each call waits for its
+// stream and copies the objective into host memory before it returns.
 //
 // The computation is the forward evaluation of the optimiser (the dose z = D x and the
 // objective of the one-sided quadratic penalties with per-structure thresholds, each
 // term scaled by w / |V_s|) done directly on the CSR rows: one warp per voxel row, a
 // fixed shuffle tree per row, FP64 objective partials per block summed in block order
-// by the last block to finish, so the result does not depend on scheduling.
+// by the last block to finish, so the result does not depend on scheduling. The kernel
+// reads only inside the caller's arrays: a row whose offsets leave [0, nnz] or decrease,
+// and an entry whose beamlet index is outside [0, n), are skipped and flagged, and the
+// call then returns IMRT_EINVAL.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -49,7 +53,9 @@ struct NaScratch {
     double G;                       // the objective of the last call
     int32_t counts[kNaMaxStruct];   // structure voxel counts (cleared by every call)
     int32_t ticket;                 // blocks finished in the current launch (cleared by every call)
-    int32_t pad[7];
+    int32_t bad;                    // input errors seen by the kernel (cleared by every call):
+                                    // 1 row offsets, 2 beamlet index
+    int32_t pad[6];
 };
 
 static __device__ __align__(256) NaScratch g_na_scratch;
@@ -81,7 +87,8 @@ __device__ __forceinline__ double na_warp_sum(double v) {
 
 __global__ void __launch_bounds__(kNaThreads) k_na_eval(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col,
-                                                      const float* __restrict__ val, int32_t m,
+                                                      const float* __restrict__ val, int32_t m, int32_t n,
+                                                      int64_t nnz,
                                                       const uint8_t* __restrict__ mask, const NaTerms terms,
                                                       const float* __restrict__ x, float* __restrict__ z,
                                                       NaScratch* s) {
@@ -102,13 +109,23 @@ __global__ void __launch_bounds__(kNaThreads) k_na_eval(const int64_t* __restric
     }
     __syncthreads();
     double F = 0.0;
+    int bad = 0;
+    if (blockIdx.x == 0 && tid == 0 && (row_ptr[0] != 0 || row_ptr[m] != nnz)) bad |= 1;
     const int row0 = blockIdx.x * kNaRowsPerBlock + wib * kNaRowsPerWarp;
     for (int k = 0; k < kNaRowsPerWarp; ++k) {
         const int j = row0 + k;
         if (j >= m) break;
-        const int64_t a = row_ptr[j], b = row_ptr[j + 1];
+        int64_t a = row_ptr[j], b = row_ptr[j + 1];
+        if (a < 0 || b < a || b > nnz) {  // malformed offsets: read nothing of this row
+            bad |= 1;
+            a = b = 0;
+        }
         float acc = 0.0f;
-        for (int64_t e = a + lane; e < b; e += 32) acc = fmaf(val[e], x[col[e]], acc);
+        for (int64_t e = a + lane; e < b; e += 32) {
+            const int32_t c = col[e];
+            if ((uint32_t)c < (uint32_t)n) acc = fmaf(val[e], x[c], acc);
+            else bad |= 2;
+        }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
             if (z) z[j] = acc;
@@ -127,7 +144,11 @@ __global__ void __launch_bounds__(kNaThreads) k_na_eval(const int64_t* __restric
             if (!isfinite(acc)) F = __longlong_as_double(0x7ff8000000000000LL);
         }
     }
-    if (lane == 0) wsum[wib] = F;
+    bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
+    if (lane == 0) {
+        wsum[wib] = F;
+        if (bad) atomicOr(&s->bad, bad);
+    }
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
@@ -192,13 +213,16 @@ imrt_status na_scratch(NaScratch** out) {
     return IMRT_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory that the current device can read as its own: device memory of
+// another GPU is refused, since the kernels would read it as peer memory or fault.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    return a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -220,11 +244,23 @@ extern "C" imrt_status imrt_eval_csr_noalloc(const imrt_csr* D, const uint8_t* s
                      (long long)kNaMaxVoxels);
         return IMRT_EUNSUPPORTED;
     }
-    if (!D->on_device || !on_device(D->row_ptr) || (D->nnz > 0 && (!on_device(D->col_idx) || !on_device(D->val))) ||
-        !on_device(structures) || !on_device(x) || (z_out && !on_device(z_out))) {
-        na_set_error("D, structures, x and z_out must be device pointers");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        na_set_error("no CUDA device");
+        return IMRT_ECUDA;
+    }
+    if (!D->on_device || !on_device(D->row_ptr, dev) ||
+        (D->nnz > 0 && (!on_device(D->col_idx, dev) || !on_device(D->val, dev))) || !on_device(structures, dev) ||
+        !on_device(x, dev) || (z_out && !on_device(z_out, dev))) {
+        na_set_error("D, structures, x and z_out must be device pointers of the current device (%d)", dev);
         return IMRT_EINVAL;
     }
+    for (int i = 0; i < 2 * n_structures; ++i)
+        if (!(weights[i] >= 0.0f) || !isfinite(weights[i]) || isinf(thresholds[i])) {
+            na_set_error("weights must be finite and >= 0; thresholds finite or NaN");
+            return IMRT_EINVAL;
+        }
     NaTerms terms;
     memset(&terms, 0, sizeof(terms));
     terms.S = n_structures;
@@ -238,18 +274,27 @@ extern "C" imrt_status imrt_eval_csr_noalloc(const imrt_csr* D, const uint8_t* s
     imrt_status st = na_scratch(&s);
     if (st != IMRT_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(&s->counts[0], 0, sizeof(int32_t) * (kNaMaxStruct + 1), cs);  // counts, ticket
+    // counts, ticket and the error flag start at zero
+    cudaError_t e = cudaMemsetAsync(&s->counts[0], 0, sizeof(int32_t) * (kNaMaxStruct + 2), cs);
     const int blocks = (int)((D->m + kNaRowsPerBlock - 1) / kNaRowsPerBlock);
     if (e == cudaSuccess) {
         k_na_counts<<<256, kNaThreads, 0, cs>>>(structures, D->m, s);
-        k_na_eval<<<blocks, kNaThreads, 0, cs>>>(D->row_ptr, D->col_idx, D->val, D->m, structures, terms, x, z_out, s);
+        k_na_eval<<<blocks, kNaThreads, 0, cs>>>(D->row_ptr, D->col_idx, D->val, D->m, D->n, D->nnz, structures,
+                                                 terms, x, z_out, s);
         e = cudaGetLastError();
     }
+    int32_t bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(G_out, &s->G, sizeof(double), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, &s->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) {
         na_set_error("CUDA error: %s", cudaGetErrorString(e));
         return IMRT_ECUDA;
+    }
+    if (bad) {
+        na_set_error("invalid CSR: %s%s%s", (bad & 1) ? "row offsets outside [0, nnz] or decreasing" : "",
+                     (bad & 3) == 3 ? "; " : "", (bad & 2) ? "beamlet index outside [0, n)" : "");
+        return IMRT_EINVAL;
     }
     return IMRT_OK;
 }
