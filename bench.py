@@ -6,8 +6,8 @@ in HBM. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
---impl reference times the FP64 CPU oracle (the paper's sequential-C analogue)
-on a bounded sample of the same workload and scales it to a full plan.
+--impl reference times the FP64 CPU oracle (the paper's sequential-C analogue):
+each step is one complete solve of the same workload on the host cores.
 Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
 plan, no data-path collective; timing is the max over ranks.
 """
@@ -137,30 +137,30 @@ def pinned(a: np.ndarray):
     return t.numpy(), t
 
 
-def cpu_oracle_sample(case, lambda0: float, iterations_full: int, budget_s: float = 20.0, threads: int = 0):
-    """Times the FP64 oracle on the full workload for a bounded number of iterations and scales it
-    to `iterations_full` iterations (all host cores unless `threads`). Returns (estimated seconds,
-    details)."""
+def common_config(workload: str, case, max_iter: int, world: int) -> dict:
+    """The workload description both arms print (identical keys and values)."""
+    csr_gb = case.nnz * 8 / 1e9
+    return {"workload": workload, "m": case.m, "n": case.n, "nnz": case.nnz, "max_iter": max_iter, "delta": 1e-6,
+            "lambda0": "rule 8/L, L = 2 lambda_max(D^T C D) by 50 power iterations",
+            "l2": f"inputs larger than L2: D alone is {csr_gb:.2f} GB of CSR values and indices > 129 MB",
+            "parallelism": f"replicas x{world}"}
+
+
+def cpu_oracle_solve(case, lambda0: float, max_iter: int, threads: int = 0):
+    """Times one complete FP64 oracle solve of the workload (the same loop, iteration cap and
+    relative-change stop as the GPU solve) on `threads` host cores (all by default). Returns
+    (seconds, iterations, cores)."""
     import oracle
     orc = oracle.get()
     threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
-    r1 = orc.solve(case, lambda0=lambda0, max_iter=1, threads=threads, trace=False)
-    t_one = time.perf_counter() - t0
-    # one iteration costs ~ (t_one - setup); pick a sample that fits the budget
-    k = max(2, min(iterations_full, int(budget_s / max(t_one, 1e-3))))
-    t0 = time.perf_counter()
-    rk = orc.solve(case, lambda0=lambda0, max_iter=k, threads=threads, trace=False)
-    t_k = time.perf_counter() - t0
-    per_iter = (t_k - t_one) / max(rk.iterations - r1.iterations, 1)
-    setup = max(t_one - per_iter, 0.0)
-    est = setup + per_iter * iterations_full
-    return est, {"cores": threads, "iterations_timed": int(rk.iterations), "seconds_timed": round(t_k + t_one, 3),
-                 "per_iteration_s": per_iter, "setup_s": setup}
+    r = orc.solve(case, lambda0=lambda0, max_iter=max_iter, delta=1e-6, threads=threads, trace=False)
+    return time.perf_counter() - t0, int(r.iterations), threads
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    """--impl reference: the FP64 CPU oracle on the host cores (rank 0 only); each step is one
+    complete solve of the workload."""
     if rank != 0:
         return 0
     spec = phantom.WORKLOADS[args.workload]
@@ -168,23 +168,20 @@ def run_reference(args, rank, world):
     import oracle
     orc = oracle.get()
     lam0 = orc.lambda0_rule(case, threads=os.cpu_count() or 1)
-    values = []
-    details = None
+    values, iters, cores = [], 0, 0
     for step in range(args.warmup + args.steps):
-        est, det = cpu_oracle_sample(case, lam0, args.max_iter, budget_s=args.cpu_budget_s / max(args.steps, 1))
+        t, iters, cores = cpu_oracle_solve(case, lam0, args.max_iter)
         if step >= args.warmup:
-            values.append(est)
-            details = det
+            values.append(t)
     value = statistics.mean(values)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "m": case.m, "n": case.n, "nnz": case.nnz,
-                   "max_iter": args.max_iter, "delta": 1e-6, "lambda0": "rule 8/L (oracle FP64)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": details["cores"], "kind": "oracle",
-                         "sample": f"{details['iterations_timed']} iterations of the full workload per step, "
-                                   f"scaled to {args.max_iter} iterations"},
+        "config": common_config(args.workload, case, args.max_iter, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one complete FP64 oracle solve of the full workload per step "
+                                   f"({iters} iterations), timed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -328,16 +325,13 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, det = cpu_oracle_sample(case, lam0, res.iterations, budget_s=args.cpu_budget_s)
-        cpu = {"value": est, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
-               "sample": f"FP64 oracle, {det['iterations_timed']} iterations of the full workload "
-                         f"({det['seconds_timed']} s), per-iteration time scaled to the GPU's "
-                         f"{res.iterations} iterations plus set-up"}
+        t_all, it_all, cores = cpu_oracle_solve(case, lam0, args.max_iter)
+        cpu = {"value": t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one complete FP64 oracle solve of the full workload ({it_all} iterations), timed"}
         # one core: the analogue of a sequential CPU implementation
-        est1, det1 = cpu_oracle_sample(case, lam0, res.iterations, budget_s=args.cpu_budget_s / 3, threads=1)
-        cpu["single_thread"] = {"value": est1, "unit": UNIT, "cores": 1,
-                                "sample": f"{det1['iterations_timed']} iterations ({det1['seconds_timed']} s), "
-                                          f"scaled the same way"}
+        t_one, it_one, _ = cpu_oracle_solve(case, lam0, args.max_iter, threads=1)
+        cpu["single_thread"] = {"value": t_one, "unit": UNIT, "cores": 1,
+                                "sample": f"one complete solve on one core ({it_one} iterations), timed"}
 
     # the reduced-precision forms (FP16 / BF16 / FP8-e4m3 storage, FP32 accumulation, FP64
     # objective and Armijo test, FP32 polish): time-to-plan, bandwidth, errors vs the FP64 oracle
@@ -394,13 +388,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == 0 else f"{args.precision}-storage/f32-accumulate",
         "data": "synthetic",
-        "config": {"workload": args.workload, "m": case.m, "n": case.n, "nnz": case.nnz,
-                   "precision": args.precision, "k_trials": best_kt,
-                   "kernel_variant": best_variant,
-                   "tuned_s": {k: round(v, 5) for k, v in tuned.items()}, "max_iter": args.max_iter, "delta": 1e-6,
-                   "lambda0": f"rule 8/L = {lam0:.6g}",
-                   "l2": f"inputs larger than L2: one forward and one transposed pass read {(info['fwd_bytes'] + info['bwd_bytes']) / 1e9:.2f} GB > 129 MB",
-                   "parallelism": f"replicas x{world}"},
+        "config": common_config(args.workload, case, args.max_iter, world),
+        "form": {"precision": args.precision, "k_trials": best_kt, "kernel_variant": best_variant,
+                 "lambda0": lam0, "tuned_s": {k: round(v, 5) for k, v in tuned.items()}},
         "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "traffic": traffic, "kernel": dominant,
                      "peak_kind": f"{peak_kind} copy bandwidth",

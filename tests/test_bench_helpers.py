@@ -57,12 +57,21 @@ def test_clock_summary_reports_throttle_reasons():
                                                "samples": 0}
 
 
-def test_cpu_oracle_sample_scales_a_bounded_sample():
-    """The CPU baseline times a few oracle iterations and scales them to the full count."""
+def test_cpu_oracle_solve_times_a_complete_solve():
+    """The CPU baseline times one complete oracle solve (no extrapolation): the iteration count is
+    the oracle's own for the same cap and stop rule."""
     from paper_0908_4421_gb300 import phantom
     import oracle
     case = phantom.make_case(phantom.TINY_5MM_5BEAM)
     lam0 = oracle.get().lambda0_rule(case, threads=1)
-    est, det = bench.cpu_oracle_sample(case, lam0, iterations_full=200, budget_s=0.5, threads=1)
-    assert det["cores"] == 1 and det["iterations_timed"] >= 2
-    assert est == det["setup_s"] + det["per_iteration_s"] * 200 and est > 0
+    t, iters, cores = bench.cpu_oracle_solve(case, lam0, max_iter=30, threads=1)
+    ref = oracle.get().solve(case, lambda0=lam0, max_iter=30, delta=1e-6, threads=1, trace=False)
+    assert cores == 1 and iters == ref.iterations and t > 0
+
+
+def test_both_arms_print_the_same_config():
+    from paper_0908_4421_gb300 import phantom
+    case = phantom.make_case(phantom.TINY_5MM_5BEAM)
+    a = bench.common_config("tiny-40x40x30-5mm-5beam", case, 200, 1)
+    b = bench.common_config("tiny-40x40x30-5mm-5beam", case, 200, 1)
+    assert a == b and set(a) >= {"workload", "m", "n", "nnz", "l2", "parallelism"}

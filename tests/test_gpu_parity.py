@@ -139,6 +139,8 @@ def test_tiny_phantom_solve_parity(orc, tiny, mode, variant):
         z_gpu = orc.dose(case, xs[k].astype(np.float64))
         z_orc = orc.dose(case, ref.xs[k])
         assert rel(z_gpu, z_orc) <= DOSE_RTOL, k
+        # voxel by voxel, relative to the largest dose
+        assert np.max(np.abs(z_gpu - z_orc)) <= DOSE_RTOL * np.max(np.abs(z_orc)), k
         assert abs(G[k] - ref.G[k]) <= FINAL_RTOL * ref.G[k]
         same_path = k
     assert same_path >= min(20, k_common)
@@ -146,6 +148,24 @@ def test_tiny_phantom_solve_parity(orc, tiny, mode, variant):
     assert rel(z_final, orc.dose(case, x_final.astype(np.float64))) <= DOSE_RTOL
     assert np.all(xs >= 0)
     assert np.all(np.diff(G) < 0)
+
+
+@pytest.mark.parametrize("max_iter", [5, 30, 200])
+def test_kkt_residual_matches_oracle(orc, tiny, max_iter):
+    """The reported KKT residual ||x - max(0, x - g)||_inf / max(1, ||g(x_1)||_inf) against the
+    oracle's for the same solve, and against the definition evaluated with the oracle's FP64
+    gradient at the GPU's own final x and at x_1."""
+    case, lam0 = tiny
+    ref = orc.solve(case, lambda0=lam0, max_iter=max_iter)
+    with Plan.from_case(case, Options(lambda0=lam0, max_iter=max_iter)) as plan:
+        res = plan.solve()
+        x = plan.get_x().astype(np.float64)
+    assert res.status == 0 and res.iterations == ref.iterations
+    assert abs(res.kkt - ref.kkt) <= 2e-3 * ref.kkt, (res.kkt, ref.kkt)
+    g = orc.eval(case, x)[3]
+    g1 = orc.eval(case, orc.initial_point(case))[3]
+    kkt = np.max(np.abs(x - np.maximum(0.0, x - g))) / max(1.0, np.max(np.abs(g1)))
+    assert abs(res.kkt - kkt) <= 2e-3 * kkt, (res.kkt, kkt)
 
 
 def test_graph_and_host_modes_agree_bitwise(tiny):
