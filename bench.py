@@ -48,11 +48,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+SOURCE_FILES = ("kernels.cu", "stream.cuh", "team.cu", "imrt_internal.cuh", "ptx.cuh", "format.cu", "api.cu")
+
+
 def kernel_source_hash() -> str:
     """Fingerprint of the kernel, layout and schedule sources; comments and blank lines do not
     count, so a profile stays valid across edits that cannot change the code."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "imrt_internal.cuh", "ptx.cuh", "format.cu", "api.cu"):
+    for f in SOURCE_FILES:
         with open(os.path.join(ROOT, "paper_0908_4421_gb300", "csrc", f)) as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         text = re.sub(r"//[^\n]*", "", text)

@@ -78,6 +78,13 @@ typedef enum {
     IMRT_MODE_HOST = 1   /* host loop, one status read-back per Armijo trial */
 } imrt_mode;
 
+typedef enum {
+    IMRT_SOLVER_GRAPH = 0, /* every pass over D is a kernel across the whole GPU (mode selects graph or host loop) */
+    IMRT_SOLVER_TEAM = 1   /* persistent multi-plan kernel: a team of CTAs runs the plan's whole solve in one
+                              cooperative launch, shared with the other plans of a batch (see plan_solve_batch);
+                              needs m <= 1,048,576 voxels and n <= 65,536 beamlets */
+} imrt_solver;
+
 /* Voxel-major D (rows = voxels, columns = beamlets), CSR (Sec. 2.3). */
 typedef struct {
     int32_t m;               /* voxels (rows), >= 1 */
@@ -110,6 +117,11 @@ typedef struct {
                                pipeline, 2 warp streaming with one device-wide schedule */
     double timeout_ms;      /* 0: none; else the device loop stops with IMRT_ETIMEOUT */
     void* stream;           /* cudaStream_t */
+    int32_t solver;         /* imrt_solver; default IMRT_SOLVER_GRAPH */
+    int32_t reserved;       /* must be 0 */
+    double polish_switch;   /* reduced precision: the reduced phase also ends, handing the rest of max_iter to
+                               the FP32 polish, once its relative change |G_new - G_old| / G_new falls below
+                               this (0: only after max_iter - polish_iter iterations); default 0 */
 } imrt_options;
 
 typedef struct {
@@ -131,6 +143,9 @@ typedef struct {
     double bwd_ms;             /* profile: summed transposed-pass kernel time */
     int32_t fwd_launches;      /* profile: timed forward launches */
     int32_t bwd_launches;      /* profile: timed transposed launches */
+    int64_t bytes;             /* algorithmic bytes of the solve's passes over D: each phase's forward and
+                                  transposed passes times their per-pass bytes at that phase's precision
+                                  (imrt_plan_info.fwd_bytes / bwd_bytes) */
 } imrt_result;
 
 typedef struct {
@@ -203,10 +218,16 @@ imrt_status plan_solve(imrt_plan* plan, const float* x0, imrt_result* res);
 
 /*
  * Solves several plans (Sec. 2.2, steps 1-5, each plan independently) in one
- * CUDA-graph launch: every plan's solve is one branch of the graph, so plans of
- * different sizes run concurrently and finish independently; each keeps its own
- * options (precision, k_trials, x_init, max_iter, ...), and reduced-precision
- * plans get their FP32 polish in a second launch.
+ * launch. When every plan has solver = IMRT_SOLVER_TEAM, the plans share one
+ * persistent cooperative kernel per storage format: its CTAs are cut into teams
+ * sized to each plan's bytes per pass (one plan per team, or, with more plans
+ * than CTAs, one-CTA teams that take several plans in turn), and every team
+ * runs its plans' whole solves without returning to the host. A plan's result
+ * is bitwise the same as when it is solved alone with the team solver (fixed
+ * reduction orders, independent of the team size). Otherwise every plan's solve
+ * is one branch of a CUDA graph. Each plan keeps its own options (precision,
+ * k_trials, x_init, max_iter, ...), and reduced-precision plans get their FP32
+ * polish in a second launch.
  *   plans    count distinct plan handles.
  *   x0s      NULL, or count pointers read for plans with x_init = 2.
  *   results  count results (host).

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ELINESEARCH",
 STOP_NONE, STOP_REL, STOP_MAXITER, STOP_EXACT, STOP_STATIONARY = 0, 1, 2, 3, 4
 FP32, FP16, BF16, FP8E4M3 = 0, 1, 2, 3
 MODE_GRAPH, MODE_HOST = 0, 1
+SOLVER_GRAPH, SOLVER_TEAM = 0, 1
 
 # Every symbol include/imrt.h declares.
 EXPORTS = ("imrt_default_options", "plan_create", "plan_set_options", "plan_solve", "plan_dose", "plan_eval",
@@ -40,7 +41,8 @@ class imrt_options(ctypes.Structure):
                 ("x_init", ctypes.c_int32), ("precision", ctypes.c_int32), ("k_trials", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("profile", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("polish_iter", ctypes.c_int32), ("kernel_variant", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("polish_switch", ctypes.c_double)]
 
 
 class imrt_result(ctypes.Structure):
@@ -50,7 +52,7 @@ class imrt_result(ctypes.Structure):
                 ("objective", ctypes.c_double), ("initial_objective", ctypes.c_double), ("kkt", ctypes.c_double),
                 ("rel_change", ctypes.c_double), ("lambda0", ctypes.c_double), ("ms", ctypes.c_double),
                 ("fwd_ms", ctypes.c_double), ("bwd_ms", ctypes.c_double), ("fwd_launches", ctypes.c_int32),
-                ("bwd_launches", ctypes.c_int32)]
+                ("bwd_launches", ctypes.c_int32), ("bytes", ctypes.c_int64)]
 
 
 class imrt_plan_info(ctypes.Structure):

@@ -36,6 +36,9 @@ class Options:
     kernel_variant: int = 0  # forward pass: 0 warp streaming, CTA-local schedule; 1 bulk-copy (TMA); 2 global schedule
     timeout_ms: float = 0.0
     stream: int = 0  # cudaStream_t as an integer; 0 = legacy default stream
+    solver: int = L.SOLVER_GRAPH  # SOLVER_TEAM: the persistent multi-plan kernel
+    reserved: int = 0
+    polish_switch: float = 0.0  # reduced precision: hand over to the FP32 polish below this relative change
 
     def to_c(self) -> L.imrt_options:
         o = L.imrt_options()
@@ -64,6 +67,7 @@ class Result:
     bwd_ms: float
     fwd_launches: int
     bwd_launches: int
+    bytes: int
 
     @classmethod
     def from_c(cls, r: L.imrt_result) -> "Result":

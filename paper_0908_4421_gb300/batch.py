@@ -1,13 +1,15 @@
-"""Batched uneven plans: many plans solved by one CUDA-graph launch (plan_solve_batch).
+"""Batched uneven plans: many plans solved in one persistent launch (plan_solve_batch).
 
-Workload (run with ``python -m paper_0908_4421_gb300.batch``): 64 seeded phantoms of
-the tiny-phantom family with voxel spacing from {2.5, 4, 5} mm, 5, 7 or 9 beams,
-5 or 10 mm beamlets and PTV radii scaled in [0.8, 1.2]; each plan evaluates k in
-{1, 4, 8} Armijo step sizes per pass over D (drawn per plan) with D in FP16 and FP32
-accumulation. The autotuner picks each shape class's forward schedule. The benchmark
-reports one batched launch against the same plans solved one after another: plans per
-second, and aggregate GB/s of the passes over D (forward and transposed algorithmic
-bytes per pass times the passes each plan made).
+Workload (``python -m paper_0908_4421_gb300.batch``): 64 seeded phantoms of the tiny-phantom
+family with voxel spacing from {2.5, 4, 5} mm, 5, 7 or 9 beams, 5 or 10 mm beamlets and PTV
+radii scaled in [0.8, 1.2]; each plan evaluates k in {1, 4, 8} Armijo step sizes per pass
+over D (drawn per plan) with D in FP16, FP32 accumulation and the FP32 polish. With the team
+solver (the default) the plans share one cooperative kernel per phase whose CTAs are cut
+into teams sized to each plan's bytes per pass; each team runs its plan's whole solve. The
+benchmark reports the batch against the same plans solved one after another (team solver
+alone, and the per-pass kernel graph): plans per second, and the aggregate algorithmic
+bandwidth of the passes over D (the libraries' per-pass bytes times the passes each plan
+made, for each phase's precision) as a fraction of the measured HBM copy bandwidth.
 """
 from __future__ import annotations
 
@@ -21,25 +23,69 @@ import numpy as np
 from . import _lib as L
 from . import phantom
 from .api import Options, Plan, solve_batch
-from .autotune import TuneCache
 
 PRECISIONS = {"fp32": L.FP32, "fp16": L.FP16, "bf16": L.BF16, "fp8": L.FP8E4M3}
 
 
-def make_plans(count: int = 64, seed0: int = 0, precision: int = L.FP16, ks=(1, 4, 8), tune: bool = True,
-               max_iter: int = 200):
-    """The batch's plans (created on the device) and the per-class tuning decisions."""
-    rng = np.random.Generator(np.random.PCG64(seed0 + 12345))
+def make_cases(count: int = 64, seed0: int = 0):
+    return [phantom.make_case(phantom.jittered_spec(seed0 + i)) for i in range(count)]
+
+
+def make_plans(cases, precision: int = L.FP16, ks=(1, 4, 8), solver: int = L.SOLVER_TEAM, max_iter: int = 200,
+               seed: int = 12345, stream: int = 0):
+    """The batch's plans (created on the device); k_trials drawn per plan from `ks`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
     plans = []
-    for i in range(count):
-        case = phantom.make_case(phantom.jittered_spec(seed0 + i))
+    for c in cases:
         k = int(rng.choice(ks))
-        plans.append(Plan.from_case(case, Options(precision=precision, k_trials=k, max_iter=max_iter)))
-    cache = TuneCache(k_trials=None, repeats=1)
-    if tune:
+        plans.append(Plan.from_case(c, Options(precision=precision, k_trials=k, max_iter=max_iter, solver=solver,
+                                               stream=stream)))
+    return plans
+
+
+def run(plans, repeats: int = 3, sequential: bool = True, stream: int = 0) -> dict:
+    """Times the batch (median of `repeats` launches after one warm-up) and, optionally, the same
+    plans one after another with the team solver and with the per-pass graph; checks that every
+    plan's batched result equals its team solve alone, bit for bit."""
+    import torch
+    infos = [p.info() for p in plans]
+    res_b = solve_batch(plans, stream=stream)  # warm-up
+    bat = []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_b = solve_batch(plans, stream=stream)
+        bat.append(time.perf_counter() - t0)
+    x_b = [p.get_x() for p in plans]
+    t_bat = statistics.median(bat)
+    moved = sum(r.bytes for r in res_b)
+    out = {"plans": len(plans), "m_total": sum(i["m"] for i in infos), "nnz_total": sum(i["nnz"] for i in infos),
+           "batched_s": t_bat, "plans_per_s": len(plans) / t_bat, "bytes": moved,
+           "aggregate_gbs": moved / t_bat / 1e9, "failed": sum(1 for r in res_b if r.status != 0),
+           "iterations_mean": statistics.mean(r.iterations + r.polish_iterations for r in res_b)}
+    if sequential:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_a = [p.solve() for p in plans]
+        t_seq = time.perf_counter() - t0
+        same = all(ra.objective == rb.objective and ra.iterations == rb.iterations and
+                   np.array_equal(p.get_x(), xb) for p, ra, rb, xb in zip(plans, res_a, res_b, x_b))
+        saved = [p.options.solver for p in plans]
         for p in plans:
-            cache.apply(p)
-    return plans, cache
+            p.set_options(solver=L.SOLVER_GRAPH)
+        for p in plans:  # warm the per-plan graphs
+            p.solve()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in plans:
+            p.solve()
+        t_graph = time.perf_counter() - t0
+        for p, s in zip(plans, saved):
+            p.set_options(solver=s)
+        out.update({"sequential_team_s": t_seq, "sequential_graph_s": t_graph,
+                    "speedup_vs_sequential_graph": t_graph / t_bat, "speedup_vs_sequential_team": t_seq / t_bat,
+                    "results_identical_alone_and_batched": same})
+    return out
 
 
 def _main():
@@ -47,35 +93,15 @@ def _main():
     ap.add_argument("--plans", type=int, default=64)
     ap.add_argument("--precision", default="fp16", choices=sorted(PRECISIONS))
     ap.add_argument("--repeats", type=int, default=3)
-    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--solver", default="team", choices=["team", "graph"])
     args = ap.parse_args()
-    plans, cache = make_plans(args.plans, precision=PRECISIONS[args.precision], tune=not args.no_tune)
+    cases = make_cases(args.plans)
+    plans = make_plans(cases, precision=PRECISIONS[args.precision],
+                       solver=L.SOLVER_TEAM if args.solver == "team" else L.SOLVER_GRAPH)
     try:
-        infos = [p.info() for p in plans]
-        for _ in range(2):  # warm-up (graph instantiation, shapes)
-            solve_batch(plans)
-            for p in plans:
-                p.solve()
-        seq, bat = [], []
-        for _ in range(args.repeats):
-            t0 = time.perf_counter()
-            res_seq = [p.solve() for p in plans]
-            seq.append(time.perf_counter() - t0)
-            t0 = time.perf_counter()
-            res_bat = solve_batch(plans)
-            bat.append(time.perf_counter() - t0)
-        same = all(a.objective == b.objective and a.iterations == b.iterations for a, b in zip(res_seq, res_bat))
-        moved = sum(r.passes * i["fwd_bytes"] + r.grad_passes * i["bwd_bytes"] for r, i in zip(res_bat, infos))
-        t_seq, t_bat = statistics.median(seq), statistics.median(bat)
-        print(json.dumps({
-            "workload": f"{args.plans} jittered tiny-family phantoms, k in {{1,4,8}}, {args.precision}",
-            "plans": args.plans, "m_total": sum(i["m"] for i in infos), "nnz_total": sum(i["nnz"] for i in infos),
-            "sequential_s": t_seq, "batched_s": t_bat, "plans_per_s_sequential": args.plans / t_seq,
-            "plans_per_s_batched": args.plans / t_bat, "speedup": t_seq / t_bat,
-            "batched_gbs": moved / t_bat / 1e9, "results_identical": same,
-            "schedules": {str(k): {"kernel_variant": v.kernel_variant, "k_trials": v.k_trials}
-                          for k, v in cache.choices.items()},
-        }))
+        out = run(plans, repeats=args.repeats)
+        out["workload"] = f"{args.plans} jittered tiny-family phantoms, k in {{1,4,8}}, {args.precision}"
+        print(json.dumps(out))
     finally:
         for p in plans:
             p.close()

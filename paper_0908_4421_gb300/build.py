@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libimrt.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ("kernels.cu", "format.cu", "api.cu", "noalloc.cu")
+SOURCES = ("kernels.cu", "team.cu", "format.cu", "api.cu", "noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

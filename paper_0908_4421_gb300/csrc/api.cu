@@ -209,6 +209,14 @@ struct imrt_plan {
     int64_t device_bytes = 0;
     std::vector<void*> allocations;
     int32_t wmax = 0, gmax = 0;
+    // persistent multi-plan solver: slices with and without entries of each SELL copy
+    // (longest first), built on first use, and the slice objective partials
+    struct TeamSlices {
+        int32_t* busy = nullptr;
+        int32_t* idle = nullptr;
+        int32_t n_busy = -1, n_idle = 0;
+    } team32, teamq;
+    double* team_obj = nullptr;
 };
 
 namespace {
@@ -322,6 +330,10 @@ imrt_status validate_options(const imrt_options* o) {
     if (o->kernel_variant < 0 || o->kernel_variant > 2)
         return set_error("kernel_variant must be 0, 1 or 2"), IMRT_EINVAL;
     if (!(o->timeout_ms >= 0.0)) return set_error("timeout_ms must be >= 0"), IMRT_EINVAL;
+    if (o->solver != IMRT_SOLVER_GRAPH && o->solver != IMRT_SOLVER_TEAM) return set_error("unknown solver"), IMRT_EINVAL;
+    if (o->reserved != 0) return set_error("reserved must be 0"), IMRT_EINVAL;
+    if (!(o->polish_switch >= 0.0) || !std::isfinite(o->polish_switch))
+        return set_error("polish_switch must be finite and >= 0"), IMRT_EINVAL;
     return IMRT_OK;
 }
 
@@ -646,6 +658,24 @@ BwdArgs bwd_args(imrt_plan* p, int precision, int guard) {
 
 const SellCopy& copy_of(const imrt_plan* p, int precision) {
     return precision == IMRT_FP32 ? p->sell32 : p->sellq;
+}
+
+// CSR-equivalent algorithmic bytes of one forward and one transposed pass at `precision`:
+// values + indices + row offsets + x + (z and r writes; mask and r-order reads) forward;
+// values + voxel indices (16-bit inside segments, else int32) + row or segment offsets + r + g.
+void pass_bytes(const imrt_plan* p, int precision, int64_t* fwd, int64_t* bwd) {
+    const SellCopy& c = copy_of(p, precision);
+    const int64_t vb = (int64_t)elem_bytes(precision), cb = c.fmt == IMRT_FP32 ? 4 : 2;
+    *fwd = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 13;
+    *bwd = p->t_H == 0 ? p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4
+                       : p->nnz * (vb + 2) + ((int64_t)p->n * p->t_H + 1) * 8 + (int64_t)p->m * 4 +
+                             (int64_t)p->n * 4;
+}
+
+void add_bytes(const imrt_plan* p, int precision, int passes, int grad_passes, imrt_result* r) {
+    int64_t f = 0, b = 0;
+    pass_bytes(p, precision, &f, &b);
+    r->bytes += f * passes + b * grad_passes;
 }
 
 // Stand-alone evaluation of the forward kernel (no step) with the copy of D at `precision`:
@@ -996,13 +1026,13 @@ imrt_status ensure_trace(imrt_plan* p) {
     return IMRT_OK;
 }
 
-SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_init, const float* x0,
-                        unsigned long long cond) {
+SolveParams make_params(imrt_plan* p, const FwdShape* sh, int max_iter, int x_init, const float* x0,
+                        unsigned long long cond, double delta) {
     const imrt_options& o = p->opt;
     SolveParams q{};
     q.eps = o.eps;
     q.alpha = o.alpha;
-    q.delta = o.delta;
+    q.delta = delta;
     q.lambda0 = o.lambda0 > 0.0 ? o.lambda0 : p->lambda0_rule;
     q.eps_over_lambda0 = q.eps / q.lambda0;
     q.inv_alpha = 1.0 / q.alpha;
@@ -1016,9 +1046,9 @@ SolveParams make_params(imrt_plan* p, const FwdShape& sh, int max_iter, int x_in
     q.n_pad = p->n_pad;
     q.m = p->m;
     q.m_pad = p->m_pad;
-    q.fwd_grid = sh.grid;
-    q.n_obj = sh.units.n_obj;
-    q.obj = sh.units.obj;
+    q.fwd_grid = sh ? sh->grid : 0;
+    q.n_obj = sh ? sh->units.n_obj : 0;
+    q.obj = sh ? sh->units.obj : nullptr;
     q.timeout_ns = o.timeout_ms > 0.0 ? (unsigned long long)(o.timeout_ms * 1e6) : 0ull;
     q.tr_G = o.trace >= 1 ? p->tr_G : nullptr;
     q.tr_lam = o.trace >= 1 ? p->tr_lam : nullptr;
@@ -1204,7 +1234,8 @@ imrt_status get_graph(imrt_plan* p, int precision, int k_trials, PhaseKernels& K
 }
 
 // One solve phase on the device. x_init / x0 as in SolveParams.
-imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, const float* x0, imrt_result* res) {
+imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, const float* x0, imrt_result* res,
+                      double delta) {
     cudaStream_t s = stream_of(p);
     PhaseKernels K;
     FwdShape* sh = nullptr;
@@ -1212,7 +1243,7 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
     const bool graph = p->opt.mode == IMRT_MODE_GRAPH;
     SolveGraph* sg = nullptr;
     if (graph) TRY(get_graph(p, precision, p->opt.k_trials, K, &sg));
-    SolveParams q = make_params(p, *sh, max_iter, x_init, x0, graph ? (unsigned long long)sg->cond : 0ull);
+    SolveParams q = make_params(p, sh, max_iter, x_init, x0, graph ? (unsigned long long)sg->cond : 0ull, delta);
     CK(cudaMemcpyAsync(p->sp, &q, sizeof(q), cudaMemcpyHostToDevice, s));
     int launches = 0;
     if (graph) {
@@ -1264,6 +1295,7 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
     res->launches += launches;
     res->passes += d.passes;
     res->grad_passes += d.grad_passes;
+    add_bytes(p, precision, d.passes, d.grad_passes, res);
     p->cur = d.cur;
     return IMRT_OK;
 }
@@ -1306,7 +1338,8 @@ void forget_plan_batches(imrt_plan* p) {
 // FP32 polish of reduced-precision plans (x_init = 2 from their current x).
 imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vector<int>& precision,
                             const std::vector<int>& max_iter, const std::vector<int>& x_init,
-                            const std::vector<const float*>& x0, cudaStream_t s, std::vector<imrt_result>& res) {
+                            const std::vector<const float*>& x0, const std::vector<double>& delta, cudaStream_t s,
+                            std::vector<imrt_result>& res) {
     const size_t n = plans.size();
     std::vector<PhaseKernels> K(n);
     std::vector<FwdShape*> sh(n, nullptr);
@@ -1342,7 +1375,7 @@ imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vec
     BatchGraph& bg = it->second;
     std::vector<SolveParams> q(n);
     for (size_t i = 0; i < n; ++i) {
-        q[i] = make_params(plans[i], *sh[i], max_iter[i], x_init[i], x0[i], (unsigned long long)bg.conds[i]);
+        q[i] = make_params(plans[i], sh[i], max_iter[i], x_init[i], x0[i], (unsigned long long)bg.conds[i], delta[i]);
         CK(cudaMemcpyAsync(plans[i]->sp, &q[i], sizeof(SolveParams), cudaMemcpyHostToDevice, s));
     }
     CK(cudaGraphLaunch(bg.exec, s));
@@ -1354,6 +1387,245 @@ imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vec
         res[i].launches += 2 + 2 * IMRT_WHILE_UNROLL * ((d.passes - 1 + IMRT_WHILE_UNROLL - 1) / IMRT_WHILE_UNROLL) + 2;
         res[i].passes += d.passes;
         res[i].grad_passes += d.grad_passes;
+        add_bytes(plans[i], precision[i], d.passes, d.grad_passes, &res[i]);
+        plans[i]->cur = d.cur;
+    }
+    return IMRT_OK;
+}
+
+// --- persistent multi-plan solver -------------------------------------------------------
+
+// The SELL copy's slices with entries (longest first) and without (built on first use).
+imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices** out) {
+    imrt_plan::TeamSlices& t = precision == IMRT_FP32 ? p->team32 : p->teamq;
+    if (t.n_busy < 0) {
+        const SellCopy& c = copy_of(p, precision);
+        std::vector<int32_t> busy, idle;
+        for (int s = 0; s < p->n_slices; ++s) (c.host_cost[s] > 8 * kSlice ? busy : idle).push_back(s);
+        std::stable_sort(busy.begin(), busy.end(), [&](int x, int y) { return c.host_cost[x] > c.host_cost[y]; });
+        TRY(dalloc(p, &t.busy, std::max<size_t>(busy.size(), 1)));
+        TRY(dalloc(p, &t.idle, std::max<size_t>(idle.size(), 1)));
+        cudaStream_t s = stream_of(p);
+        if (!busy.empty())
+            CK(cudaMemcpyAsync(t.busy, busy.data(), sizeof(int32_t) * busy.size(), cudaMemcpyHostToDevice, s));
+        if (!idle.empty())
+            CK(cudaMemcpyAsync(t.idle, idle.data(), sizeof(int32_t) * idle.size(), cudaMemcpyHostToDevice, s));
+        if (!p->team_obj) TRY(dalloc(p, &p->team_obj, (size_t)2 * kMaxTrials * std::max(p->n_slices, 1)));
+        CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+        t.n_busy = (int32_t)busy.size();
+        t.n_idle = (int32_t)idle.size();
+    }
+    *out = &t;
+    return IMRT_OK;
+}
+
+// Why plan p cannot run in the team solver at `precision`, or nullptr.
+const char* team_unsupported(const imrt_plan* p, int precision, int max_smem) {
+    if (p->t_H <= 0) return "the team solver needs at most 1048576 voxels (segmented beamlet-major copy)";
+    if (copy_of(p, precision).fmt == IMRT_FP32) return "the team solver needs at most 65536 beamlets";
+    if (team_smem_bytes(p->n_pad, p->opt.k_trials) + 16384 > (size_t)max_smem)
+        return "the team solver stages x, g and the trial points in shared memory: n * (2 + k_trials) * 4 bytes "
+               "exceed it";
+    return nullptr;
+}
+
+// Team sizes for one launch of `grid` CTAs: proportional to each plan's bytes per iteration
+// times its iteration budget (at least one CTA each, at most one CTA per 16 of the plan's
+// forward units or beamlet rows); plans beyond one CTA each share one-CTA teams, the longest
+// first to the least-loaded team. Fills team0 / team_size of every TeamPlan and the team lists.
+void team_partition(const std::vector<double>& cost, const std::vector<int>& cap, int grid,
+                    std::vector<TeamPlan>& tp, std::vector<int32_t>& cta_team, std::vector<int32_t>& team_first,
+                    std::vector<int32_t>& team_plan) {
+    const int n = (int)cost.size();
+    double total = 0.0;
+    for (double c : cost) total += c;
+    std::vector<int> T(n, 1);
+    int used = n;
+    if (n <= grid) {
+        used = 0;
+        for (int i = 0; i < n; ++i) {
+            T[i] = std::max(1, std::min(cap[i], (int)std::floor(grid * cost[i] / std::max(total, 1e-300))));
+            used += T[i];
+        }
+        while (used > grid) {  // the floor of 1 can overshoot: shrink the largest teams
+            int k = (int)(std::max_element(T.begin(), T.end()) - T.begin());
+            if (T[k] <= 1) break;
+            --T[k];
+            --used;
+        }
+        while (used < grid) {  // hand out the rest where a CTA saves the most time
+            int best = -1;
+            double gain = 0.0;
+            for (int i = 0; i < n; ++i) {
+                if (T[i] >= cap[i]) continue;
+                const double g = cost[i] / T[i] - cost[i] / (T[i] + 1);
+                if (g > gain) gain = g, best = i;
+            }
+            if (best < 0) break;
+            ++T[best];
+            ++used;
+        }
+    }
+    cta_team.assign(grid, -1);
+    team_first.clear();
+    team_plan.clear();
+    if (n <= grid && used <= grid) {
+        int c0 = 0;
+        for (int i = 0; i < n; ++i) {
+            tp[i].team0 = c0;
+            tp[i].team_size = T[i];
+            for (int k = 0; k < T[i]; ++k) cta_team[c0 + k] = i;
+            team_first.push_back(i);
+            team_plan.push_back(i);
+            c0 += T[i];
+        }
+        team_first.push_back(n);
+        return;
+    }
+    // more plans than CTAs: one-CTA teams, plans dealt longest first to the least-loaded team
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int t = 0; t < grid; ++t) heap.push(Load{0.0, t});
+    std::vector<std::vector<int>> lists(grid);
+    for (int i : order) {
+        Load l = heap.top();
+        heap.pop();
+        lists[l.second].push_back(i);
+        tp[i].team0 = l.second;
+        tp[i].team_size = 1;
+        heap.push(Load{l.first + cost[i], l.second});
+    }
+    for (int t = 0; t < grid; ++t) {
+        cta_team[t] = t;
+        team_first.push_back((int32_t)team_plan.size());
+        for (int i : lists[t]) team_plan.push_back(i);
+    }
+    team_first.push_back((int32_t)team_plan.size());
+}
+
+// One phase of the given plans in the team solver: one cooperative launch per storage format
+// (in the order of first appearance), then every plan's state read back.
+imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vector<int>& precision,
+                           const std::vector<int>& max_iter, const std::vector<int>& x_init,
+                           const std::vector<const float*>& x0, const std::vector<double>& delta, cudaStream_t s,
+                           std::vector<imrt_result>& res) {
+    const size_t n = plans.size();
+    int dev = 0, sm_count = 0, max_smem = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    std::vector<int> fmts;
+    for (size_t i = 0; i < n; ++i) {
+        const char* why = team_unsupported(plans[i], precision[i], max_smem);
+        if (why) return set_error("plan %zu: %s", i, why), IMRT_EUNSUPPORTED;
+        const int f = copy_of(plans[i], precision[i]).fmt;
+        if (std::find(fmts.begin(), fmts.end(), f) == fmts.end()) fmts.push_back(f);
+    }
+    for (int fmt : fmts) {
+        std::vector<size_t> idx;
+        for (size_t i = 0; i < n; ++i)
+            if (copy_of(plans[i], precision[i]).fmt == fmt) idx.push_back(i);
+        const size_t np = idx.size();
+        std::vector<TeamPlan> tp(np);
+        std::vector<double> cost(np);
+        std::vector<int> cap(np);
+        size_t smem = 0;
+        for (size_t k = 0; k < np; ++k) {
+            imrt_plan* p = plans[idx[k]];
+            const int prec = precision[idx[k]];
+            const imrt_plan::TeamSlices* ts = nullptr;
+            TRY(team_slices(p, prec, &ts));
+            const SellCopy& c = copy_of(p, prec);
+            TeamPlan& t = tp[k];
+            t.slice_off = c.slice_off;
+            t.slice_len = c.slice_len;
+            t.val = c.val;
+            t.col = c.col;
+            t.busy = ts->busy;
+            t.idle = ts->idle;
+            t.mask = p->mask;
+            t.r_index = p->perm;
+            t.scale = prec == IMRT_FP32 ? nullptr : p->scale;
+            t.vt = p->vt_on ? p->vt_p : nullptr;
+            t.vtm = p->vt_on ? p->vtm_p : nullptr;
+            t.terms = p->terms_dev;
+            t.rows = p->bwd_order;
+            t.seg = p->t_seg;
+            t.lo = p->t_lo;
+            t.tval = prec == IMRT_FP32 ? (const void*)p->t_vals : (const void*)p->t_valq;
+            t.v = p->v;
+            t.obj = p->team_obj;
+            t.st = p->st;
+            t.sp = p->sp;
+            t.m = p->m;
+            t.n = p->n;
+            t.n_pad = p->n_pad;
+            t.m_pad = p->m_pad;
+            t.n_slices = p->n_slices;
+            t.n_busy = ts->n_busy;
+            t.n_idle = ts->n_idle;
+            t.H = p->t_H;
+            const int64_t vb = (int64_t)elem_bytes(prec);
+            cost[k] = (double)std::max(max_iter[idx[k]], 1) *
+                      (double)(p->nnz * 2 * (vb + 2) + (int64_t)p->m * 17 + (int64_t)p->n * 8);
+            cap[k] = std::max(1, std::min(ts->n_busy, p->n) / 16);
+            smem = std::max(smem, team_smem_bytes(p->n_pad, p->opt.k_trials));
+        }
+        const int per_sm = team_ctas_per_sm(fmt, smem);
+        if (per_sm < 1) return set_error("the team solver does not fit on an SM"), IMRT_EUNSUPPORTED;
+        const int grid = sm_count * per_sm;
+        std::vector<int32_t> cta_team, team_first, team_plan;
+        team_partition(cost, cap, grid, tp, cta_team, team_first, team_plan);
+        const int n_teams = (int)team_first.size() - 1;
+        // one device block: plans, CTA map, team lists, barrier / stop words (zero)
+        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t o_plans = 0, o_cta = al(sizeof(TeamPlan) * np), o_first = o_cta + al(4 * cta_team.size()),
+                     o_list = o_first + al(4 * team_first.size()), o_sync = o_list + al(4 * team_plan.size()),
+                     total = o_sync + al(16 * np);
+        std::vector<uint8_t> host(total, 0);
+        void* dbuf = nullptr;
+        CK(pool_malloc(&dbuf, total, dev, s));
+        uint8_t* d = static_cast<uint8_t*>(dbuf);
+        for (size_t k = 0; k < np; ++k) tp[k].sync = reinterpret_cast<unsigned int*>(d + o_sync) + 4 * k;
+        memcpy(host.data() + o_plans, tp.data(), sizeof(TeamPlan) * np);
+        memcpy(host.data() + o_cta, cta_team.data(), 4 * cta_team.size());
+        memcpy(host.data() + o_first, team_first.data(), 4 * team_first.size());
+        memcpy(host.data() + o_list, team_plan.data(), 4 * team_plan.size());
+        cudaError_t e = cudaMemcpyAsync(d, host.data(), total, cudaMemcpyHostToDevice, s);
+        for (size_t k = 0; k < np && e == cudaSuccess; ++k) {
+            const size_t i = idx[k];
+            const SolveParams q = make_params(plans[i], nullptr, max_iter[i], x_init[i], x0[i], 0ull, delta[i]);
+            e = cudaMemcpyAsync(plans[i]->sp, &q, sizeof(q), cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess) {
+            TeamArgs a{};
+            a.plans = reinterpret_cast<const TeamPlan*>(d + o_plans);
+            a.cta_team = reinterpret_cast<const int32_t*>(d + o_cta);
+            a.team_first = reinterpret_cast<const int32_t*>(d + o_first);
+            a.team_plan = reinterpret_cast<const int32_t*>(d + o_list);
+            a.n_plans = (int32_t)np;
+            a.n_teams = n_teams;
+            e = launch_team(fmt, a, grid, smem, s);
+        }
+        // the pageable copies above have been staged when they return; the block is freed in stream order
+        cudaFreeAsync(dbuf, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error("team solver launch failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;
+        }
+    }
+    for (size_t i = 0; i < n; ++i)
+        CK(cudaMemcpyAsync(plans[i]->st_host, plans[i]->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < n; ++i) {
+        const DevState& d = *plans[i]->st_host;
+        res[i].launches += (int)fmts.size();
+        res[i].passes += d.passes;
+        res[i].grad_passes += d.grad_passes;
+        add_bytes(plans[i], precision[i], d.passes, d.grad_passes, &res[i]);
         plans[i]->cur = d.cur;
     }
     return IMRT_OK;
@@ -1362,6 +1634,17 @@ imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vec
 }  // namespace
 
 void imrt::set_last_error_message(const char* msg) { g_error = msg ? msg : ""; }
+
+namespace {
+const char* status_text(int status) {
+    return status == IMRT_ELINESEARCH ? "line search exceeded max_backtracks"
+           : status == IMRT_ENUMERIC  ? "non-finite dose or objective"
+           : status == IMRT_ETIMEOUT  ? "timeout"
+           : status == IMRT_ECANCELLED ? "cancelled"
+           : status == IMRT_EINVAL     ? "x0 must be finite and >= 0"
+                                       : "device error";
+}
+}  // namespace
 
 // =============================================================================
 // C ABI
@@ -1387,6 +1670,9 @@ void imrt_default_options(imrt_options* o) {
     o->polish_iter = 20;
     o->timeout_ms = 0.0;
     o->stream = nullptr;
+    o->solver = IMRT_SOLVER_GRAPH;
+    o->reserved = 0;
+    o->polish_switch = 0.0;
 }
 
 const char* imrt_last_error(void) { return g_error.c_str(); }
@@ -1581,6 +1867,10 @@ imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_
 imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     g_error.clear();
     if (!p || !res) return set_error("NULL argument"), IMRT_EINVAL;
+    if (p->opt.solver == IMRT_SOLVER_TEAM) {  // a batch of one in the persistent multi-plan kernel
+        const float* x0s[1] = {x0};
+        return plan_solve_batch(&p, 1, x0s, res, p->opt.stream);
+    }
     memset(res, 0, sizeof(*res));
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = stream_of(p);
@@ -1597,7 +1887,9 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     const int precision = o.precision;
     const bool polish = precision != IMRT_FP32 && o.polish_iter > 0;
     const int first_iter = polish ? std::max(0, o.max_iter - std::min(o.polish_iter, o.max_iter)) : o.max_iter;
-    TRY(run_phase(p, precision, first_iter, o.x_init, x0_dev, res));
+    // the reduced phase may also end on its own relative change (polish_switch)
+    const double first_delta = polish && o.polish_switch > 0.0 ? std::max(o.delta, o.polish_switch) : o.delta;
+    TRY(run_phase(p, precision, first_iter, o.x_init, x0_dev, res, first_delta));
     DevState d = *p->st_host;
     res->iterations = d.iter;
     res->backtracks = d.total_bt;
@@ -1611,7 +1903,7 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
         // the polish gets the iterations the reduced phase left (at least polish_iter): a
         // reduced phase that stalls early hands the rest of the budget to the FP32 copy
         const int budget = std::max(std::min(o.polish_iter, o.max_iter), o.max_iter - d.iter);
-        imrt_status ps = run_phase(p, IMRT_FP32, budget, 2, p->g_stage, res);
+        imrt_status ps = run_phase(p, IMRT_FP32, budget, 2, p->g_stage, res, o.delta);
         p->opt.trace = trace_saved;
         TRY(ps);
         d = *p->st_host;
@@ -1625,15 +1917,7 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     res->lambda0 = o.lambda0 > 0.0 ? o.lambda0 : p->lambda0_rule;
     p->last_iterations = res->iterations;
     res->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (d.status != IMRT_OK) {
-        const char* what = d.status == IMRT_ELINESEARCH ? "line search exceeded max_backtracks"
-                           : d.status == IMRT_ENUMERIC  ? "non-finite dose or objective"
-                           : d.status == IMRT_ETIMEOUT  ? "timeout"
-                           : d.status == IMRT_ECANCELLED ? "cancelled"
-                           : d.status == IMRT_EINVAL     ? "x0 must be finite and >= 0"
-                                                         : "device error";
-        set_error("solve stopped: %s", what);
-    }
+    if (d.status != IMRT_OK) set_error("solve stopped: %s", status_text(d.status));
     return (imrt_status)d.status;
 }
 
@@ -1644,14 +1928,18 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<imrt_plan*> ps(plans, plans + count);
+    bool team = true;
     for (int i = 0; i < count; ++i) {
         if (!ps[i]) return set_error("plan %d is NULL", i), IMRT_EINVAL;
         for (int j = 0; j < i; ++j)
             if (ps[j] == ps[i]) return set_error("plan %d appears twice in the batch", i), IMRT_EINVAL;
+        team = team && ps[i]->opt.solver == IMRT_SOLVER_TEAM;
     }
+    auto phase = team ? run_team_phase : run_batch_phase;
     std::vector<imrt_result> res(count);
     memset(res.data(), 0, sizeof(imrt_result) * count);
     std::vector<int> prec(count), iters(count), xinit(count);
+    std::vector<double> delta(count);
     std::vector<const float*> x0(count, nullptr);
     for (int i = 0; i < count; ++i) {
         imrt_plan* p = ps[i];
@@ -1668,11 +1956,13 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         prec[i] = o.precision;
         iters[i] = polish ? std::max(0, o.max_iter - std::min(o.polish_iter, o.max_iter)) : o.max_iter;
         xinit[i] = o.x_init;
+        delta[i] = polish && o.polish_switch > 0.0 ? std::max(o.delta, o.polish_switch) : o.delta;
     }
-    TRY(run_batch_phase(ps, prec, iters, xinit, x0, s, res));
+    TRY(phase(ps, prec, iters, xinit, x0, delta, s, res));
     // FP32 polish of the reduced-precision plans that ended without an error
     std::vector<imrt_plan*> pp;
     std::vector<int> pidx, pprec, piters, pxinit;
+    std::vector<double> pdelta;
     std::vector<const float*> px0;
     for (int i = 0; i < count; ++i) {
         imrt_plan* p = ps[i];
@@ -1693,6 +1983,7 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
             pprec.push_back(IMRT_FP32);
             piters.push_back(std::max(std::min(p->opt.polish_iter, p->opt.max_iter), p->opt.max_iter - d.iter));
             pxinit.push_back(2);
+            pdelta.push_back(p->opt.delta);
             px0.push_back(p->g_stage);
         }
     }
@@ -1704,7 +1995,7 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         }
         std::vector<imrt_result> pres(pp.size());
         memset(pres.data(), 0, sizeof(imrt_result) * pp.size());
-        const imrt_status st = run_batch_phase(pp, pprec, piters, pxinit, px0, s, pres);
+        const imrt_status st = phase(pp, pprec, piters, pxinit, px0, pdelta, s, pres);
         for (size_t k = 0; k < pp.size(); ++k) pp[k]->opt.trace = saved[k];
         TRY(st);
         for (size_t k = 0; k < pp.size(); ++k) {
@@ -1719,6 +2010,7 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
             r.launches += pres[k].launches;
             r.passes += pres[k].passes;
             r.grad_passes += pres[k].grad_passes;
+            r.bytes += pres[k].bytes;
         }
     }
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1731,7 +2023,10 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         results[i] = res[i];
         if (first == IMRT_OK && res[i].status != IMRT_OK) first = (imrt_status)res[i].status;
     }
-    if (first != IMRT_OK) set_error("at least one solve of the batch stopped with status %d", (int)first);
+    if (first != IMRT_OK) {
+        if (count == 1) set_error("solve stopped: %s", status_text(first));
+        else set_error("at least one solve of the batch stopped with status %d", (int)first);
+    }
     return first;
 }
 
@@ -1809,14 +2104,7 @@ imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     const SellCopy& c = copy_of(p, p->opt.precision);
     info->sell_entries = c.entries;
     info->t_entries = p->t_H > 0 ? p->tq_entries : p->t_entries;
-    const int64_t vb = (int64_t)elem_bytes(p->opt.precision), cb = c.fmt == IMRT_FP32 ? 4 : 2;
-    // CSR-equivalent algorithmic bytes: values + indices + row offsets + x + (z, r writes; mask and
-    // r-order reads)
-    info->fwd_bytes = p->nnz * (vb + cb) + (int64_t)(p->m + 1) * 8 + (int64_t)p->n * 4 + (int64_t)p->m * 13;
-    info->bwd_bytes = p->t_H == 0
-                          ? p->nnz * (vb + 4) + (int64_t)(p->n + 1) * 8 + (int64_t)p->m * 4 + (int64_t)p->n * 4
-                          : p->nnz * (vb + 2) + ((int64_t)p->n * p->t_H + 1) * 8 + (int64_t)p->m * 4 +
-                                (int64_t)p->n * 4;
+    pass_bytes(p, p->opt.precision, &info->fwd_bytes, &info->bwd_bytes);
     info->device_bytes = p->device_bytes;
     FwdShape* sh = nullptr;
     if (get_shape(p, p->opt.precision, p->opt.k_trials, &sh) == IMRT_OK) {

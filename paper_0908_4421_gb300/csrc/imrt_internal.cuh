@@ -227,6 +227,62 @@ struct BwdArgs {
     int32_t m_pad, guard;     // r = r_sets + cur * m_pad (0: a fixed r); guard: skip unless st->need_grad
 };
 
+// Persistent multi-plan solver (team.cu). One cooperative launch holds a set of plans of one
+// storage format; its CTAs form teams, and each team solves its plans one after another,
+// each completely (all iterations) inside the launch. Every CTA of a team runs the Armijo
+// controller on the same sums in the same order, so all take identical decisions; the
+// objective is summed from one partial per slice and every g_i is reduced by one warp, in
+// fixed orders, so a plan's result does not depend on its team's size or on the other plans
+// of the launch.
+struct TeamPlan {
+    // voxel-major SELL copy at the phase's precision
+    const int64_t* slice_off;
+    const int32_t* slice_len;
+    const void* val;
+    const void* col;
+    const int32_t* busy;      // slices holding entries, longest first (n_busy)
+    const int32_t* idle;      // slices without entries (n_idle): z = 0, evaluated once per solve
+    const uint8_t* mask;      // m_pad, permuted order
+    const int32_t* r_index;   // m_pad: the caller's index of permuted voxel p
+    const float* scale;       // n_pad per-beamlet value scale of a reduced copy, or NULL (FP32)
+    const float* vt;          // per-voxel targets (permuted), or NULL
+    const uint8_t* vtm;
+    const Terms* terms;
+    // beamlet-major segmented copy (16-bit voxel offsets in segments of 65536 voxels)
+    const int32_t* rows;      // beamlet rows, longest first
+    const int64_t* seg;       // n * H + 1
+    const uint16_t* lo;
+    const void* tval;
+    Vecs v;
+    double* obj;              // 2 * kMaxTrials * n_slices: objective partial of each slice and step size,
+                              // in two buffers that alternate between forward passes
+    DevState* st;
+    const SolveParams* sp;
+    unsigned int* sync;       // [4]: barrier arrivals, stop request; zeroed before every launch
+    int32_t m, n, n_pad, m_pad, n_slices, n_busy, n_idle, H;
+    int32_t team0, team_size; // the team's first CTA and its size
+    int32_t pad[2];
+};
+
+struct TeamArgs {
+    const TeamPlan* plans;
+    const int32_t* cta_team;    // grid: team of each CTA, -1 for a CTA without a team
+    const int32_t* team_first;  // n_teams + 1: each team's plans are team_plan[team_first[t] ..]
+    const int32_t* team_plan;   // plan indices in the order each team solves them
+    int32_t n_plans, n_teams;
+};
+
+constexpr int kTeamThreads = 512;
+constexpr unsigned kTeamSpinLimit = 1u << 24;  // barrier polls before a team gives up (about 1.5 s)
+
+// Launches the team solver for SELL format `fmt` (kFmtF32C16, IMRT_FP16, IMRT_BF16,
+// IMRT_FP8E4M3) as a cooperative grid of `grid` CTAs with `smem` bytes of dynamic shared memory.
+cudaError_t launch_team(int fmt, const TeamArgs& args, int grid, size_t smem, cudaStream_t stream);
+// Resident team CTAs per SM at `smem` dynamic bytes (0 if the format has no team kernel).
+int team_ctas_per_sm(int fmt, size_t smem);
+// Dynamic shared memory of a team CTA for a plan of n_pad beamlets at k_trials step sizes.
+inline size_t team_smem_bytes(int n_pad, int k_trials) { return (size_t)n_pad * 4u * (size_t)(2 + k_trials); }
+
 // Sets the message imrt_last_error() returns on this thread (api.cu).
 void set_last_error_message(const char* msg);
 

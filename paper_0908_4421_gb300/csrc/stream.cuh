@@ -1,0 +1,287 @@
+// Device helpers shared by the solver kernels (sm_103a): the per-voxel penalty of Eq. (1),
+// the storage formats of the voxel-major SELL copy, 128-bit streaming of a slice row with
+// the x gather from shared memory, and warp reductions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "../../include/imrt.h"
+#include "imrt_internal.cuh"
+#include "ptx.cuh"
+
+namespace imrt {
+
+// Tuning knobs of the warp-streaming forward kernel (compile-time).
+#ifndef IMRT_FWD_MINB1
+#define IMRT_FWD_MINB1 1  // resident CTAs per SM the single-trial instance is built for
+#endif
+#ifndef IMRT_FWD_MINB_Q
+#define IMRT_FWD_MINB_Q 1  // resident CTAs per SM for the 16-bit formats (1 or 2)
+#endif
+#ifndef IMRT_FWD_UNROLL
+#define IMRT_FWD_UNROLL 8  // groups in flight per lane (FP8: half as many, each is 48 bytes)
+#endif
+#ifndef IMRT_BWD_PREFETCH_KB
+#define IMRT_BWD_PREFETCH_KB 64  // forward tail: L2 prefetch (KB per row) of the next transposed pass's first rows
+#endif
+
+// ---------------------------------------------------------------------------
+// Per-voxel penalty (Eq. (1)): F_j and r_j = dF_j / dz_j at dose z.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void penalty(float z, uint32_t bits, const Terms& T, double& F, float& r, float tj = 0.0f,
+                                        uint32_t tg = 0u) {
+    F = 0.0;
+    r = 0.0f;
+    if (T.has_vt) {  // per-voxel dose T_j (Eq. (1) as printed)
+        const float eo = z - tj;
+        if (eo > 0.0f) {
+            F += T.vcod * ((double)eo * (double)eo);
+            r += 2.0f * T.vco * eo;
+        }
+        const float eu = tj - z;
+        if (tg && eu > 0.0f) {
+            F += T.vcud * ((double)eu * (double)eu);
+            r -= 2.0f * T.vcu * eu;
+        }
+    }
+    while (bits) {
+        const int s = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if ((T.has_u >> s) & 1u) {
+            const float e = T.Tu[s] - z;
+            if (e > 0.0f) {
+                F += T.cud[s] * ((double)e * (double)e);
+                r -= 2.0f * T.cu[s] * e;
+            }
+        }
+        if ((T.has_o >> s) & 1u) {
+            const float e = z - T.To[s];
+            if (e > 0.0f) {
+                F += T.cod[s] * ((double)e * (double)e);
+                r += 2.0f * T.co[s] * e;
+            }
+        }
+    }
+    if (!isfinite(z)) F = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+__device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T, uint32_t tg = 0u) {
+    float c = T.has_vt ? T.vco + (tg ? T.vcu : 0.0f) : 0.0f;
+    while (bits) {
+        const int s = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if ((T.has_u >> s) & 1u) c += T.cu[s];
+        if ((T.has_o >> s) & 1u) c += T.co[s];
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Storage formats of the voxel-major copy. GE = entries per 16-byte value load.
+// ---------------------------------------------------------------------------
+// VB / CB: bytes of values / column indices per lane and group.
+// SELL copy formats. KIND: 0 FP32 values / int32 columns, 1 FP32 values / 16-bit columns,
+// 2 FP16 / 16-bit, 3 BF16 / 16-bit, 4 FP8-e4m3 / 16-bit. GE entries per lane and group;
+// VB / CB bytes of values / columns per lane and group.
+struct FmtF32 {
+    static constexpr int GE = 4, VB = 16, CB = 16, KIND = 0;
+};
+struct FmtF32C16 {
+    static constexpr int GE = 8, VB = 32, CB = 16, KIND = 1;
+};
+struct FmtF16 {
+    static constexpr int GE = 8, VB = 16, CB = 16, KIND = 2;
+};
+struct FmtBF16 {
+    static constexpr int GE = 8, VB = 16, CB = 16, KIND = 3;
+};
+struct FmtF8 {
+    static constexpr int GE = 16, VB = 16, CB = 32, KIND = 4;
+};
+
+// acc[q] += v * xs[c * KT + q] for one entry (x_t of all trials interleaved in shared memory).
+template <int KT>
+__device__ __forceinline__ void fma_entry(float v, int c, const float* __restrict__ xs, float (&acc)[KT]) {
+    if constexpr (KT == 1) {
+        acc[0] = fmaf(v, xs[c], acc[0]);
+    } else if constexpr (KT == 2) {
+        const float2 xv = *reinterpret_cast<const float2*>(xs + 2 * c);
+        acc[0] = fmaf(v, xv.x, acc[0]);
+        acc[1] = fmaf(v, xv.y, acc[1]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < KT; h += 4) {
+            const float4 xv = *reinterpret_cast<const float4*>(xs + KT * c + h);
+            acc[h + 0] = fmaf(v, xv.x, acc[h + 0]);
+            acc[h + 1] = fmaf(v, xv.y, acc[h + 1]);
+            acc[h + 2] = fmaf(v, xv.z, acc[h + 2]);
+            acc[h + 3] = fmaf(v, xv.w, acc[h + 3]);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 h2f(uint32_t w) {
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h);
+}
+__device__ __forceinline__ float2 b2f(uint32_t w) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+    return __bfloat1622float2(h);
+}
+__device__ __forceinline__ float2 e4m3x2f(uint16_t w) {
+    __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w), __NV_E4M3);
+    __half2 h = *reinterpret_cast<__half2*>(&hr);
+    return __half22float2(h);
+}
+
+// One group of one lane: GE consecutive entries of the lane's row (values, then columns).
+struct GroupRegs {
+    uint4 v;   // FP32: 4 values; FP16 / BF16: 8 values; FP8: 16 values
+    uint4 c0;  // FP32: 4 int32 columns; 16-bit formats: 8 uint16 columns
+    uint4 c1;  // FP8: columns 8..15
+};
+
+template <class F>
+__device__ __forceinline__ void load_group(const void* __restrict__ val, const void* __restrict__ col, int64_t off,
+                                           int k, int lane, GroupRegs& g) {
+    if constexpr (F::KIND == 0) {
+        g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 32 + lane);
+        g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const int32_t*>(col) + off) + (size_t)k * 32 + lane);
+    } else if constexpr (F::KIND == 1) {  // 8 FP32 values (two words), 8 16-bit columns
+        const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 64 + 2 * lane;
+        g.v = ld_stream(vp);
+        g.c1 = ld_stream(vp + 1);
+        g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane);
+    } else if constexpr (F::GE == 8) {
+        g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + off) + (size_t)k * 32 + lane);
+        g.c0 = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane);
+    } else {
+        const uint4* cp = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 64 + 2 * lane;
+        g.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(val) + off) + (size_t)k * 32 + lane);
+        g.c0 = ld_stream(cp);
+        g.c1 = ld_stream(cp + 1);
+    }
+}
+
+// acc[q] += the group's entries in storage order.
+template <class F, int KT>
+__device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __restrict__ xs, float (&acc)[KT]) {
+    const uint32_t vv[4] = {g.v.x, g.v.y, g.v.z, g.v.w};
+    const uint32_t cc[4] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w};
+    if constexpr (F::KIND == 0) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) fma_entry<KT>(__uint_as_float(vv[h]), (int)cc[h], xs, acc);
+    } else if constexpr (F::KIND == 1) {
+        const uint32_t v8[8] = {g.v.x, g.v.y, g.v.z, g.v.w, g.c1.x, g.c1.y, g.c1.z, g.c1.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            fma_entry<KT>(__uint_as_float(v8[2 * h]), (int)(cc[h] & 0xffffu), xs, acc);
+            fma_entry<KT>(__uint_as_float(v8[2 * h + 1]), (int)(cc[h] >> 16), xs, acc);
+        }
+    } else if constexpr (F::GE == 8) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 f = std::is_same<F, FmtF16>::value ? h2f(vv[h]) : b2f(vv[h]);
+            fma_entry<KT>(f.x, (int)(cc[h] & 0xffffu), xs, acc);
+            fma_entry<KT>(f.y, (int)(cc[h] >> 16), xs, acc);
+        }
+    } else {
+        const uint32_t c8[8] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w, g.c1.x, g.c1.y, g.c1.z, g.c1.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 lo = e4m3x2f((uint16_t)(vv[h] & 0xffffu));
+            const float2 hi = e4m3x2f((uint16_t)(vv[h] >> 16));
+            fma_entry<KT>(lo.x, (int)(c8[2 * h] & 0xffffu), xs, acc);
+            fma_entry<KT>(lo.y, (int)(c8[2 * h] >> 16), xs, acc);
+            fma_entry<KT>(hi.x, (int)(c8[2 * h + 1] & 0xffffu), xs, acc);
+            fma_entry<KT>(hi.y, (int)(c8[2 * h + 1] >> 16), xs, acc);
+        }
+    }
+}
+
+// One row (one lane) of a slice: acc[q] += the row's entries in groups [g0, g1), in storage
+// order. Default: two register stages of IMRT_FWD_UNROLL / 2 groups; the 128-bit loads of the
+// next stage are issued before the current stage is used, so loads stay in flight while the
+// lane gathers x and accumulates. Otherwise: rounds of IMRT_FWD_UNROLL groups, all loads of
+// a round before any use. The last groups are guarded (the guard is uniform across the warp).
+#ifndef IMRT_FWD_PIPE
+#define IMRT_FWD_PIPE 1  // 1: software-pipelined rounds (the next round's loads before this round's use)
+#endif
+template <class F, int KT>
+__device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, const void* __restrict__ col,
+                                              int64_t off, int g0, int g1, int lane, const float* __restrict__ xs,
+                                              float (&acc)[KT]) {
+#if IMRT_FWD_PIPE
+    // two register stages of U groups: while one stage is consumed the other is in flight
+    constexpr bool q16 = F::KIND == 2 || F::KIND == 3;
+    constexpr int U = (F::KIND == 4 || KT >= 4 || (q16 && IMRT_FWD_MINB_Q > 1)) ? 2
+                      : F::KIND == 1                                              ? 3
+                                                                                  : IMRT_FWD_UNROLL / 2;
+    GroupRegs a[U], b[U];
+    auto load = [&](GroupRegs(&r)[U], int k) {
+#pragma unroll
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) load_group<F>(val, col, off, k + h, lane, r[h]);
+    };
+    auto use = [&](const GroupRegs(&r)[U], int k) {
+#pragma unroll
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) fma_group<F, KT>(r[h], xs, acc);
+    };
+    int k = g0;
+    if (k < g1) load(a, k);
+    while (k < g1) {
+        if (k + U < g1) load(b, k + U);
+        use(a, k);
+        k += U;
+        if (k >= g1) break;
+        if (k + U < g1) load(a, k + U);
+        use(b, k);
+        k += U;
+    }
+#else
+    // FP8 groups are 48 bytes and four or more trials need their accumulators: half the rounds
+    constexpr int U = ((F::KIND == 4 || F::KIND == 1 || KT >= 4) && IMRT_FWD_UNROLL > 4) ? IMRT_FWD_UNROLL / 2
+                                                                                       : IMRT_FWD_UNROLL;
+    for (int k = g0; k < g1; k += U) {
+        GroupRegs r[U];
+#pragma unroll
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) load_group<F>(val, col, off, k + h, lane, r[h]);
+#pragma unroll
+        for (int h = 0; h < U; ++h)
+            if (k + h < g1) fma_group<F, KT>(r[h], xs, acc);
+    }
+#endif
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Copies a POD struct between global and shared memory with all threads of the CTA.
+template <class T>
+__device__ __forceinline__ void cta_copy_in(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(dst)[i] = __ldcg(reinterpret_cast<const uint32_t*>(src) + i);
+}
+template <class T>
+__device__ __forceinline__ void cta_copy_out(T* dst, const T* src) {
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
+}
+
+}  // namespace imrt

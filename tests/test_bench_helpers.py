@@ -5,7 +5,7 @@ import shutil
 
 import bench
 
-FILES = ("kernels.cu", "imrt_internal.cuh", "ptx.cuh", "format.cu", "api.cu")
+FILES = bench.SOURCE_FILES
 
 
 def copy_tree(tmp_path):
