@@ -191,6 +191,72 @@ def run_reference(args, rank, world):
     return 0
 
 
+def batch_block(peak: float) -> dict:
+    """64 uneven plans (seeds 0-63: spacing {2.5, 4, 5} mm, 5/7/9 beams, 5/10 mm beamlets, PTV
+    radii x U(0.8, 1.2), k_trials from {1, 4, 8}, FP16 D with the FP32 polish) solved in one
+    persistent launch per phase, against the same plans one after another."""
+    from paper_0908_4421_gb300 import batch as B
+    cases = B.make_cases(64)
+    plans = B.make_plans(cases)
+    try:
+        out = B.run(plans, repeats=5)
+    finally:
+        for p in plans:
+            p.close()
+    out["workload"] = "64 jittered tiny-family phantoms (seeds 0-63), k_trials in {1,4,8}, FP16 D + FP32 polish"
+    out["frac_of_peak"] = out["aggregate_gbs"] / peak
+    return out
+
+
+def serve_block(n_requests: int) -> dict:
+    """Poisson streams of re-planning requests (the tiny phantom with the PTV shifted by up to
+    +-5 mm and D regenerated; 50 patients in turn, warm start from each patient's last x):
+    sequential plain FP32 solves against the batched mixed-precision form (FP16 D, FP32 polish,
+    team solver, resident patient plans), at 20 Hz and at a rate that saturates the sequential
+    form; p50 / p99 time-to-plan, plans per second, and the batched form's objective error
+    against the FP64 oracle on a sample of its requests."""
+    import oracle
+    from paper_0908_4421_gb300 import serve as S
+    specs = [phantom.jittered_spec(500000 + i, shift_mm=5.0, vary=False) for i in range(n_requests)]
+    cases = [phantom.make_case(sp) for sp in specs]
+    patients = [f"patient{i % 50}" for i in range(n_requests)]
+    out = {"requests": n_requests, "geometry": "tiny phantom, PTV shift U(+-5 mm), D regenerated",
+           "forms": {k: {"workers": v["workers"], "batched": v["batched"], "precision": v["options"].precision,
+                         "solver": v["options"].solver} for k, v in S.FORMS.items()}}
+    for rate, count in ((20.0, min(200, n_requests)), (1000.0, n_requests)):
+        for form in S.FORMS:
+            kw = dict(S.FORMS[form])
+            srv = S.ReplanServer(warm_start=True, **kw)
+            try:
+                futs = S.poisson_stream(srv, cases[:count], rate, seed=7, patients=patients[:count])
+                for f in futs:
+                    f.result()
+            finally:
+                srv.close()
+            st = srv.stats()
+            if form.startswith("batched") and rate > 100:
+                # objective error of a sample of served requests against the oracle on the same start
+                orc = oracle.get()
+                errs = []
+                res = sorted(srv.results(), key=lambda r: r.request_id)
+                for r in res[:: max(1, len(res) // 12)]:
+                    c = cases[r.request_id]
+                    with S.Plan.from_case(c, S.Options()) as p:
+                        lam0 = p.info()["lambda0_rule"]
+                    x0 = None
+                    prev = [q for q in res if q.patient == r.patient and q.request_id < r.request_id]
+                    if prev and prev[-1].x.shape[0] == c.n:
+                        x0 = prev[-1].x.astype(np.float64)
+                    ref = orc.solve(c, lambda0=lam0, max_iter=200, x_init=2 if x0 is not None else 0, x0=x0,
+                                    trace=False)
+                    G_served = orc.eval(c, r.x.astype(np.float64), gradient=False)[0]
+                    errs.append(abs(G_served - ref.objective) / ref.objective)
+                st["objective_rel_err_max"] = max(errs)
+                st["objective_rel_err_sample"] = len(errs)
+            out[f"{form}@{rate:g}Hz"] = st
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,6 +272,9 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision forms")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven plans (64 plans, FP16)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the re-planning serving streams")
+    ap.add_argument("--serve-requests", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -384,6 +453,15 @@ def main():
                            "bytes_per_pass": {"forward": fi["fwd_bytes"], "transposed": fi["bwd_bytes"]},
                            **errors(x_)}
 
+    # batched uneven plans: 64 jittered phantoms in the persistent multi-plan kernel
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = batch_block(peak)
+    # re-planning streams: sequential plain FP32 against the batched mixed-precision form
+    serve_out = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serve_out = serve_block(args.serve_requests)
+
     traffic = profiled_traffic(dominant, args.workload)
     lat = sorted(times)
     line = {
@@ -411,6 +489,8 @@ def main():
         "latency_p50_s": lat[len(lat) // 2], "latency_p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
         "cpu_baseline": cpu,
         "forms": forms,
+        "batch": batch,
+        "serve": serve_out,
         "e2e": None if e2e_s is None else {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "includes": "plan_create from pinned host CSR (copy, layouts, step-size rule), plan_solve, "
                             "plan_get_x and plan_dose to host", "plan_create_s": create_s},

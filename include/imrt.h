@@ -189,6 +189,20 @@ imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_
                         const float* thresholds, const float* weights, const imrt_options* opt,
                         imrt_plan** out);
 
+/*
+ * Rebuilds the plan in place from a new D, structures and terms (the arguments as for
+ * plan_create; m, n and nnz may change). Serves re-planning (Sec. 1, Sec. 2.1): a patient's
+ * plan stays resident and each new fraction's D replaces the old one. The options, the
+ * handle and the host-side state are kept; the old layouts go back to the library's device
+ * pool in stream order and the rebuild takes the memory from there, so a re-plan of similar
+ * size maps no new device memory. Per-voxel targets and traces are dropped (set them again).
+ * The result equals that of a plan created from the same inputs with the same options.
+ * Errors: as for plan_create; after a failed rebuild the plan holds no matrix and every
+ * call on it but plan_update and plan_destroy returns IMRT_EINVAL.
+ */
+imrt_status plan_update(imrt_plan* plan, const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
+                        const float* thresholds, const float* weights);
+
 /* Replaces the plan's options (the stream, step parameters, mode, trace...). */
 imrt_status plan_set_options(imrt_plan* plan, const imrt_options* opt);
 

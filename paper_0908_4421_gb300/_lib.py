@@ -26,7 +26,7 @@ SOLVER_GRAPH, SOLVER_TEAM = 0, 1
 EXPORTS = ("imrt_default_options", "plan_create", "plan_set_options", "plan_solve", "plan_dose", "plan_eval",
            "plan_get_x", "plan_get_trace", "plan_info", "plan_cancel", "plan_destroy", "imrt_last_error",
            "imrt_version", "imrt_eval_csr_noalloc", "plan_solve_batch", "plan_set_voxel_targets",
-           "imrt_trim_memory")
+           "imrt_trim_memory", "plan_update")
 
 
 class imrt_csr(ctypes.Structure):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.imrt_default_options.argtypes = [P(imrt_options)]
     lib.plan_create.restype = ctypes.c_int
     lib.plan_create.argtypes = [P(imrt_csr), vp, ctypes.c_int32, vp, vp, P(imrt_options), P(vp)]
+    lib.plan_update.restype = ctypes.c_int
+    lib.plan_update.argtypes = [vp, P(imrt_csr), vp, ctypes.c_int32, vp, vp]
     lib.plan_set_options.restype = ctypes.c_int
     lib.plan_set_options.argtypes = [vp, P(imrt_options)]
     lib.plan_solve.restype = ctypes.c_int

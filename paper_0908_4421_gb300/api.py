@@ -87,6 +87,24 @@ def _is_torch_cuda(a) -> bool:
     return hasattr(a, "is_cuda") and bool(a.is_cuda)
 
 
+def _matrix_args(row_ptr, col, val, mask, thresholds, weights, m, n):
+    """(imrt_csr, mask, thresholds, weights, arrays to keep alive) for plan_create / plan_update."""
+    on_device = _is_torch_cuda(val)
+    if not on_device:
+        row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float32)
+    if not _is_torch_cuda(mask):
+        mask = np.ascontiguousarray(mask, np.uint8)
+    thr = np.ascontiguousarray(thresholds, np.float32)
+    w = np.ascontiguousarray(weights, np.float32)
+    m = int(m if m is not None else row_ptr.shape[0] - 1)
+    if n is None:
+        raise ValueError("n (number of beamlets) is required")
+    csr = L.imrt_csr(m, int(n), int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val), 1 if on_device else 0)
+    return csr, mask, thr, w, (row_ptr, col, val)
+
+
 class Plan:
     """One planning problem resident on the GPU (plan_create / plan_destroy)."""
 
@@ -95,26 +113,26 @@ class Plan:
         lib = L.load()
         self._lib = lib
         self.options = options or Options()
-        on_device = _is_torch_cuda(val)
-        if not on_device:
-            row_ptr = np.ascontiguousarray(row_ptr, np.int64)
-            col = np.ascontiguousarray(col, np.int32)
-            val = np.ascontiguousarray(val, np.float32)
-        if not _is_torch_cuda(mask):
-            mask = np.ascontiguousarray(mask, np.uint8)
-        thr = np.ascontiguousarray(thresholds, np.float32)
-        w = np.ascontiguousarray(weights, np.float32)
-        m = int(m if m is not None else row_ptr.shape[0] - 1)
-        nnz = int(col.shape[0])
-        if n is None:
-            raise ValueError("n (number of beamlets) is required")
-        csr = L.imrt_csr(m, int(n), nnz, _ptr(row_ptr), _ptr(col), _ptr(val), 1 if on_device else 0)
+        csr, mask, thr, w, keep = _matrix_args(row_ptr, col, val, mask, thresholds, weights, m, n)
         handle = ctypes.c_void_p()
         opts = self.options.to_c()
         L.check(lib.plan_create(ctypes.byref(csr), _ptr(mask), thr.shape[0], _ptr(thr), _ptr(w),
                                 ctypes.byref(opts), ctypes.byref(handle)))
         self._h = handle
-        self.m, self.n = m, int(n)
+        self.m, self.n = csr.m, csr.n
+
+    def update(self, row_ptr, col, val, mask, thresholds, weights, m: Optional[int] = None,
+               n: Optional[int] = None) -> None:
+        """plan_update: rebuilds this plan in place from a new D (sizes may change)."""
+        csr, mask, thr, w, keep = _matrix_args(row_ptr, col, val, mask, thresholds, weights, m, n)
+        L.check(self._lib.plan_update(self._h, ctypes.byref(csr), _ptr(mask), thr.shape[0], _ptr(thr), _ptr(w)))
+        self.m, self.n = csr.m, csr.n
+
+    def update_from_case(self, case) -> None:
+        self.update(case.row_ptr, case.col, case.val, case.mask, case.thresholds, case.weights, m=case.m, n=case.n)
+        vt = getattr(case, "voxel_targets", None)
+        if vt is not None:
+            self.set_voxel_targets(vt.dose, vt.target, vt.w_under, vt.w_over, vt.normalise)
 
     @classmethod
     def from_case(cls, case, options: Optional[Options] = None, device: bool = False) -> "Plan":
