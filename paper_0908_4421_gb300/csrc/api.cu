@@ -213,6 +213,7 @@ struct imrt_plan {
     // (longest first), built on first use, and the slice objective partials
     struct TeamSlices {
         int32_t* busy = nullptr;
+        TeamUnit* units = nullptr;
         int32_t* idle = nullptr;
         int32_t n_busy = -1, n_idle = 0;
     } team32, teamq;
@@ -1000,12 +1001,53 @@ imrt_status alloc_vectors(imrt_plan* p) {
     CK(cudaMemsetAsync(p->x_stage, 0, sizeof(float) * p->n_pad, s));
     CK(cudaMemsetAsync(p->g_stage, 0, sizeof(float) * p->n_pad, s));
     CK(cudaMemsetAsync(p->st, 0, sizeof(DevState), s));
+    return IMRT_OK;
+}
+
+// Host-side state a plan keeps for its whole life (kept by plan_update): the mapped pinned
+// block of state read-back and cancel flag, and the profiling events.
+imrt_status acquire_host_state(imrt_plan* p) {
     TRY(pinned_acquire(&p->pinned));
     p->st_host = &p->pinned->state;
     p->cancel_host = &p->pinned->cancel;
     *p->cancel_host = 0;
     CK(cudaHostGetDevicePointer((void**)&p->cancel_dev, p->cancel_host, 0));
     for (auto& e : p->ev) CK(cudaEventCreate(&e));
+    return IMRT_OK;
+}
+
+// Argument checks shared by plan_create and plan_update.
+imrt_status validate_inputs(const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
+                            const float* thresholds, const float* weights, const imrt_options& o) {
+    if (!D || !structures || !thresholds || !weights) return set_error("NULL argument"), IMRT_EINVAL;
+    if (D->m < 1 || D->n < 1 || D->nnz < 0) return set_error("need m >= 1, n >= 1, nnz >= 0"), IMRT_EINVAL;
+    if (D->nnz > 0 && (!D->row_ptr || !D->col_idx || !D->val)) return set_error("NULL CSR array"), IMRT_EINVAL;
+    if (!D->row_ptr) return set_error("NULL row_ptr"), IMRT_EINVAL;
+    if (n_structures < 1 || n_structures > kMaxStruct) return set_error("n_structures must be 1..8"), IMRT_EINVAL;
+    if ((int64_t)D->m > (int64_t)INT32_MAX - 1024) return set_error("m too large"), IMRT_EUNSUPPORTED;
+    for (int i = 0; i < 2 * n_structures; ++i)
+        if (!(weights[i] >= 0.0f) || !std::isfinite(weights[i]) || std::isinf(thresholds[i]))
+            return set_error("weights must be finite and >= 0; thresholds finite or NaN"), IMRT_EINVAL;
+    if (o.precision != IMRT_FP32 && D->n > 65536)
+        return set_error("16-bit beamlet indices need n <= 65536"), IMRT_EUNSUPPORTED;
+    return IMRT_OK;
+}
+
+// Sizes of a plan for D; the shared-memory staging limit of the forward pass.
+imrt_status set_sizes(imrt_plan* p, const imrt_csr* D, int32_t n_structures) {
+    p->m = D->m;
+    p->n = D->n;
+    p->nnz = D->nnz;
+    p->S = n_structures;
+    p->n_pad = (int32_t)round_up(D->n, 4);
+    p->m_pad = (int32_t)round_up(D->m, kSlice);
+    p->n_slices = p->m_pad / kSlice;
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if ((size_t)p->n_pad * 8 + 4096 > (size_t)max_smem)
+        return set_error("n = %d beamlets exceeds the shared-memory staging limit (%d bytes per CTA)", p->n,
+                         max_smem),
+               IMRT_EUNSUPPORTED;
     return IMRT_OK;
 }
 
@@ -1403,11 +1445,18 @@ imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices
         std::vector<int32_t> busy, idle;
         for (int s = 0; s < p->n_slices; ++s) (c.host_cost[s] > 8 * kSlice ? busy : idle).push_back(s);
         std::stable_sort(busy.begin(), busy.end(), [&](int x, int y) { return c.host_cost[x] > c.host_cost[y]; });
+        std::vector<TeamUnit> units(busy.size());
+        for (size_t k = 0; k < busy.size(); ++k)
+            units[k] = TeamUnit{c.host_off[busy[k]], busy[k],
+                                (int32_t)((c.host_cost[busy[k]] - 8 * kSlice) / ((int64_t)kSlice * c.ge))};
         TRY(dalloc(p, &t.busy, std::max<size_t>(busy.size(), 1)));
+        TRY(dalloc(p, &t.units, std::max<size_t>(busy.size(), 1)));
         TRY(dalloc(p, &t.idle, std::max<size_t>(idle.size(), 1)));
         cudaStream_t s = stream_of(p);
-        if (!busy.empty())
+        if (!busy.empty()) {
             CK(cudaMemcpyAsync(t.busy, busy.data(), sizeof(int32_t) * busy.size(), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(t.units, units.data(), sizeof(TeamUnit) * units.size(), cudaMemcpyHostToDevice, s));
+        }
         if (!idle.empty())
             CK(cudaMemcpyAsync(t.idle, idle.data(), sizeof(int32_t) * idle.size(), cudaMemcpyHostToDevice, s));
         if (!p->team_obj) TRY(dalloc(p, &p->team_obj, (size_t)2 * kMaxTrials * std::max(p->n_slices, 1)));
@@ -1423,9 +1472,9 @@ imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices
 const char* team_unsupported(const imrt_plan* p, int precision, int max_smem) {
     if (p->t_H <= 0) return "the team solver needs at most 1048576 voxels (segmented beamlet-major copy)";
     if (copy_of(p, precision).fmt == IMRT_FP32) return "the team solver needs at most 65536 beamlets";
-    if (team_smem_bytes(p->n_pad, p->opt.k_trials) + 16384 > (size_t)max_smem)
-        return "the team solver stages x, g and the trial points in shared memory: n * (2 + k_trials) * 4 bytes "
-               "exceed it";
+    if (team_smem_bytes(p->n_pad, p->opt.k_trials, copy_of(p, precision).fmt) + 16384 > (size_t)max_smem)
+        return "the team solver stages x, g, the trial points (n * (2 + k_trials) * 4 bytes) and its copy rings "
+               "in shared memory: they exceed it";
     return nullptr;
 }
 
@@ -1545,6 +1594,7 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
             t.val = c.val;
             t.col = c.col;
             t.busy = ts->busy;
+            t.units = ts->units;
             t.idle = ts->idle;
             t.mask = p->mask;
             t.r_index = p->perm;
@@ -1572,7 +1622,7 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
             cost[k] = (double)std::max(max_iter[idx[k]], 1) *
                       (double)(p->nnz * 2 * (vb + 2) + (int64_t)p->m * 17 + (int64_t)p->n * 8);
             cap[k] = std::max(1, std::min(ts->n_busy, p->n) / 16);
-            smem = std::max(smem, team_smem_bytes(p->n_pad, p->opt.k_trials));
+            smem = std::max(smem, team_smem_bytes(p->n_pad, p->opt.k_trials, fmt));
         }
         const int per_sm = team_ctas_per_sm(fmt, smem);
         if (per_sm < 1) return set_error("the team solver does not fit on an SM"), IMRT_EUNSUPPORTED;
@@ -1636,6 +1686,14 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
 void imrt::set_last_error_message(const char* msg) { g_error = msg ? msg : ""; }
 
 namespace {
+// A plan whose plan_update failed holds no matrix; every call on it but plan_destroy and another
+// plan_update is refused.
+bool empty_plan(const imrt_plan* p) {
+    if (p->m > 0) return false;
+    set_error("the plan holds no matrix (its last plan_update failed)");
+    return true;
+}
+
 const char* status_text(int status) {
     return status == IMRT_ELINESEARCH ? "line search exceeded max_backtracks"
            : status == IMRT_ENUMERIC  ? "non-finite dose or objective"
@@ -1723,32 +1781,13 @@ imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_
     g_error.clear();
     if (!out) return set_error("out is NULL"), IMRT_EINVAL;
     *out = nullptr;
-    if (!D || !structures || !thresholds || !weights) return set_error("NULL argument"), IMRT_EINVAL;
-    if (D->m < 1 || D->n < 1 || D->nnz < 0) return set_error("need m >= 1, n >= 1, nnz >= 0"), IMRT_EINVAL;
-    if (D->nnz > 0 && (!D->row_ptr || !D->col_idx || !D->val)) return set_error("NULL CSR array"), IMRT_EINVAL;
-    if (!D->row_ptr) return set_error("NULL row_ptr"), IMRT_EINVAL;
-    if (n_structures < 1 || n_structures > kMaxStruct) return set_error("n_structures must be 1..8"), IMRT_EINVAL;
-    if ((int64_t)D->m > (int64_t)INT32_MAX - 1024) return set_error("m too large"), IMRT_EUNSUPPORTED;
-    for (int i = 0; i < 2 * n_structures; ++i)
-        if (!(weights[i] >= 0.0f) || !std::isfinite(weights[i]) || std::isinf(thresholds[i]))
-            return set_error("weights must be finite and >= 0; thresholds finite or NaN"), IMRT_EINVAL;
     imrt_options o;
     if (opt) o = *opt;
     else imrt_default_options(&o);
     TRY(validate_options(&o));
-    if (o.precision != IMRT_FP32 && D->n > 65536)
-        return set_error("16-bit beamlet indices need n <= 65536"), IMRT_EUNSUPPORTED;
-
+    TRY(validate_inputs(D, structures, n_structures, thresholds, weights, o));
     imrt_plan* p = new imrt_plan();
     p->opt = o;
-    p->m = D->m;
-    p->n = D->n;
-    p->nnz = D->nnz;
-    p->S = n_structures;
-    p->n_pad = (int32_t)round_up(D->n, 4);
-    p->m_pad = (int32_t)round_up(D->m, kSlice);
-    p->n_slices = p->m_pad / kSlice;
-    imrt_status st = IMRT_OK;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) {
@@ -1757,14 +1796,9 @@ imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_
         delete p;
         return IMRT_ECUDA;
     }
-    int max_smem = 0;
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    if ((size_t)p->n_pad * 8 + 4096 > (size_t)max_smem) {
-        set_error("n = %d beamlets exceeds the shared-memory staging limit (%d bytes per CTA)", p->n, max_smem);
-        delete p;
-        return IMRT_EUNSUPPORTED;
-    }
-    st = alloc_vectors(p);
+    imrt_status st = set_sizes(p, D, n_structures);
+    if (st == IMRT_OK) st = acquire_host_state(p);
+    if (st == IMRT_OK) st = alloc_vectors(p);
     if (st == IMRT_OK) st = plan_build(p, D, structures, thresholds, weights);
     if (st != IMRT_OK) {
         std::string msg = g_error;
@@ -1774,6 +1808,43 @@ imrt_status plan_create(const imrt_csr* D, const uint8_t* structures, int32_t n_
     }
     *out = p;
     return IMRT_OK;
+}
+
+imrt_status plan_update(imrt_plan* p, const imrt_csr* D, const uint8_t* structures, int32_t n_structures,
+                        const float* thresholds, const float* weights) {
+    g_error.clear();
+    if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    TRY(validate_inputs(D, structures, n_structures, thresholds, weights, p->opt));
+    // Release the old layouts in stream order: the library's pool keeps the memory, so the
+    // rebuild below takes the same blocks back without mapping new device memory.
+    forget_plan_batches(p);
+    for (auto& kv : p->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    for (void* a : p->allocations) cudaFreeAsync(a, stream_of(p));
+    imrt_plan fresh;
+    fresh.device = p->device;
+    fresh.sm_count = p->sm_count;
+    fresh.opt = p->opt;
+    fresh.pinned = p->pinned;
+    fresh.st_host = p->st_host;
+    fresh.cancel_host = p->cancel_host;
+    fresh.cancel_dev = p->cancel_dev;
+    for (int k = 0; k < 4; ++k) fresh.ev[k] = p->ev[k];
+    *p = std::move(fresh);
+    imrt_status st = set_sizes(p, D, n_structures);
+    if (st == IMRT_OK) st = alloc_vectors(p);
+    if (st == IMRT_OK) st = plan_build(p, D, structures, thresholds, weights);
+    if (st != IMRT_OK) {  // leave an empty plan that every call refuses; plan_destroy still frees it
+        std::string msg = g_error;
+        for (void* a : p->allocations) cudaFreeAsync(a, stream_of(p));
+        p->allocations.clear();
+        p->device_bytes = 0;
+        p->m = 0;
+        g_error = msg;
+    }
+    return st;
 }
 
 imrt_status plan_set_options(imrt_plan* p, const imrt_options* opt) {
@@ -1790,6 +1861,7 @@ imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_
                                    float w_over, int32_t normalise) {
     g_error.clear();
     if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    if (empty_plan(p)) return IMRT_EINVAL;
     cudaStream_t s = stream_of(p);
     g_temp_stream = s;
     // graphs captured the old arguments: rebuild them on the next solve
@@ -1867,6 +1939,7 @@ imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_
 imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     g_error.clear();
     if (!p || !res) return set_error("NULL argument"), IMRT_EINVAL;
+    if (empty_plan(p)) return IMRT_EINVAL;
     if (p->opt.solver == IMRT_SOLVER_TEAM) {  // a batch of one in the persistent multi-plan kernel
         const float* x0s[1] = {x0};
         return plan_solve_batch(&p, 1, x0s, res, p->opt.stream);
@@ -1931,6 +2004,7 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
     bool team = true;
     for (int i = 0; i < count; ++i) {
         if (!ps[i]) return set_error("plan %d is NULL", i), IMRT_EINVAL;
+        if (empty_plan(ps[i])) return IMRT_EINVAL;
         for (int j = 0; j < i; ++j)
             if (ps[j] == ps[i]) return set_error("plan %d appears twice in the batch", i), IMRT_EINVAL;
         team = team && ps[i]->opt.solver == IMRT_SOLVER_TEAM;
@@ -2043,6 +2117,7 @@ imrt_status plan_dose(imrt_plan* p, const float* x, float* z_out) {
 imrt_status plan_eval(imrt_plan* p, const float* x, double* G, float* z_out, float* g_out) {
     g_error.clear();
     if (!p) return set_error("NULL plan"), IMRT_EINVAL;
+    if (empty_plan(p)) return IMRT_EINVAL;
     cudaStream_t s = stream_of(p);
     const float* xs = p->v.x + (size_t)p->cur * p->n_pad;
     if (x) {
@@ -2068,6 +2143,7 @@ imrt_status plan_eval(imrt_plan* p, const float* x, double* G, float* z_out, flo
 imrt_status plan_get_x(imrt_plan* p, float* x_out) {
     g_error.clear();
     if (!p || !x_out) return set_error("NULL argument"), IMRT_EINVAL;
+    if (empty_plan(p)) return IMRT_EINVAL;
     cudaStream_t s = stream_of(p);
     CK(cudaMemcpyAsync(x_out, p->v.x + (size_t)p->cur * p->n_pad, sizeof(float) * p->n, cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
@@ -2094,6 +2170,7 @@ imrt_status plan_get_trace(imrt_plan* p, int32_t cap, double* G, double* lambda,
 imrt_status plan_info(const imrt_plan* pc, imrt_plan_info* info) {
     g_error.clear();
     if (!pc || !info) return set_error("NULL argument"), IMRT_EINVAL;
+    if (empty_plan(pc)) return IMRT_EINVAL;
     imrt_plan* p = const_cast<imrt_plan*>(pc);
     memset(info, 0, sizeof(*info));
     info->m = p->m;

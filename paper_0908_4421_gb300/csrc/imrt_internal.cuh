@@ -234,6 +234,13 @@ struct BwdArgs {
 // objective is summed from one partial per slice and every g_i is reduced by one warp, in
 // fixed orders, so a plan's result does not depend on its team's size or on the other plans
 // of the launch.
+// A forward work unit of the team solver: one slice with entries (16 bytes).
+struct __align__(16) TeamUnit {
+    int64_t off;  // the slice's first stored entry
+    int32_t s;    // slice
+    int32_t L;    // groups
+};
+
 struct TeamPlan {
     // voxel-major SELL copy at the phase's precision
     const int64_t* slice_off;
@@ -241,6 +248,7 @@ struct TeamPlan {
     const void* val;
     const void* col;
     const int32_t* busy;      // slices holding entries, longest first (n_busy)
+    const TeamUnit* units;    // the same slices as work units (n_busy)
     const int32_t* idle;      // slices without entries (n_idle): z = 0, evaluated once per solve
     const uint8_t* mask;      // m_pad, permuted order
     const int32_t* r_index;   // m_pad: the caller's index of permuted voxel p
@@ -280,8 +288,12 @@ constexpr unsigned kTeamSpinLimit = 1u << 24;  // barrier polls before a team gi
 cudaError_t launch_team(int fmt, const TeamArgs& args, int grid, size_t smem, cudaStream_t stream);
 // Resident team CTAs per SM at `smem` dynamic bytes (0 if the format has no team kernel).
 int team_ctas_per_sm(int fmt, size_t smem);
-// Dynamic shared memory of a team CTA for a plan of n_pad beamlets at k_trials step sizes.
-inline size_t team_smem_bytes(int n_pad, int k_trials) { return (size_t)n_pad * 4u * (size_t)(2 + k_trials); }
+// Dynamic shared memory of a team CTA: x, g and the trial points of a plan of n_pad beamlets at
+// k_trials step sizes, then the warps' copy rings for format `fmt` (team_ring_bytes).
+size_t team_ring_bytes(int fmt);
+inline size_t team_smem_bytes(int n_pad, int k_trials, int fmt) {
+    return (((size_t)n_pad * 4u * (size_t)(2 + k_trials) + 127) & ~(size_t)127) + team_ring_bytes(fmt);
+}
 
 // Sets the message imrt_last_error() returns on this thread (api.cu).
 void set_last_error_message(const char* msg);

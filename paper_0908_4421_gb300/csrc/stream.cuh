@@ -212,14 +212,16 @@ __device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __res
 #ifndef IMRT_FWD_PIPE
 #define IMRT_FWD_PIPE 1  // 1: software-pipelined rounds (the next round's loads before this round's use)
 #endif
-template <class F, int KT>
+template <class F, int KT, int UF = 0>
 __device__ __forceinline__ void slice_row_dot(const void* __restrict__ val, const void* __restrict__ col,
                                               int64_t off, int g0, int g1, int lane, const float* __restrict__ xs,
                                               float (&acc)[KT]) {
 #if IMRT_FWD_PIPE
     // two register stages of U groups: while one stage is consumed the other is in flight
+    // (UF > 0: a caller with less register room fixes U)
     constexpr bool q16 = F::KIND == 2 || F::KIND == 3;
-    constexpr int U = (F::KIND == 4 || KT >= 4 || (q16 && IMRT_FWD_MINB_Q > 1)) ? 2
+    constexpr int U = UF > 0 ? UF
+                      : (F::KIND == 4 || KT >= 4 || (q16 && IMRT_FWD_MINB_Q > 1)) ? 2
                       : F::KIND == 1                                              ? 3
                                                                                   : IMRT_FWD_UNROLL / 2;
     GroupRegs a[U], b[U];

@@ -6,8 +6,10 @@
 //   x_t = max(0, x - lambda_q g) for k_trials step sizes -> z_t, r_t, G(x_t) -> Eq. (5) test,
 //   lambda / alpha (steps 3-4) -> stop test (step 5) } -> g at the final x -> KKT residual.
 // Within a team the passes over D are split among all its warps: a warp streams whole SELL
-// slices (forward) or whole beamlet rows (transposed). A team of one CTA synchronises with
-// __syncthreads only; larger teams add a barrier in global memory after each pass.
+// slices (forward) or whole beamlet rows (transposed) through its own ring of cp.async stages
+// in shared memory, so several stages are in flight across slice and row boundaries. A team of
+// one CTA synchronises with __syncthreads only; larger teams add a barrier in global memory
+// after each pass.
 //
 // Every CTA of a team keeps the accepted x and g in shared memory and runs the controller
 // itself on the same sums in the same order, so the CTAs take identical decisions without
@@ -23,6 +25,10 @@ namespace imrt {
 namespace {
 
 constexpr int kTW = kTeamThreads / 32;  // warps per team CTA
+#ifndef IMRT_TEAM_STAGE
+#define IMRT_TEAM_STAGE 1
+#endif
+constexpr int kTeamStage = IMRT_TEAM_STAGE;  // groups per register stage in a team's slice loop
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned int* p) {
     unsigned v;
@@ -157,7 +163,8 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
         float acc[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-        slice_row_dot<F, KT>(P.val, P.col, __ldg(P.slice_off + s), 0, __ldg(P.slice_len + s), lane, xs, acc);
+        slice_row_dot<F, KT, kTeamStage>(P.val, P.col, __ldg(P.slice_off + s), 0, __ldg(P.slice_len + s), lane, xs,
+                                         acc);
         slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, eval ? 1 : KT, objb, 1);
     }
     if (eval) {
@@ -171,93 +178,320 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
     }
 }
 
-// g_i = sum over the segmented beamlet-major row i of D_ij r_j, one warp per row, in a fixed
-// order (lane l takes groups l, l + 64, ... and l + 32, l + 96, ...; then a shuffle tree).
-// Groups of 8 entries: 16-bit voxel offsets inside the row's segment runs (see kTqBlock).
+// ---------------------------------------------------------------------------------------------
+// Copy rings. A warp streams its share of a pass through its own ring of kRingStages stages in
+// shared memory, filled with cp.async: while the warp computes one stage the next
+// kRingStages - 1 are in flight, also across slice and row boundaries (the next unit's record
+// and segment table are fetched a unit ahead), so a short slice or row no longer costs a
+// chain of dependent round trips. Each lane copies and reads only its own 16-byte chunks,
+// laid out [stage][chunk][lane] so the reads are free of bank conflicts; the few bytes one lane
+// copies for others (mask bytes) are read after the warp's cp.async wait and __syncwarp.
+// ---------------------------------------------------------------------------------------------
+constexpr int kRingStages = 4;
+
+// forward stage: NCH 16-byte chunks of one group per lane, and, with a slice's last group, the
+// epilogue inputs of its 32 voxels (caller row index, target dose, mask and target bytes)
+template <class F>
+__host__ __device__ constexpr int fwd_chunks() { return (F::VB + F::CB) / 16; }
+template <class F>
+__host__ __device__ constexpr int fwd_ring_bytes() {
+    return kRingStages * (fwd_chunks<F>() * 512 + 32 * 4 * 2 + 32 * 2 + 8);
+}
+// transposed stage: per lane one group of 8 entries (values, 16-bit offsets) and its segment
 template <int PREC>
-__device__ __noinline__ void team_transposed(const TeamPlan& P, const float* __restrict__ r, int gw, int W, int64_t* sb) {
+__host__ __device__ constexpr int bwd_val_bytes() {
+    return PREC == kFmtF32C16 ? 32 : PREC == IMRT_FP8E4M3 ? 8 : 16;
+}
+template <int PREC>
+__host__ __device__ constexpr int bwd_ring_bytes() {
+    return kRingStages * (32 * bwd_val_bytes<PREC>() + 512 + 32 + 8);
+}
+template <class F>
+__host__ __device__ constexpr int bwd_prec() {
+    return F::KIND == 1 ? kFmtF32C16 : F::KIND == 2 ? IMRT_FP16 : F::KIND == 3 ? IMRT_BF16 : IMRT_FP8E4M3;
+}
+template <class F>
+__host__ __device__ constexpr int warp_ring_bytes() {
+    return ((fwd_ring_bytes<F>() > bwd_ring_bytes<bwd_prec<F>()>() ? fwd_ring_bytes<F>()
+                                                                   : bwd_ring_bytes<bwd_prec<F>()>()) + 127) & ~127;
+}
+
+// Source of chunk c of group k (one lane) in the SELL copy: the 16-byte words load_group reads.
+template <class F>
+__device__ __forceinline__ const uint4* group_chunk(const void* val, const void* col, int64_t off, int k, int lane,
+                                                    int c) {
+    if constexpr (F::KIND == 0) {
+        return c == 0 ? reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 32 + lane
+                      : reinterpret_cast<const uint4*>(static_cast<const int32_t*>(col) + off) + (size_t)k * 32 + lane;
+    } else if constexpr (F::KIND == 1) {
+        return c < 2 ? reinterpret_cast<const uint4*>(static_cast<const float*>(val) + off) + (size_t)k * 64 + 2 * lane + c
+                     : reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane;
+    } else if constexpr (F::GE == 8) {
+        return c == 0 ? reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(val) + off) + (size_t)k * 32 + lane
+                      : reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 32 + lane;
+    } else {
+        return c == 0 ? reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(val) + off) + (size_t)k * 32 + lane
+                      : reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(col) + off) + (size_t)k * 64 +
+                            2 * lane + (c - 1);
+    }
+}
+
+// The group's registers from its staged chunks (the layout load_group produces).
+template <class F>
+__device__ __forceinline__ GroupRegs group_from_chunks(const uint4* ch) {
+    GroupRegs g;
+    g.v = ch[0];
+    if constexpr (F::KIND == 1) {
+        g.c1 = ch[32];
+        g.c0 = ch[64];
+    } else {
+        g.c0 = ch[32];
+        if constexpr (F::KIND == 4) g.c1 = ch[64];
+    }
+    return g;
+}
+
+__device__ __forceinline__ TeamUnit load_unit(const TeamUnit* u) {
+    const int4 w = __ldg(reinterpret_cast<const int4*>(u));
+    TeamUnit t;
+    t.off = (int64_t)(((uint64_t)(uint32_t)w.y << 32) | (uint32_t)w.x);
+    t.s = w.z;
+    t.L = w.w;
+    return t;
+}
+
+// Trial pass of a team over its busy slices through the warp's copy ring (see above): the same
+// dot products, epilogue and slice partials as team_forward.
+template <class F, int KT>
+__device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T, const float* xs, int cur, int gw,
+                                               int W, double* objb, unsigned char* ring) {
+    constexpr int NS = kRingStages, NCH = fwd_chunks<F>();
+    const int lane = threadIdx.x & 31;
+    uint4* data = reinterpret_cast<uint4*>(ring);                        // [NS][NCH][32]
+    int32_t* e_ro = reinterpret_cast<int32_t*>(ring + NS * NCH * 512);  // [NS][32]
+    float* e_vt = reinterpret_cast<float*>(e_ro + NS * 32);             // [NS][32]
+    uint8_t* e_mask = reinterpret_cast<uint8_t*>(e_vt + NS * 32);       // [NS][32]
+    uint8_t* e_vtm = e_mask + NS * 32;                                   // [NS][32]
+    int2* meta = reinterpret_cast<int2*>(e_vtm + NS * 32);              // [NS]: slice, 1 first | 2 last
+    float* zq[KT];
+    float* rq[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const int set = (cur + 1 + q) % kSets;
+        zq[q] = P.v.z + (size_t)set * P.m_pad;
+        rq[q] = P.v.r + (size_t)set * P.m_pad;
+    }
+    const int nb = P.n_busy;
+    int pu = gw, pg = 0;  // producer: unit and group
+    TeamUnit pr{}, pn{};
+    if (pu < nb) pr = load_unit(P.units + pu);
+    if (pu + W < nb) pn = load_unit(P.units + pu + W);
+    auto produce = [&](int st) {
+        if (pu < nb) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                cp_async16(data + (st * NCH + c) * 32 + lane, group_chunk<F>(P.val, P.col, pr.off, pg, lane, c));
+            const bool last = pg + 1 == pr.L;
+            if (last) {  // the epilogue inputs travel with the slice's last group
+                const int p = pr.s * kSlice + lane;
+                cp_async4(e_ro + st * 32 + lane, P.r_index + p);
+                if (lane < 8) cp_async4(e_mask + st * 32 + 4 * lane, P.mask + (size_t)pr.s * kSlice + 4 * lane);
+                if (P.vt) {
+                    cp_async4(e_vt + st * 32 + lane, P.vt + p);
+                    if (lane < 8) cp_async4(e_vtm + st * 32 + 4 * lane, P.vtm + (size_t)pr.s * kSlice + 4 * lane);
+                }
+            }
+            if (lane == 0) meta[st] = make_int2(pr.s, (pg == 0 ? 1 : 0) | (last ? 2 : 0));
+            if (last) {
+                pu += W;
+                pr = pn;
+                pg = 0;
+                if (pu + W < nb) pn = load_unit(P.units + pu + W);
+            } else {
+                ++pg;
+            }
+        } else if (lane == 0) {
+            meta[st] = make_int2(-1, 0);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < NS - 1; ++st) produce(st);
+    float acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+    for (int cs = 0;; cs = (cs + 1) % NS) {
+        cp_async_wait<NS - 2>();  // this lane's copies into stage cs have landed
+        __syncwarp();             // and every lane's (the mask bytes); stage cs - 1 is free
+        const int2 mt = meta[cs];
+        if (mt.x < 0) break;
+        produce((cs + NS - 1) % NS);
+        if (mt.y & 1) {
+#pragma unroll
+            for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
+        }
+        fma_group<F, KT>(group_from_chunks<F>(data + cs * NCH * 32 + lane), xs, acc);
+        if (mt.y & 2) {  // the slice is complete: Eq. (1)'s penalties and its objective partials
+            const int s = mt.x, p = s * kSlice + lane;
+            double Fq[KT];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+            if (p < P.m) {
+                const uint32_t bits = e_mask[cs * 32 + lane];
+                const float tj = P.vt ? e_vt[cs * 32 + lane] : 0.0f;
+                const uint32_t tg = P.vt ? e_vtm[cs * 32 + lane] : 0u;
+                const int ro = e_ro[cs * 32 + lane];
+#pragma unroll
+                for (int q = 0; q < KT; ++q) {
+                    float rj;
+                    penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
+                    zq[q][p] = acc[q];
+                    rq[q][ro] = rj;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                const double g = warp_sum(Fq[q]);
+                if (lane == 0) objb[(size_t)q * P.n_slices + s] = g;
+            }
+        }
+    }
+    cp_async_wait<0>();  // only empty groups can remain
+    __syncwarp();
+}
+
+// Transposed pass of a team through the warp's copy ring: a stage is one round of a row (group
+// 32 j + l for lane l, 8 entries each), its segment found when the copy is issued. The row's
+// records are fetched ahead: the next row's index two rows ahead and its segment table one row
+// ahead (lanes 0..H hold one entry each). The same fixed order as team_transposed's rows: lane l
+// accumulates its groups of the row in round order, then a shuffle tree.
+template <int PREC>
+__device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float* __restrict__ r, int gw, int W,
+                                                  unsigned char* ring, int64_t* sb) {
+    constexpr int NS = kRingStages, VB = bwd_val_bytes<PREC>();
     const int lane = threadIdx.x & 31;
     const bool multi = P.team_size > 1;
-    const int H = P.H;
-    for (int u = gw; u < P.n; u += W) {
-        const int i = __ldg(P.rows + u);
+    const int H = P.H, n = P.n;
+    unsigned char* vals = ring;                                             // [NS][VB / 16][32] 16 B (or [NS][32] 8 B)
+    uint4* los = reinterpret_cast<uint4*>(ring + NS * 32 * VB);            // [NS][32]
+    int8_t* hh = reinterpret_cast<int8_t*>(los + NS * 32);                 // [NS][32]: segment, -1 no group
+    int2* meta = reinterpret_cast<int2*>(hh + NS * 32);                    // [NS]: row, 1 first | 2 last
+    // producer: row unit pu, row i, round j; the current row's segment table in sb
+    int pu = gw, i = -1, j = 0, G = 0;
+    int64_t r0 = 0;
+    int ni = -1, nni = -1;  // rows of units pu + W, pu + 2W
+    int64_t nb = 0;         // lane l <= H: entry l of the segment table of row ni
+    auto start_row = [&]() {  // sb <- the prefetched table of the next row; prefetch the one after
         __syncwarp();
-        if (lane <= H) sb[lane] = __ldg(P.seg + (int64_t)i * H + lane);
+        if (lane <= H) sb[lane] = nb;
         __syncwarp();
-        const int64_t r0 = sb[0];
-        const int G = (int)((sb[H] - r0) >> 3);
-        struct Raw {
-            uint4 v, v2, lw;
-            int h;
-        };
-        auto load = [&](int k, Raw& q) {
-            const int64_t e = r0 + 8 * (int64_t)k;
-            int h = 0;
-            while (h + 1 < H && e >= sb[h + 1]) ++h;
-            q.h = h;
-            if constexpr (PREC == IMRT_FP8E4M3) {
-                const uint2 w = ld_stream_u2(reinterpret_cast<const uint2*>(static_cast<const uint8_t*>(P.tval) + e));
-                q.v = make_uint4(w.x, w.y, 0u, 0u);
-            } else if constexpr (PREC == kFmtF32C16) {
-                const uint4* vp = reinterpret_cast<const uint4*>(static_cast<const float*>(P.tval) + e);
-                q.v = ld_stream(vp);
-                q.v2 = ld_stream(vp + 1);
-            } else {
-                q.v = ld_stream(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(P.tval) + e));
+        i = ni;
+        r0 = sb[0];
+        G = (int)((sb[H] - r0) >> 3);
+        j = 0;
+        ni = nni;
+        if (ni >= 0 && lane <= H) nb = __ldg(P.seg + (int64_t)ni * H + lane);
+        nni = pu + 2 * W < n ? __ldg(P.rows + pu + 2 * W) : -1;
+    };
+    if (pu < n) {
+        const int i0 = __ldg(P.rows + pu);
+        if (lane <= H) nb = __ldg(P.seg + (int64_t)i0 * H + lane);
+        ni = i0;
+        nni = pu + W < n ? __ldg(P.rows + pu + W) : -1;
+        start_row();
+    }
+    auto produce = [&](int st) {
+        if (pu < n) {
+            const int k = 32 * j + lane;
+            int h = -1;
+            if (k < G) {
+                const int64_t e = r0 + 8 * (int64_t)k;
+                h = 0;
+                while (h + 1 < H && e >= sb[h + 1]) ++h;
+                if constexpr (VB == 8) {
+                    cp_async8(vals + ((size_t)st * 32 + lane) * 8, static_cast<const uint8_t*>(P.tval) + e);
+                } else {
+                    const unsigned char* src = static_cast<const unsigned char*>(P.tval) + e * (VB / 8);
+#pragma unroll
+                    for (int c = 0; c < VB / 16; ++c)
+                        cp_async16(vals + (((size_t)st * (VB / 16) + c) * 32 + lane) * 16, src + 16 * c);
+                }
+                cp_async16(los + st * 32 + lane, P.lo + e);
             }
-            q.lw = ld_stream(reinterpret_cast<const uint4*>(P.lo + e));
-        };
-        auto use = [&](const Raw& q, float& acc) {
-            const float* rb = r + ((size_t)q.h << 16);
-            float v[8];
+            hh[st * 32 + lane] = (int8_t)h;
+            const bool last = 32 * (j + 1) >= G;
+            if (lane == 0) meta[st] = make_int2(i, (j == 0 ? 1 : 0) | (last ? 2 : 0));
+            if (last) {
+                pu += W;
+                if (pu < n) start_row();
+            } else {
+                ++j;
+            }
+        } else if (lane == 0) {
+            meta[st] = make_int2(-1, 0);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < NS - 1; ++st) produce(st);
+    float acc = 0.0f;
+    for (int cs = 0;; cs = (cs + 1) % NS) {
+        cp_async_wait<NS - 2>();
+        __syncwarp();
+        const int2 mt = meta[cs];
+        if (mt.x < 0) break;
+        const int h = hh[cs * 32 + lane];
+        float v[8];
+        uint4 lw = make_uint4(0u, 0u, 0u, 0u);
+        if (h >= 0) {
             if constexpr (PREC == kFmtF32C16) {
-                const uint32_t ww[8] = {q.v.x, q.v.y, q.v.z, q.v.w, q.v2.x, q.v2.y, q.v2.z, q.v2.w};
+                const uint4 a = *reinterpret_cast<const uint4*>(vals + (((size_t)cs * 2) * 32 + lane) * 16);
+                const uint4 b = *reinterpret_cast<const uint4*>(vals + (((size_t)cs * 2 + 1) * 32 + lane) * 16);
+                const uint32_t ww[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int h = 0; h < 8; ++h) v[h] = __uint_as_float(ww[h]);
+                for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(ww[t]);
             } else if constexpr (PREC == IMRT_FP8E4M3) {
-                const uint32_t ww[2] = {q.v.x, q.v.y};
+                const uint2 w = *reinterpret_cast<const uint2*>(vals + ((size_t)cs * 32 + lane) * 8);
+                const uint32_t ww[2] = {w.x, w.y};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 lo = e4m3x2f((uint16_t)(ww[h] & 0xffffu));
-                    const float2 hi = e4m3x2f((uint16_t)(ww[h] >> 16));
-                    v[4 * h + 0] = lo.x;
-                    v[4 * h + 1] = lo.y;
-                    v[4 * h + 2] = hi.x;
-                    v[4 * h + 3] = hi.y;
+                for (int t = 0; t < 2; ++t) {
+                    const float2 lo = e4m3x2f((uint16_t)(ww[t] & 0xffffu));
+                    const float2 hi = e4m3x2f((uint16_t)(ww[t] >> 16));
+                    v[4 * t + 0] = lo.x;
+                    v[4 * t + 1] = lo.y;
+                    v[4 * t + 2] = hi.x;
+                    v[4 * t + 3] = hi.y;
                 }
             } else {
-                const uint32_t ww[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+                const uint4 a = *reinterpret_cast<const uint4*>(vals + ((size_t)cs * 32 + lane) * 16);
+                const uint32_t ww[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const float2 f = PREC == IMRT_FP16 ? h2f(ww[h]) : b2f(ww[h]);
-                    v[2 * h] = f.x;
-                    v[2 * h + 1] = f.y;
+                for (int t = 0; t < 4; ++t) {
+                    const float2 f = PREC == IMRT_FP16 ? h2f(ww[t]) : b2f(ww[t]);
+                    v[2 * t] = f.x;
+                    v[2 * t + 1] = f.y;
                 }
             }
-            const uint32_t l4[4] = {q.lw.x, q.lw.y, q.lw.z, q.lw.w};
+            lw = los[cs * 32 + lane];
+        }
+        if (mt.y & 1) acc = 0.0f;
+        produce((cs + NS - 1) % NS);
+        if (h >= 0) {
+            const float* rb = r + ((size_t)h << 16);
+            const uint32_t l4[4] = {lw.x, lw.y, lw.z, lw.w};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 acc = fmaf(v[2 * t], ld_team(rb + (l4[t] & 0xffffu), multi), acc);
                 acc = fmaf(v[2 * t + 1], ld_team(rb + (l4[t] >> 16), multi), acc);
             }
-        };
-        float acc0 = 0.0f, acc1 = 0.0f;
-        int k = lane;
-        for (; k + 32 < G; k += 64) {
-            Raw q0, q1;
-            load(k, q0);
-            load(k + 32, q1);
-            use(q0, acc0);
-            use(q1, acc1);
         }
-        if (k < G) {
-            Raw q0;
-            load(k, q0);
-            use(q0, acc0);
+        if (mt.y & 2) {
+            const float t = warp_sum(acc);
+            if (lane == 0) P.v.g[mt.x] = P.scale ? t * __ldg(P.scale + mt.x) : t;
         }
-        const float t = warp_sum(acc0 + acc1);
-        if (lane == 0) P.v.g[i] = P.scale ? t * __ldg(P.scale + i) : t;
     }
+    cp_async_wait<0>();
+    __syncwarp();
 }
 
 struct TeamShared {
@@ -281,6 +515,9 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
     float* xa = smem;             // accepted x
     float* gs = xa + n_pad;       // g at the accepted x
     float* xs = gs + n_pad;       // trial points (scaled), interleaved by step size
+    unsigned char* ring = reinterpret_cast<unsigned char*>(smem) +
+                          (((size_t)n_pad * 4u * (size_t)(2 + KT) + 127) & ~(size_t)127) +
+                          (size_t)wib * warp_ring_bytes<F>();  // this warp's copy ring
     cta_copy_in(&sh.sp, P.sp);
     cta_copy_in(&sh.T, P.terms);  // P was staged by the caller before its __syncthreads
     __syncthreads();
@@ -328,8 +565,7 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
     else if (status == 0 && G == 0.0) stop = IMRT_STOP_EXACT;
 
     auto gradient = [&]() -> bool {  // g = D^T r at the accepted x, into gs
-        team_transposed<(F::KIND == 1 ? kFmtF32C16 : F::KIND == 2 ? IMRT_FP16 : F::KIND == 3 ? IMRT_BF16 : IMRT_FP8E4M3)>(
-            P, P.v.r + (size_t)cur * P.m_pad, gw, W, sh.sb[wib]);
+        team_transposed_ring<bwd_prec<F>()>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
         const bool ok = team_barrier(P, ++bar);
         float gm = 0.0f;
         for (int i = tid; i < n_pad; i += BW) {
@@ -386,7 +622,7 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
             }
             cta_sum<KT>(d2, sh.d2);  // also makes xs visible to every warp
             double* objb = P.obj + (size_t)(passes & 1) * obj_buf;
-            team_forward<F, KT>(P, sh.T, xs, cur, false, gw, W, objb);
+            team_forward_ring<F, KT>(P, sh.T, xs, cur, gw, W, objb, ring);
             ++passes;
             // The stop request is the team lead's alone, so every CTA reads the same one; its two
             // slots alternate with the barriers, as the partial buffers do.
@@ -533,6 +769,16 @@ const void* team_kernel(int fmt) {
 }
 
 }  // namespace
+
+size_t team_ring_bytes(int fmt) {
+    switch (fmt) {
+        case kFmtF32C16: return (size_t)kTW * warp_ring_bytes<FmtF32C16>();
+        case IMRT_FP16: return (size_t)kTW * warp_ring_bytes<FmtF16>();
+        case IMRT_BF16: return (size_t)kTW * warp_ring_bytes<FmtBF16>();
+        case IMRT_FP8E4M3: return (size_t)kTW * warp_ring_bytes<FmtF8>();
+        default: return 0;
+    }
+}
 
 int team_ctas_per_sm(int fmt, size_t smem) {
     const void* fn = team_kernel(fmt);
