@@ -111,7 +111,8 @@ typedef struct {
     int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
     int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy
                                (more when the reduced phase stops early: the polish gets the rest of
-                               max_iter); default 20 */
+                               max_iter; a reduced phase whose line search runs out of halvings also
+                               hands over); default 20 */
     int32_t kernel_variant; /* forward pass: 0 warp streaming with a CTA-local schedule (default; falls back
                                to 2 when a CTA's tables do not fit in shared memory), 1 bulk-copy (TMA)
                                pipeline, 2 warp streaming with one device-wide schedule */

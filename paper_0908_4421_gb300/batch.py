@@ -94,13 +94,16 @@ def _main():
     ap.add_argument("--precision", default="fp16", choices=sorted(PRECISIONS))
     ap.add_argument("--repeats", type=int, default=3)
     ap.add_argument("--solver", default="team", choices=["team", "graph"])
+    ap.add_argument("--ks", default="1,4,8", help="k_trials drawn per plan from these")
+    ap.add_argument("--no-sequential", action="store_true")
     args = ap.parse_args()
     cases = make_cases(args.plans)
-    plans = make_plans(cases, precision=PRECISIONS[args.precision],
+    ks = tuple(int(k) for k in args.ks.split(","))
+    plans = make_plans(cases, precision=PRECISIONS[args.precision], ks=ks,
                        solver=L.SOLVER_TEAM if args.solver == "team" else L.SOLVER_GRAPH)
     try:
-        out = run(plans, repeats=args.repeats)
-        out["workload"] = f"{args.plans} jittered tiny-family phantoms, k in {{1,4,8}}, {args.precision}"
+        out = run(plans, repeats=args.repeats, sequential=not args.no_sequential)
+        out["workload"] = f"{args.plans} jittered tiny-family phantoms, k in {set(ks)}, {args.precision}"
         print(json.dumps(out))
     finally:
         for p in plans:

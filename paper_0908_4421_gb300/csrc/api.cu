@@ -945,11 +945,13 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
                 T.has_u |= 1u << st;
                 T.Tu[st] = t;
                 T.cu[st] = (float)c;
+                T.cul[st] = (float)(c - (double)T.cu[st]);
                 T.cud[st] = c;
             } else {
                 T.has_o |= 1u << st;
                 T.To[st] = t;
                 T.co[st] = (float)c;
+                T.col[st] = (float)(c - (double)T.co[st]);
                 T.cod[st] = c;
             }
         }
@@ -1437,6 +1439,10 @@ imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vec
 
 // --- persistent multi-plan solver -------------------------------------------------------
 
+#ifndef IMRT_TEAM_KT_COST
+#define IMRT_TEAM_KT_COST 2  // byte-equivalents per stored entry of each step size beyond the first
+#endif
+
 // The SELL copy's slices with entries (longest first) and without (built on first use).
 imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices** out) {
     imrt_plan::TeamSlices& t = precision == IMRT_FP32 ? p->team32 : p->teamq;
@@ -1618,9 +1624,12 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
             t.n_busy = ts->n_busy;
             t.n_idle = ts->n_idle;
             t.H = p->t_H;
+            // cost: bytes per iteration, plus the arithmetic of the step sizes beyond the first
+            // (each forms and accumulates one more trial point per entry), times the budget
             const int64_t vb = (int64_t)elem_bytes(prec);
             cost[k] = (double)std::max(max_iter[idx[k]], 1) *
-                      (double)(p->nnz * 2 * (vb + 2) + (int64_t)p->m * 17 + (int64_t)p->n * 8);
+                      ((double)(p->nnz * 2 * (vb + 2) + (int64_t)p->m * 17 + (int64_t)p->n * 8) +
+                       (double)IMRT_TEAM_KT_COST * (double)p->nnz * (double)(p->opt.k_trials - 1));
             cap[k] = std::max(1, std::min(ts->n_busy, p->n) / 16);
             smem = std::max(smem, team_smem_bytes(p->n_pad, p->opt.k_trials, fmt));
         }
@@ -1876,7 +1885,7 @@ imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_
     if (!dose) {
         p->vt_on = false;
         T.has_vt = 0;
-        T.vcu = T.vco = 0.0f;
+        T.vcu = T.vco = T.vcul = T.vcol = 0.0f;
         T.vcud = T.vcod = 0.0;
         CK(cudaMemcpyAsync(p->terms_dev, &T, sizeof(Terms), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -1917,6 +1926,8 @@ imrt_status plan_set_voxel_targets(imrt_plan* p, const float* dose, const uint8_
     T.has_vt = 1;
     T.vcu = (float)cu;
     T.vco = (float)co;
+    T.vcul = (float)(cu - (double)T.vcu);
+    T.vcol = (float)(co - (double)T.vco);
     T.vcud = cu;
     T.vcod = co;
     p->vt_on = true;
@@ -1967,8 +1978,10 @@ imrt_status plan_solve(imrt_plan* p, const float* x0, imrt_result* res) {
     res->iterations = d.iter;
     res->backtracks = d.total_bt;
     res->initial_objective = d.G0;
-    // Reduced-precision D: polish with the FP32 copy from the reached x (warm start).
-    if (polish && d.status == IMRT_OK) {
+    // Reduced-precision D: polish with the FP32 copy from the reached x (warm start). A reduced
+    // phase whose line search ran out of halvings stalled on its own rounding (near an optimum
+    // the reduced copy's objective noise exceeds any decrease): the polish takes over from its x.
+    if (polish && (d.status == IMRT_OK || d.status == IMRT_ELINESEARCH)) {
         CK(cudaMemcpyAsync(p->g_stage, p->v.x + (size_t)d.cur * p->n_pad, sizeof(float) * p->n_pad,
                            cudaMemcpyDeviceToDevice, s));
         const int trace_saved = p->opt.trace;
@@ -2049,7 +2062,8 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         res[i].objective = d.G;
         res[i].kkt = d.kkt;
         res[i].rel_change = d.rel;
-        if (p->opt.precision != IMRT_FP32 && p->opt.polish_iter > 0 && d.status == IMRT_OK) {
+        if (p->opt.precision != IMRT_FP32 && p->opt.polish_iter > 0 &&
+            (d.status == IMRT_OK || d.status == IMRT_ELINESEARCH)) {  // as in plan_solve
             CK(cudaMemcpyAsync(p->g_stage, p->v.x + (size_t)d.cur * p->n_pad, sizeof(float) * p->n_pad,
                                cudaMemcpyDeviceToDevice, s));
             pp.push_back(p);

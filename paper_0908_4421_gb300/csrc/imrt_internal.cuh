@@ -70,6 +70,10 @@ struct Terms {
     int32_t has_vt, pad;
     float vcu, vco;
     double vcud, vcod;
+    // low parts of the coefficients as float pairs (c = c_hi + c_lo, c_hi the float copy above)
+    // for the double-float objective terms
+    float cul[kMaxStruct], col[kMaxStruct];
+    float vcul, vcol;
 };
 
 // Solver state, device-resident, updated only by the single-CTA controller.
@@ -290,9 +294,13 @@ cudaError_t launch_team(int fmt, const TeamArgs& args, int grid, size_t smem, cu
 int team_ctas_per_sm(int fmt, size_t smem);
 // Dynamic shared memory of a team CTA: x, g and the trial points of a plan of n_pad beamlets at
 // k_trials step sizes, then the warps' copy rings for format `fmt` (team_ring_bytes).
+// Floats per beamlet of a team CTA's trial-point area: the trial point itself for one step size,
+// else the scaled pair (x s, g s) from which each step size's point is formed on the fly.
+__host__ __device__ constexpr int team_x_floats(int k_trials) { return k_trials == 1 ? 1 : 2; }
 size_t team_ring_bytes(int fmt);
 inline size_t team_smem_bytes(int n_pad, int k_trials, int fmt) {
-    return (((size_t)n_pad * 4u * (size_t)(2 + k_trials) + 127) & ~(size_t)127) + team_ring_bytes(fmt);
+    return (((size_t)n_pad * 4u * (size_t)(2 + team_x_floats(k_trials)) + 127) & ~(size_t)127) +
+           team_ring_bytes(fmt);
 }
 
 // Sets the message imrt_last_error() returns on this thread (api.cu).

@@ -240,11 +240,12 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
 // n_groups values and every sum is independent of the schedule. The counters are cleared by
 // the last CTA of the launch.
 template <int KT>
-__device__ __forceinline__ void publish_objective(const FwdUnits& U, int s, int lane, const double (&Fq)[KT]) {
+__device__ __forceinline__ void publish_objective(const FwdUnits& U, int s, int lane, const Df (&Fq)[KT]) {
+    float2* gp = reinterpret_cast<float2*>(U.gpart);  // a double-float pair per slot
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
-        const double g = warp_sum(Fq[q]);
-        if (lane == 0) U.gpart[(size_t)q * U.gstride + s] = g;
+        const Df g = warp_sum(Fq[q]);
+        if (lane == 0) gp[(size_t)q * U.gstride + s] = make_float2(g.hi, g.lo);
     }
     const int grp = s / kGroupSlices;
     int old = 0;
@@ -258,10 +259,14 @@ __device__ __forceinline__ void publish_objective(const FwdUnits& U, int s, int 
     __threadfence();
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
-        double v = lane < size ? __ldcg(U.gpart + (size_t)q * U.gstride + (size_t)grp * kGroupSlices + lane) : 0.0;
+        Df v{0.0f, 0.0f};
+        if (lane < size) {
+            const float2 w = __ldcg(gp + (size_t)q * U.gstride + (size_t)grp * kGroupSlices + lane);
+            v = Df{w.x, w.y};
+        }
         v = warp_sum(v);
         if (lane == 0) {
-            U.gsum[(size_t)q * U.n_groups + grp] = v;
+            U.gsum[(size_t)q * U.n_groups + grp] = df_to_double(v);
             __threadfence();
         }
     }
@@ -317,9 +322,9 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
         if (!LOCAL && lane == 0) U.counters[R.sid] = 0;
     }
     const int p = s * kSlice + lane;
-    double Fq[KT];
+    Df Fq[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+    for (int q = 0; q < KT; ++q) Fq[q] = Df{0.0f, 0.0f};
     if (p < a.m) {
         const uint32_t bits = a.mask[p];
         const float tj = a.vt ? a.vt[p] : 0.0f;
@@ -332,7 +337,7 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
                 float rj;
-                penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
+                penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
                 zq[q][p] = acc[q];
                 rq[q][ro] = rj;
             }
@@ -341,8 +346,8 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
     if constexpr (LOCAL) {
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            const double g = warp_sum(Fq[q]);
-            if (lane == 0) lt.slots[(size_t)R.slot * KT + q] = g;
+            const Df g = warp_sum(Fq[q]);
+            if (lane == 0) reinterpret_cast<Df*>(lt.slots)[(size_t)R.slot * KT + q] = g;
         }
     } else {
         publish_objective<KT>(U, s, lane, Fq);
@@ -430,7 +435,8 @@ __global__ void __launch_bounds__(kFwdThreads,
         lam = st->lambda;
         alpha = a.sp->alpha;
     }
-    if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
+    for (int i = tid; i < (int)(sizeof(Terms) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&T)[i] = reinterpret_cast<const uint32_t*>(a.terms)[i];
     __shared__ CtlStage cs;
     int cancel_req = 0;
     if (done) {  // the solve has ended (uniform over the grid): leave once the copy has landed
@@ -554,11 +560,11 @@ __global__ void __launch_bounds__(kFwdThreads,
         // the CTA's objective partial of each trial: its slots added in slot order
         if (wib < KT) {
             const int q = wib;
-            double t = 0.0;
-            for (int i = lane; i < s_slots; i += 32) t += lt.slots[(size_t)i * KT + q];
+            Df t{0.0f, 0.0f};
+            for (int i = lane; i < s_slots; i += 32) t = df_add(t, reinterpret_cast<const Df*>(lt.slots)[(size_t)i * KT + q]);
             t = warp_sum(t);
             if (lane == 0) {
-                U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : t;
+                U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : df_to_double(t);
                 __threadfence();
             }
         }
@@ -729,7 +735,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
         }
         fence_mbar_init();
     }
-    if (tid < (int)(sizeof(Terms) / 4)) reinterpret_cast<uint32_t*>(&T)[tid] = reinterpret_cast<const uint32_t*>(a.terms)[tid];
+    for (int i = tid; i < (int)(sizeof(Terms) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&T)[i] = reinterpret_cast<const uint32_t*>(a.terms)[i];
     __shared__ CtlStage cs;
     int cancel_req = 0;
     __syncthreads();
@@ -946,9 +953,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
             if (!mt.last) continue;
             // rows of slice mt.s are complete: penalty epilogue and the slice's objective partial
             const int p = mt.s * kSlice + lane;
-            double Fq[KT];
+            Df Fq[KT];
 #pragma unroll
-            for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+            for (int q = 0; q < KT; ++q) Fq[q] = Df{0.0f, 0.0f};
             if (p < a.m) {
                 const float tj = a.vt ? a.vt[p] : 0.0f;
                 const uint32_t tg = a.vt ? a.vtm[p] : 0u;
@@ -960,7 +967,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
 #pragma unroll
                     for (int q = 0; q < KT; ++q) {
                         float rj;
-                        penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
+                        penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
                         zq[q][p] = acc[q];
                         rq[q][ro] = rj;
                     }

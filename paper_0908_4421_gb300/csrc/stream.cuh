@@ -31,21 +31,61 @@ namespace imrt {
 #endif
 
 // ---------------------------------------------------------------------------
-// Per-voxel penalty (Eq. (1)): F_j and r_j = dF_j / dz_j at dose z.
+// Per-voxel penalty (Eq. (1)): penalty_df below gives F_j and r_j = dF_j / dz_j at dose z.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void penalty(float z, uint32_t bits, const Terms& T, double& F, float& r, float tj = 0.0f,
-                                        uint32_t tg = 0u) {
-    F = 0.0;
+// Double-float arithmetic: a value hi + lo held in two floats, about 44 bits of precision, built
+// from error-free transformations (TwoSum, TwoProduct with fmaf). This part runs FP64 at a small
+// fraction of its FP32 rate, so objective terms and their in-warp sums use these pairs; the sums
+// across slices and the Armijo test stay in double precision.
+// ---------------------------------------------------------------------------
+struct Df {
+    float hi, lo;
+};
+__device__ __forceinline__ Df df_add(Df a, Df b) {  // accurate for operands of one sign
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float h = s + e;
+    return Df{h, e - (h - s)};
+}
+__device__ __forceinline__ Df df_sqr(float e) {  // exact
+    const float p = e * e;
+    return Df{p, fmaf(e, e, -p)};
+}
+__device__ __forceinline__ Df df_mul(Df a, Df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const float h = p + e;
+    return Df{h, e - (h - p)};
+}
+__device__ __forceinline__ Df warp_sum(Df v) {  // fixed xor-tree order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Df w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return v;
+}
+__device__ __forceinline__ double df_to_double(Df v) { return (double)v.hi + (double)v.lo; }
+
+// penalty() with the objective term as a double-float: the same terms and r_j, F_j = sum of
+// c * e^2 with e^2 exact and c = c_hi + c_lo.
+__device__ __forceinline__ void penalty_df(float z, uint32_t bits, const Terms& T, Df& F, float& r, float tj = 0.0f,
+                                           uint32_t tg = 0u) {
+    F = Df{0.0f, 0.0f};
     r = 0.0f;
-    if (T.has_vt) {  // per-voxel dose T_j (Eq. (1) as printed)
+    if (T.has_vt) {
         const float eo = z - tj;
         if (eo > 0.0f) {
-            F += T.vcod * ((double)eo * (double)eo);
+            F = df_add(F, df_mul(Df{T.vco, T.vcol}, df_sqr(eo)));
             r += 2.0f * T.vco * eo;
         }
         const float eu = tj - z;
         if (tg && eu > 0.0f) {
-            F += T.vcud * ((double)eu * (double)eu);
+            F = df_add(F, df_mul(Df{T.vcu, T.vcul}, df_sqr(eu)));
             r -= 2.0f * T.vcu * eu;
         }
     }
@@ -55,19 +95,19 @@ __device__ __forceinline__ void penalty(float z, uint32_t bits, const Terms& T, 
         if ((T.has_u >> s) & 1u) {
             const float e = T.Tu[s] - z;
             if (e > 0.0f) {
-                F += T.cud[s] * ((double)e * (double)e);
+                F = df_add(F, df_mul(Df{T.cu[s], T.cul[s]}, df_sqr(e)));
                 r -= 2.0f * T.cu[s] * e;
             }
         }
         if ((T.has_o >> s) & 1u) {
             const float e = z - T.To[s];
             if (e > 0.0f) {
-                F += T.cod[s] * ((double)e * (double)e);
+                F = df_add(F, df_mul(Df{T.co[s], T.col[s]}, df_sqr(e)));
                 r += 2.0f * T.co[s] * e;
             }
         }
     }
-    if (!isfinite(z)) F = __longlong_as_double(0x7ff8000000000000LL);
+    if (!isfinite(z)) F.hi = __int_as_float(0x7fc00000);
 }
 
 __device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T, uint32_t tg = 0u) {
@@ -168,27 +208,27 @@ __device__ __forceinline__ void load_group(const void* __restrict__ val, const v
     }
 }
 
-// acc[q] += the group's entries in storage order.
-template <class F, int KT>
-__device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __restrict__ xs, float (&acc)[KT]) {
+// Calls entry(v, c) for the group's entries in storage order (value, beamlet index).
+template <class F, class E>
+__device__ __forceinline__ void for_group_entries(const GroupRegs& g, E&& entry) {
     const uint32_t vv[4] = {g.v.x, g.v.y, g.v.z, g.v.w};
     const uint32_t cc[4] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w};
     if constexpr (F::KIND == 0) {
 #pragma unroll
-        for (int h = 0; h < 4; ++h) fma_entry<KT>(__uint_as_float(vv[h]), (int)cc[h], xs, acc);
+        for (int h = 0; h < 4; ++h) entry(__uint_as_float(vv[h]), (int)cc[h]);
     } else if constexpr (F::KIND == 1) {
         const uint32_t v8[8] = {g.v.x, g.v.y, g.v.z, g.v.w, g.c1.x, g.c1.y, g.c1.z, g.c1.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            fma_entry<KT>(__uint_as_float(v8[2 * h]), (int)(cc[h] & 0xffffu), xs, acc);
-            fma_entry<KT>(__uint_as_float(v8[2 * h + 1]), (int)(cc[h] >> 16), xs, acc);
+            entry(__uint_as_float(v8[2 * h]), (int)(cc[h] & 0xffffu));
+            entry(__uint_as_float(v8[2 * h + 1]), (int)(cc[h] >> 16));
         }
     } else if constexpr (F::GE == 8) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const float2 f = std::is_same<F, FmtF16>::value ? h2f(vv[h]) : b2f(vv[h]);
-            fma_entry<KT>(f.x, (int)(cc[h] & 0xffffu), xs, acc);
-            fma_entry<KT>(f.y, (int)(cc[h] >> 16), xs, acc);
+            entry(f.x, (int)(cc[h] & 0xffffu));
+            entry(f.y, (int)(cc[h] >> 16));
         }
     } else {
         const uint32_t c8[8] = {g.c0.x, g.c0.y, g.c0.z, g.c0.w, g.c1.x, g.c1.y, g.c1.z, g.c1.w};
@@ -196,12 +236,18 @@ __device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __res
         for (int h = 0; h < 4; ++h) {
             const float2 lo = e4m3x2f((uint16_t)(vv[h] & 0xffffu));
             const float2 hi = e4m3x2f((uint16_t)(vv[h] >> 16));
-            fma_entry<KT>(lo.x, (int)(c8[2 * h] & 0xffffu), xs, acc);
-            fma_entry<KT>(lo.y, (int)(c8[2 * h] >> 16), xs, acc);
-            fma_entry<KT>(hi.x, (int)(c8[2 * h + 1] & 0xffffu), xs, acc);
-            fma_entry<KT>(hi.y, (int)(c8[2 * h + 1] >> 16), xs, acc);
+            entry(lo.x, (int)(c8[2 * h] & 0xffffu));
+            entry(lo.y, (int)(c8[2 * h] >> 16));
+            entry(hi.x, (int)(c8[2 * h + 1] & 0xffffu));
+            entry(hi.y, (int)(c8[2 * h + 1] >> 16));
         }
     }
+}
+
+// acc[q] += the group's entries in storage order.
+template <class F, int KT>
+__device__ __forceinline__ void fma_group(const GroupRegs& g, const float* __restrict__ xs, float (&acc)[KT]) {
+    for_group_entries<F>(g, [&](float v, int c) { fma_entry<KT>(v, c, xs, acc); });
 }
 
 // One row (one lane) of a slice: acc[q] += the row's entries in groups [g0, g1), in storage

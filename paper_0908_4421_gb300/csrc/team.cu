@@ -69,37 +69,41 @@ __device__ bool team_barrier(const TeamPlan& P, unsigned k) {
     return ok != 0;
 }
 
-// Fixed-order CTA reduction of NQ FP64 values per thread into out[q] (thread-strided order,
-// then a shuffle tree per warp, then the warps in index order).
+// Fixed-order CTA reduction of NQ double-float values per thread into out[q] (thread-strided
+// order, then a shuffle tree per warp, then the warps in index order; one conversion to double).
 template <int NQ>
-__device__ __forceinline__ void cta_sum(double (&v)[NQ], double* out) {
-    __shared__ double red[kTW][kMaxTrials];
+__device__ __forceinline__ void cta_sum(Df (&v)[NQ], double* out) {
+    __shared__ Df red[kTW][kMaxTrials];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        const double t = warp_sum(v[q]);
+        const Df t = warp_sum(v[q]);
         if (lane == 0) red[wib][q] = t;
     }
     __syncthreads();
     if (threadIdx.x < NQ) {
-        double t = 0.0;
-        for (int w = 0; w < kTW; ++w) t += red[w][threadIdx.x];
-        out[threadIdx.x] = t;
+        Df t = red[0][threadIdx.x];
+        for (int w = 1; w < kTW; ++w) t = df_add(t, red[w][threadIdx.x]);
+        out[threadIdx.x] = df_to_double(t);
     }
     __syncthreads();
 }
 
-// G of every evaluated step size: the slice partials added in slice order.
+// G of every evaluated step size: the slice partials (double-float pairs) added in slice order.
 template <int NQ>
 __device__ __forceinline__ void sum_objective(const TeamPlan& P, const double* objb, int nq, double* out) {
     const bool multi = P.team_size > 1;
-    double v[NQ];
+    const float2* ob = reinterpret_cast<const float2*>(objb);
+    Df v[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) v[q] = Df{0.0f, 0.0f};
     for (int s = threadIdx.x; s < P.n_slices; s += kTeamThreads) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
-            if (q < nq) v[q] += ld_team(objb + (size_t)q * P.n_slices + s, multi);
+            if (q < nq) {
+                const float2 w = ld_team(ob + (size_t)q * P.n_slices + s, multi);
+                v[q] = df_add(v[q], Df{w.x, w.y});
+            }
     }
     cta_sum<NQ>(v, out);
 }
@@ -111,9 +115,9 @@ __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T
                                                const float (&acc)[KT], float* const (&zq)[KT],
                                                float* const (&rq)[KT], int nq, double* objb, int rows) {
     const int p = s * kSlice + lane;
-    double Fq[KT];
+    Df Fq[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+    for (int q = 0; q < KT; ++q) Fq[q] = Df{0.0f, 0.0f};
     if (p < P.m) {
         const uint32_t bits = __ldg(P.mask + p);
         const float tj = P.vt ? __ldg(P.vt + p) : 0.0f;
@@ -123,19 +127,20 @@ __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T
         for (int q = 0; q < KT; ++q) {
             if (q >= nq) continue;
             float rj;
-            penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
+            penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
             zq[q][p] = acc[q];
             rq[q][ro] = rj;
         }
     }
+    float2* ob = reinterpret_cast<float2*>(objb);
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
         if (q >= nq) continue;
-        const double g = warp_sum(Fq[q]);
+        const Df g = warp_sum(Fq[q]);
         if (lane == 0) {
-            if (rows == 1) objb[(size_t)q * P.n_slices + s] = g;
+            if (rows == 1) ob[(size_t)q * P.n_slices + s] = make_float2(g.hi, g.lo);
             else
-                for (int k = 0; k < rows; ++k) objb[(size_t)k * P.n_slices + s] = g;
+                for (int k = 0; k < rows; ++k) ob[(size_t)k * P.n_slices + s] = make_float2(g.hi, g.lo);
         }
     }
 }
@@ -263,8 +268,8 @@ __device__ __forceinline__ TeamUnit load_unit(const TeamUnit* u) {
 // Trial pass of a team over its busy slices through the warp's copy ring (see above): the same
 // dot products, epilogue and slice partials as team_forward.
 template <class F, int KT>
-__device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T, const float* xs, int cur, int gw,
-                                               int W, double* objb, unsigned char* ring) {
+__device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T, const float* xs, const float* lamp,
+                                               int cur, int gw, int W, double* objb, unsigned char* ring) {
     constexpr int NS = kRingStages, NCH = fwd_chunks<F>();
     const int lane = threadIdx.x & 31;
     uint4* data = reinterpret_cast<uint4*>(ring);                        // [NS][NCH][32]
@@ -281,6 +286,9 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
         zq[q] = P.v.z + (size_t)set * P.m_pad;
         rq[q] = P.v.r + (size_t)set * P.m_pad;
     }
+    float lam[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) lam[q] = lamp[q];
     const int nb = P.n_busy;
     int pu = gw, pg = 0;  // producer: unit and group
     TeamUnit pr{}, pn{};
@@ -330,12 +338,20 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
 #pragma unroll
             for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
         }
-        fma_group<F, KT>(group_from_chunks<F>(data + cs * NCH * 32 + lane), xs, acc);
+        if constexpr (KT == 1) {
+            fma_group<F, 1>(group_from_chunks<F>(data + cs * NCH * 32 + lane), xs, acc);
+        } else {  // acc[q] += v * max(0, x s - lambda_q g s), the pair read once per entry
+            for_group_entries<F>(group_from_chunks<F>(data + cs * NCH * 32 + lane), [&](float v, int c) {
+                const float2 xg = *reinterpret_cast<const float2*>(xs + 2 * c);
+#pragma unroll
+                for (int q = 0; q < KT; ++q) acc[q] = fmaf(v, fmaxf(0.0f, fmaf(-lam[q], xg.y, xg.x)), acc[q]);
+            });
+        }
         if (mt.y & 2) {  // the slice is complete: Eq. (1)'s penalties and its objective partials
             const int s = mt.x, p = s * kSlice + lane;
-            double Fq[KT];
+            Df Fq[KT];
 #pragma unroll
-            for (int q = 0; q < KT; ++q) Fq[q] = 0.0;
+            for (int q = 0; q < KT; ++q) Fq[q] = Df{0.0f, 0.0f};
             if (p < P.m) {
                 const uint32_t bits = e_mask[cs * 32 + lane];
                 const float tj = P.vt ? e_vt[cs * 32 + lane] : 0.0f;
@@ -344,15 +360,16 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
 #pragma unroll
                 for (int q = 0; q < KT; ++q) {
                     float rj;
-                    penalty(acc[q], bits, T, Fq[q], rj, tj, tg);
+                    penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
                     zq[q][p] = acc[q];
                     rq[q][ro] = rj;
                 }
             }
+            float2* ob = reinterpret_cast<float2*>(objb);
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
-                const double g = warp_sum(Fq[q]);
-                if (lane == 0) objb[(size_t)q * P.n_slices + s] = g;
+                const Df g = warp_sum(Fq[q]);
+                if (lane == 0) ob[(size_t)q * P.n_slices + s] = make_float2(g.hi, g.lo);
             }
         }
     }
@@ -496,6 +513,7 @@ __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float
 
 struct TeamShared {
     TeamPlan P;
+    float lam[kMaxTrials];  // the step sizes of the current trial pass
     SolveParams sp;
     Terms T;
     double sums[kMaxTrials];
@@ -514,9 +532,9 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
     const int n = P.n, n_pad = P.n_pad;
     float* xa = smem;             // accepted x
     float* gs = xa + n_pad;       // g at the accepted x
-    float* xs = gs + n_pad;       // trial points (scaled), interleaved by step size
+    float* xs = gs + n_pad;       // the scaled trial point (one step size), or the pairs (x s, g s)
     unsigned char* ring = reinterpret_cast<unsigned char*>(smem) +
-                          (((size_t)n_pad * 4u * (size_t)(2 + KT) + 127) & ~(size_t)127) +
+                          (((size_t)n_pad * 4u * (size_t)(2 + team_x_floats(KT)) + 127) & ~(size_t)127) +
                           (size_t)wib * warp_ring_bytes<F>();  // this warp's copy ring
     cta_copy_in(&sh.sp, P.sp);
     cta_copy_in(&sh.T, P.terms);  // P was staged by the caller before its __syncthreads
@@ -606,23 +624,33 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
                     l = l / sp.alpha;
                 }
             }
-            double d2[KT];
+            Df d2[KT];
 #pragma unroll
-            for (int q = 0; q < KT; ++q) d2[q] = 0.0;
+            for (int q = 0; q < KT; ++q) d2[q] = Df{0.0f, 0.0f};
             for (int i = tid; i < n_pad; i += BW) {
                 const float xv = xa[i], gv = gs[i];
                 const float sc = P.scale ? __ldg(P.scale + i) : 1.0f;
+                // the dose pass forms max(0, x s - lambda g s) from the scaled pair (x s, g s),
+                // for one step size here, for several on the fly (the same expression either way)
+                const float xsc = xv * sc, gsc = gv * sc;
+                if constexpr (KT == 1) {
+                    xs[i] = fmaxf(0.0f, fmaf(-lamf[0], gsc, xsc));
+                } else {
+                    xs[2 * i] = xsc;
+                    xs[2 * i + 1] = gsc;
+                }
 #pragma unroll
-                for (int q = 0; q < KT; ++q) {
+                for (int q = 0; q < KT; ++q) {  // (x_t - x)^2: the difference exact as a pair, then squared
                     const float xt = fmaxf(0.0f, fmaf(-lamf[q], gv, xv));
-                    xs[(size_t)i * KT + q] = xt * sc;
-                    const double e = (double)xt - (double)xv;
-                    d2[q] += e * e;
+                    const float dh = xt - xv, bb = dh - xt, dl = (xt - (dh - bb)) + (-xv - bb);
+                    const Df sq = df_sqr(dh);
+                    d2[q] = df_add(d2[q], Df{sq.hi, fmaf(2.0f * dh, dl, sq.lo)});
                 }
             }
+            if (tid < KT) sh.lam[tid] = lamf[tid];
             cta_sum<KT>(d2, sh.d2);  // also makes xs visible to every warp
             double* objb = P.obj + (size_t)(passes & 1) * obj_buf;
-            team_forward_ring<F, KT>(P, sh.T, xs, cur, gw, W, objb, ring);
+            team_forward_ring<F, KT>(P, sh.T, xs, sh.lam, cur, gw, W, objb, ring);
             ++passes;
             // The stop request is the team lead's alone, so every CTA reads the same one; its two
             // slots alternate with the barriers, as the partial buffers do.

@@ -55,6 +55,7 @@ class ServeResult:
     start: float
     done: float
     batch: int = 1  # plans in the launch that solved this request
+    x0: Optional[np.ndarray] = None  # the warm start used (None: the x_init rule)
 
     @property
     def time_to_plan(self) -> float:
@@ -116,6 +117,7 @@ class ReplanServer:
         self._next_id = 0
         self._last_x: Dict[str, np.ndarray] = {}
         self._residents: "collections.OrderedDict[str, _Resident]" = collections.OrderedDict()
+        self._active = set()  # patients with a request being built or solved
         self._results: List[ServeResult] = []
         self._streams = [torch.cuda.Stream(device=device) for _ in range(workers + 1)]
         self._threads = [threading.Thread(target=self._builder, args=(i,), daemon=True) for i in range(workers)]
@@ -160,7 +162,8 @@ class ReplanServer:
                 "mean_s": statistics.mean(lat), "plans_per_s": len(res) / span if span > 0 else float("nan"),
                 "peak_in_flight_bytes": self.peak_in_flight, "budget_bytes": self.budget,
                 "launches": self.launches, "mean_batch": statistics.mean(r.batch for r in res),
-                "failed": sum(1 for r in res if r.status != 0)}
+                "failed": sum(1 for r in res if r.status != 0),
+                "failed_status": sorted({L.STATUS_NAMES.get(r.status, r.status) for r in res if r.status != 0})}
 
     # -- admission ---------------------------------------------------------
     def _estimate(self, req: _Request) -> int:
@@ -183,24 +186,33 @@ class ReplanServer:
             del self._residents[pid]
 
     def _admit(self) -> Optional[_Request]:
+        """The oldest waiting request that can start: its patient has no request in progress
+        (requests of one patient keep their order, so warm starts follow it) and its footprint
+        fits the budget, after evicting idle resident plans if needed. A request that does not
+        fit holds back the ones behind it (no overtaking on memory)."""
         with self._cv:
             while True:
-                if self._pending:
-                    req = self._pending[0]
+                blocked = set()
+                for idx, req in enumerate(self._pending):
+                    if req.patient is not None and (req.patient in blocked or req.patient in self._active):
+                        blocked.add(req.patient)
+                        continue
                     res = self._residents.get(req.patient) if req.patient is not None else None
-                    if res is None or not res.busy:
-                        need = self._estimate(req)
-                        if self.in_flight + need > self.budget:
-                            self._evict_for(need, req.patient)
-                        if self.in_flight + need <= self.budget:
-                            self._pending.pop(0)
-                            self.in_flight += need
-                            self.peak_in_flight = max(self.peak_in_flight, self.in_flight)
-                            req.reserved = need
-                            if res is not None:
-                                res.busy = True
-                            self._building += 1
-                            return req
+                    need = self._estimate(req)
+                    if self.in_flight + need > self.budget:
+                        self._evict_for(need, req.patient)
+                    if self.in_flight + need > self.budget:
+                        break
+                    self._pending.pop(idx)
+                    self.in_flight += need
+                    self.peak_in_flight = max(self.peak_in_flight, self.in_flight)
+                    req.reserved = need
+                    if res is not None:
+                        res.busy = True
+                    if req.patient is not None:
+                        self._active.add(req.patient)
+                    self._building += 1
+                    return req
                 if self._closed and not self._pending:
                     return None
                 self._cv.wait(timeout=0.05)
@@ -242,10 +254,12 @@ class ReplanServer:
         z = plan.dose(x) if self.want_dose else None
         done = time.perf_counter()
         out = ServeResult(req.rid, req.patient, x, z, objective, iterations, status, req.arrival, req.start, done,
-                          launch)
+                          launch, req.x0)
         with self._cv:
             if req.patient is not None:
                 self._last_x[req.patient] = x
+                self._active.discard(req.patient)
+                self._cv.notify_all()
             r = self._residents.get(req.patient) if req.patient is not None else None
             if r is not None and r.plan is plan:
                 r.busy = False
@@ -265,6 +279,8 @@ class ReplanServer:
 
     def _fail(self, req: _Request, exc: BaseException) -> None:
         with self._cv:
+            if req.patient is not None:
+                self._active.discard(req.patient)
             r = self._residents.get(req.patient) if req.patient is not None else None
             if r is not None and (req.plan is None or r.plan is req.plan):  # drop a half-rebuilt resident
                 r.plan.close()
