@@ -36,6 +36,7 @@ METRIC = "time-to-plan"
 UNIT = "s"
 L2_BYTES = 129 * 1024 * 1024
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
+FP8_POLISH_SWITCH = 1e-3
 
 
 def measured_peaks():
@@ -234,12 +235,15 @@ def serve_block(n_requests: int) -> dict:
             finally:
                 srv.close()
             st = srv.stats()
-            if form.startswith("batched") and rate > 100:
-                # objective error of a sample of served requests against the oracle on the same start
+            if rate > 100:
+                # objective error of a sample of served requests against the FP64 oracle on the same
+                # start (the warm start the server used) and the same step-size rule: each form's
+                # distribution, since the relative-change stop fires on single small steps and so
+                # moves with any rounding difference, FP32 included
                 orc = oracle.get()
                 errs = []
                 res = sorted(srv.results(), key=lambda r: r.request_id)
-                for r in [q for q in res if q.status == 0][:: max(1, len(res) // 12)]:
+                for r in [q for q in res if q.status == 0][:: max(1, len(res) // 24)]:
                     c = cases[r.request_id]
                     with S.Plan.from_case(c, S.Options()) as p:
                         lam0 = p.info()["lambda0_rule"]
@@ -247,9 +251,12 @@ def serve_block(n_requests: int) -> dict:
                     ref = orc.solve(c, lambda0=lam0, max_iter=200, x_init=2 if x0 is not None else 0, x0=x0,
                                     trace=False)
                     G_served = orc.eval(c, r.x.astype(np.float64), gradient=False)[0]
-                    errs.append(abs(G_served - ref.objective) / ref.objective)
-                st["objective_rel_err_max"] = max(errs)
-                st["objective_rel_err_sample"] = len(errs)
+                    errs.append((G_served - ref.objective) / ref.objective)
+                mag = sorted(abs(e) for e in errs)
+                st["objective_rel_err"] = {"sample": len(errs), "p50": mag[len(mag) // 2], "max": mag[-1],
+                                           "over_1e-3": sum(1 for e in mag if e > 1e-3),
+                                           "max_worse": max(0.0, max(errs)),  # served above the oracle
+                                           "worse_by_over_1e-3": sum(1 for e in errs if e > 1e-3)}
             out[f"{form}@{rate:g}Hz"] = st
     return out
 
@@ -303,14 +310,16 @@ def main():
     info = plan.info()
     lam0 = info["lambda0_rule"]
 
-    # forward kernel variant and k_trials by the project autotuner (identical Armijo
-    # decisions for every candidate; only speed differs)
+    # solver, forward kernel variant and k_trials by the project autotuner (within a solver the
+    # candidates take identical Armijo decisions; only speed differs)
     kts = [args.k_trials] if args.k_trials else [1, 2]
     variants = [args.variant] if args.variant >= 0 else [0, 1, 2]
+    solvers = (L.SOLVER_GRAPH,) if args.variant >= 0 else (L.SOLVER_GRAPH, L.SOLVER_TEAM)
     tuned = {}
-    if len(kts) * len(variants) > 1:
-        tr = autotune.tune(plan, variants=variants, k_trials=kts, repeats=3, warmup=1)
-        best_kt, best_variant, tuned = tr.k_trials, tr.kernel_variant, tr.table
+    best_solver = L.SOLVER_GRAPH
+    if len(kts) * len(variants) * len(solvers) > 1:
+        tr = autotune.tune(plan, variants=variants, k_trials=kts, repeats=3, warmup=1, solvers=solvers)
+        best_kt, best_variant, tuned, best_solver = tr.k_trials, tr.kernel_variant, tr.table, tr.solver
     else:
         best_kt, best_variant = kts[0], variants[0]
         plan.set_options(k_trials=best_kt, kernel_variant=best_variant)
@@ -339,7 +348,8 @@ def main():
     res = results[-1]
 
     # per-kernel durations with CUDA events on the launch stream (host-driven loop, same kernels)
-    plan.set_options(mode=L.MODE_HOST, profile=1)
+    # (the per-launch timing is the graph solver's: its passes are separate kernels)
+    plan.set_options(mode=L.MODE_HOST, profile=1, solver=L.SOLVER_GRAPH)
     fwd_ms = bwd_ms = 0.0
     fwd_n = bwd_n = 0
     for _ in range(max(2, args.steps // 3)):
@@ -348,7 +358,7 @@ def main():
         bwd_ms += r.bwd_ms
         fwd_n += r.fwd_launches
         bwd_n += r.bwd_launches
-    plan.set_options(mode=L.MODE_GRAPH, profile=0)
+    plan.set_options(mode=L.MODE_GRAPH, profile=0, solver=best_solver)
     fwd_avg_s = fwd_ms / max(fwd_n, 1) / 1e3
     bwd_avg_s = bwd_ms / max(bwd_n, 1) / 1e3
     peak, peak_kind = measured_peaks()
@@ -374,7 +384,7 @@ def main():
     h2d = h_rp.nbytes + h_col.nbytes + h_val.nbytes + h_mask.nbytes
     d2h = x_out.nbytes + z_out.nbytes
     e2e_opts = Options(max_iter=args.max_iter, delta=1e-6, precision=prec, k_trials=best_kt,
-                       kernel_variant=best_variant, stream=stream.cuda_stream)
+                       kernel_variant=best_variant, solver=best_solver, stream=stream.cuda_stream)
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         barrier()
@@ -422,10 +432,14 @@ def main():
         forms = {"oracle_fp64": {"objective": ref.objective, "iterations": ref.iterations},
                  "fp32": {"time_to_plan_s": step_s, "objective": res.objective, **errors(plan.get_x())}}
         for name in ("fp16", "bf16", "fp8"):
+            # FP8-e4m3 keeps 3 mantissa bits: its phase hands over to the FP32 polish once its
+            # relative change falls below 1e-3, so the polish has the iterations to reach 1e-3
+            switch = FP8_POLISH_SWITCH if name == "fp8" else 0.0
             with torch.cuda.stream(stream):
                 fp = Plan.from_case(case, Options(max_iter=args.max_iter, delta=1e-6, precision=PRECISIONS[name],
                                                   k_trials=best_kt, kernel_variant=best_variant,
-                                                  lambda0=lam0, stream=stream.cuda_stream), device=True)
+                                                  lambda0=lam0, polish_switch=switch,
+                                                  stream=stream.cuda_stream), device=True)
             for _ in range(2):
                 fp.solve()
             ts = []
@@ -443,6 +457,7 @@ def main():
             f_s = rp.fwd_ms / max(rp.fwd_launches, 1) / 1e3
             b_s = rp.bwd_ms / max(rp.bwd_launches, 1) / 1e3
             forms[name] = {"time_to_plan_s": statistics.mean(ts), "speedup_vs_fp32": step_s / statistics.mean(ts),
+                           "polish_switch": switch,
                            "iterations": r_.iterations, "polish_iterations": r_.polish_iterations,
                            "objective": r_.objective,
                            "k_forward_gbs": fi["fwd_bytes"] / f_s / 1e9 if f_s > 0 else None,
@@ -468,6 +483,7 @@ def main():
         "data": "synthetic",
         "config": common_config(args.workload, case, args.max_iter, world),
         "form": {"precision": args.precision, "k_trials": best_kt, "kernel_variant": best_variant,
+                 "solver": "team" if best_solver == L.SOLVER_TEAM else "graph",
                  "lambda0": lam0, "tuned_s": {k: round(v, 5) for k, v in tuned.items()}},
         "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "traffic": traffic, "kernel": dominant,

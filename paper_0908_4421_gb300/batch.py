@@ -96,10 +96,11 @@ def _main():
     ap.add_argument("--solver", default="team", choices=["team", "graph"])
     ap.add_argument("--ks", default="1,4,8", help="k_trials drawn per plan from these")
     ap.add_argument("--no-sequential", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=200)
     args = ap.parse_args()
     cases = make_cases(args.plans)
     ks = tuple(int(k) for k in args.ks.split(","))
-    plans = make_plans(cases, precision=PRECISIONS[args.precision], ks=ks,
+    plans = make_plans(cases, precision=PRECISIONS[args.precision], ks=ks, max_iter=args.max_iter,
                        solver=L.SOLVER_TEAM if args.solver == "team" else L.SOLVER_GRAPH)
     try:
         out = run(plans, repeats=args.repeats, sequential=not args.no_sequential)

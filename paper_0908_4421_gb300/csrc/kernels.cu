@@ -242,10 +242,10 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
 template <int KT>
 __device__ __forceinline__ void publish_objective(const FwdUnits& U, int s, int lane, const Df (&Fq)[KT]) {
     float2* gp = reinterpret_cast<float2*>(U.gpart);  // a double-float pair per slot
-#pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        const Df g = warp_sum(Fq[q]);
-        if (lane == 0) gp[(size_t)q * U.gstride + s] = make_float2(g.hi, g.lo);
+    {
+        const Df g = warp_sum_multi<KT>(Fq, lane);
+        if ((lane & (32 / KT - 1)) == 0)
+            gp[(size_t)warp_sum_multi_q<KT>(lane) * U.gstride + s] = make_float2(g.hi, g.lo);
     }
     const int grp = s / kGroupSlices;
     int old = 0;
@@ -334,21 +334,19 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
             zq[0][p] = acc[0];
             rq[0][ro] = cdiag(bits, T, tg) * acc[0];
         } else {
+            float rj[KT];
+            penalty_multi<KT>(acc, bits, T, Fq, rj, tj, tg);
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
-                float rj;
-                penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
                 zq[q][p] = acc[q];
-                rq[q][ro] = rj;
+                rq[q][ro] = rj[q];
             }
         }
     }
     if constexpr (LOCAL) {
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            const Df g = warp_sum(Fq[q]);
-            if (lane == 0) reinterpret_cast<Df*>(lt.slots)[(size_t)R.slot * KT + q] = g;
-        }
+        const Df g = warp_sum_multi<KT>(Fq, lane);  // each step size's slice partial, warp_sum's tree
+        if ((lane & (32 / KT - 1)) == 0)
+            reinterpret_cast<Df*>(lt.slots)[(size_t)R.slot * KT + warp_sum_multi_q<KT>(lane)] = g;
     } else {
         publish_objective<KT>(U, s, lane, Fq);
     }
@@ -964,12 +962,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_forward_tma(const FwdArgs a)
                     zq[0][p] = acc[0];
                     rq[0][ro] = cdiag(bits, T, tg) * acc[0];
                 } else {
+                    float rj[KT];
+                    penalty_multi<KT>(acc, bits, T, Fq, rj, tj, tg);
 #pragma unroll
                     for (int q = 0; q < KT; ++q) {
-                        float rj;
-                        penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
                         zq[q][p] = acc[q];
-                        rq[q][ro] = rj;
+                        rq[q][ro] = rj[q];
                     }
                 }
             }

@@ -110,6 +110,107 @@ __device__ __forceinline__ void penalty_df(float z, uint32_t bits, const Terms& 
     if (!isfinite(z)) F.hi = __int_as_float(0x7fc00000);
 }
 
+// warp_sum of K values at once: each butterfly step hands half of the remaining values to the
+// partner lane and adds the half it keeps, so every sum is the same xor tree as warp_sum (the
+// same pairs in the same order; df_add is symmetric) with K - 1 + 5 - log2 K exchanges instead
+// of 5 K. On return lane l holds the sum of value q = q_of(l) (the lane bits 4, 3, 2 above K's
+// width), and every lane of a group of 32 / K lanes holds the same.
+template <int K>
+__device__ __forceinline__ Df warp_sum_multi(const Df (&v0)[K], int lane) {
+    Df v[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] = v0[q];
+    int k = K;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (k > 1) {
+            const bool upper = (lane & o) != 0;
+            const int h = k / 2;
+#pragma unroll
+            for (int j = 0; j < K / 2; ++j) {
+                if (j >= h) break;
+                const Df give = upper ? v[j] : v[h + j];
+                const Df keep = upper ? v[h + j] : v[j];
+                Df got;
+                got.hi = __shfl_xor_sync(0xffffffffu, give.hi, o);
+                got.lo = __shfl_xor_sync(0xffffffffu, give.lo, o);
+                v[j] = df_add(keep, got);
+            }
+            k = h;
+        } else {
+            Df got;
+            got.hi = __shfl_xor_sync(0xffffffffu, v[0].hi, o);
+            got.lo = __shfl_xor_sync(0xffffffffu, v[0].lo, o);
+            v[0] = df_add(v[0], got);
+        }
+    }
+    return v[0];
+}
+// The value whose sum lane l holds after warp_sum_multi<K>.
+template <int K>
+__device__ __forceinline__ int warp_sum_multi_q(int lane) {
+    return K == 1 ? 0 : K == 2 ? (lane >> 4) & 1 : K == 4 ? (lane >> 3) & 3 : (lane >> 2) & 7;
+}
+
+// penalty_df for K doses of one voxel (the trial points of one pass): the voxel's structure
+// terms are decoded once and applied to every dose. Per dose the same terms in the same order
+// as penalty_df, so F and r are bitwise those of K separate calls.
+template <int K>
+__device__ __forceinline__ void penalty_multi(const float (&z)[K], uint32_t bits, const Terms& T, Df (&F)[K],
+                                              float (&r)[K], float tj = 0.0f, uint32_t tg = 0u) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        F[q] = Df{0.0f, 0.0f};
+        r[q] = 0.0f;
+    }
+    if (T.has_vt) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float eo = z[q] - tj;
+            if (eo > 0.0f) {
+                F[q] = df_add(F[q], df_mul(Df{T.vco, T.vcol}, df_sqr(eo)));
+                r[q] += 2.0f * T.vco * eo;
+            }
+            const float eu = tj - z[q];
+            if (tg && eu > 0.0f) {
+                F[q] = df_add(F[q], df_mul(Df{T.vcu, T.vcul}, df_sqr(eu)));
+                r[q] -= 2.0f * T.vcu * eu;
+            }
+        }
+    }
+    while (bits) {
+        const int s = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if ((T.has_u >> s) & 1u) {
+            const float Tu = T.Tu[s], cu = T.cu[s];
+            const Df c{cu, T.cul[s]};
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const float e = Tu - z[q];
+                if (e > 0.0f) {
+                    F[q] = df_add(F[q], df_mul(c, df_sqr(e)));
+                    r[q] -= 2.0f * cu * e;
+                }
+            }
+        }
+        if ((T.has_o >> s) & 1u) {
+            const float To = T.To[s], co = T.co[s];
+            const Df c{co, T.col[s]};
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const float e = z[q] - To;
+                if (e > 0.0f) {
+                    F[q] = df_add(F[q], df_mul(c, df_sqr(e)));
+                    r[q] += 2.0f * co * e;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        if (!isfinite(z[q])) F[q].hi = __int_as_float(0x7fc00000);
+}
+
 __device__ __forceinline__ float cdiag(uint32_t bits, const Terms& T, uint32_t tg = 0u) {
     float c = T.has_vt ? T.vco + (tg ? T.vcu : 0.0f) : 0.0f;
     while (bits) {

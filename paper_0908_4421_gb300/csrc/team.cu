@@ -184,33 +184,40 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// Copy rings. A warp streams its share of a pass through its own ring of kRingStages stages in
-// shared memory, filled with cp.async: while the warp computes one stage the next
-// kRingStages - 1 are in flight, also across slice and row boundaries (the next unit's record
+// Copy rings. A warp streams its share of a pass through its own ring of stages in shared
+// memory, filled with cp.async: while the warp computes one stage the following ones are in
+// flight, also across slice and row boundaries (the next unit's record
 // and segment table are fetched a unit ahead), so a short slice or row no longer costs a
 // chain of dependent round trips. Each lane copies and reads only its own 16-byte chunks,
 // laid out [stage][chunk][lane] so the reads are free of bank conflicts; the few bytes one lane
 // copies for others (mask bytes) are read after the warp's cp.async wait and __syncwarp.
 // ---------------------------------------------------------------------------------------------
-constexpr int kRingStages = 4;
+// Each warp's ring gets about kRingWarpBytes: as many stages as fit (bytes in flight per SM is
+// what a latency-bound stream needs: about 66 KB per SM at the copy bandwidth and a loaded
+// DRAM latency near 1.5 us).
+constexpr int kRingWarpBytes = 10240;
 
 // forward stage: NCH 16-byte chunks of one group per lane, and, with a slice's last group, the
 // epilogue inputs of its 32 voxels (caller row index, target dose, mask and target bytes)
 template <class F>
 __host__ __device__ constexpr int fwd_chunks() { return (F::VB + F::CB) / 16; }
 template <class F>
-__host__ __device__ constexpr int fwd_ring_bytes() {
-    return kRingStages * (fwd_chunks<F>() * 512 + 32 * 4 * 2 + 32 * 2 + 8);
-}
+__host__ __device__ constexpr int fwd_stage_bytes() { return fwd_chunks<F>() * 512 + 32 * 4 * 2 + 32 * 2 + 8; }
+template <class F>
+__host__ __device__ constexpr int fwd_stages() { return kRingWarpBytes / fwd_stage_bytes<F>(); }
+template <class F>
+__host__ __device__ constexpr int fwd_ring_bytes() { return fwd_stages<F>() * fwd_stage_bytes<F>(); }
 // transposed stage: per lane one group of 8 entries (values, 16-bit offsets) and its segment
 template <int PREC>
 __host__ __device__ constexpr int bwd_val_bytes() {
     return PREC == kFmtF32C16 ? 32 : PREC == IMRT_FP8E4M3 ? 8 : 16;
 }
 template <int PREC>
-__host__ __device__ constexpr int bwd_ring_bytes() {
-    return kRingStages * (32 * bwd_val_bytes<PREC>() + 512 + 32 + 8);
-}
+__host__ __device__ constexpr int bwd_stage_bytes() { return 32 * bwd_val_bytes<PREC>() + 512 + 32 + 8; }
+template <int PREC>
+__host__ __device__ constexpr int bwd_stages() { return kRingWarpBytes / bwd_stage_bytes<PREC>(); }
+template <int PREC>
+__host__ __device__ constexpr int bwd_ring_bytes() { return bwd_stages<PREC>() * bwd_stage_bytes<PREC>(); }
 template <class F>
 __host__ __device__ constexpr int bwd_prec() {
     return F::KIND == 1 ? kFmtF32C16 : F::KIND == 2 ? IMRT_FP16 : F::KIND == 3 ? IMRT_BF16 : IMRT_FP8E4M3;
@@ -270,7 +277,8 @@ __device__ __forceinline__ TeamUnit load_unit(const TeamUnit* u) {
 template <class F, int KT>
 __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T, const float* xs, const float* lamp,
                                                int cur, int gw, int W, double* objb, unsigned char* ring) {
-    constexpr int NS = kRingStages, NCH = fwd_chunks<F>();
+    constexpr int NS = fwd_stages<F>(), NCH = fwd_chunks<F>();
+    static_assert(NS >= 3, "the forward ring needs three stages");
     const int lane = threadIdx.x & 31;
     uint4* data = reinterpret_cast<uint4*>(ring);                        // [NS][NCH][32]
     int32_t* e_ro = reinterpret_cast<int32_t*>(ring + NS * NCH * 512);  // [NS][32]
@@ -357,20 +365,19 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
                 const float tj = P.vt ? e_vt[cs * 32 + lane] : 0.0f;
                 const uint32_t tg = P.vt ? e_vtm[cs * 32 + lane] : 0u;
                 const int ro = e_ro[cs * 32 + lane];
+                float rj[KT];
+                penalty_multi<KT>(acc, bits, T, Fq, rj, tj, tg);
 #pragma unroll
                 for (int q = 0; q < KT; ++q) {
-                    float rj;
-                    penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
                     zq[q][p] = acc[q];
-                    rq[q][ro] = rj;
+                    rq[q][ro] = rj[q];
                 }
             }
-            float2* ob = reinterpret_cast<float2*>(objb);
-#pragma unroll
-            for (int q = 0; q < KT; ++q) {
-                const Df g = warp_sum(Fq[q]);
-                if (lane == 0) ob[(size_t)q * P.n_slices + s] = make_float2(g.hi, g.lo);
-            }
+            // every step size's slice partial in one butterfly (warp_sum's tree for each)
+            const Df g = warp_sum_multi<KT>(Fq, lane);
+            if ((lane & (32 / KT - 1)) == 0)
+                reinterpret_cast<float2*>(objb)[(size_t)warp_sum_multi_q<KT>(lane) * P.n_slices + s] =
+                    make_float2(g.hi, g.lo);
         }
     }
     cp_async_wait<0>();  // only empty groups can remain
@@ -385,7 +392,8 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
 template <int PREC>
 __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float* __restrict__ r, int gw, int W,
                                                   unsigned char* ring, int64_t* sb) {
-    constexpr int NS = kRingStages, VB = bwd_val_bytes<PREC>();
+    constexpr int NS = bwd_stages<PREC>(), VB = bwd_val_bytes<PREC>();
+    static_assert(NS >= 3, "the transposed ring needs three stages");
     const int lane = threadIdx.x & 31;
     const bool multi = P.team_size > 1;
     const int H = P.H, n = P.n;

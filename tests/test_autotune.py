@@ -13,6 +13,7 @@ from paper_0908_4421_gb300 import autotune
 class _Opts:
     kernel_variant: int = 0
     k_trials: int = 1
+    solver: int = L.SOLVER_GRAPH
 
 
 class FakePlan:
@@ -30,7 +31,8 @@ class FakePlan:
         return dict(self._info)
 
     def solve(self, raise_on_error=True):
-        key = (self.options.kernel_variant, self.options.k_trials)
+        key = (("team" if self.options.solver == L.SOLVER_TEAM else self.options.kernel_variant),
+               self.options.k_trials)
         if key not in self.cost:
             raise L.ImrtError(L.IMRT_EUNSUPPORTED, "unsupported shape")
         self.solves += 1
@@ -68,3 +70,15 @@ def test_cache_tunes_each_class_once():
     assert a.solves > 0 and b.solves == 0 and c.solves > 0  # b shares a's class; c is larger
     assert b.options.kernel_variant == 2
     assert len(cache.choices) == 2
+
+
+def test_tune_compares_the_two_solvers():
+    """Team-solver candidates vary k_trials only (the forward variant is the graph solver's);
+    the fastest solver and its k_trials are left on the plan."""
+    cost = {(0, 1): 0.004, (2, 1): 0.005, ("team", 1): 0.006, ("team", 2): 0.002}
+    plan = FakePlan(cost)
+    r = autotune.tune(plan, variants=(0, 2), k_trials=(1, 2), repeats=1, warmup=0,
+                      solvers=(L.SOLVER_GRAPH, L.SOLVER_TEAM))
+    assert (r.solver, r.k_trials) == (L.SOLVER_TEAM, 2)
+    assert plan.options.solver == L.SOLVER_TEAM and plan.options.k_trials == 2
+    assert set(r.table) == {"v0k1", "v2k1", "teamk1", "teamk2"}

@@ -358,13 +358,17 @@ def test_reduced_precision_refuses_more_than_16_segments(many_segments):
         Plan.from_case(case, Options(precision=L.FP16))
 
 
-@pytest.mark.parametrize("prec,obj_tol", [(L.FP16, 1e-3), (L.BF16, 1e-3), (L.FP8E4M3, 1e-2)])
-def test_reduced_precision_solve_with_polish(orc, tiny, prec, obj_tol):
+# FP8-e4m3 (3 mantissa bits) hands over to the FP32 polish once its relative change is below 1e-3
+# (polish_switch); its final objective still differs from the FP64 oracle's 200-iteration value
+# by up to a few 1e-3 (on either side) on these small plans, so its bound is 1e-2
+@pytest.mark.parametrize("prec,obj_tol,switch", [(L.FP16, 1e-3, 0.0), (L.BF16, 1e-3, 0.0), (L.FP8E4M3, 1e-2, 1e-3)])
+def test_reduced_precision_solve_with_polish(orc, tiny, prec, obj_tol, switch):
     """Reduced-precision iterations, then the last polish_iter iterations on the FP32 copy:
     the final objective is within obj_tol of the FP64 oracle's after the same iteration count."""
     case, lam0 = tiny
     ref = orc.solve(case, lambda0=lam0, max_iter=200)
-    with Plan.from_case(case, Options(lambda0=lam0, precision=prec, max_iter=200, polish_iter=20)) as plan:
+    with Plan.from_case(case, Options(lambda0=lam0, precision=prec, max_iter=200, polish_iter=20,
+                                      polish_switch=switch)) as plan:
         res = plan.solve()
         x = plan.get_x()
         z = plan.dose(x)

@@ -208,12 +208,15 @@ def test_team_multi_segment(orc):
     assert abs(res.objective - ref.objective) <= FINAL_RTOL * ref.objective
 
 
-@pytest.mark.parametrize("prec,obj_tol", [(L.FP16, 1e-3), (L.BF16, 1e-3), (L.FP8E4M3, 1e-2)])
-def test_team_reduced_precision_with_polish(orc, tiny, prec, obj_tol):
+# FP8-e4m3 (3 mantissa bits) hands over to the FP32 polish once its relative change is below 1e-3
+# (polish_switch); its final objective still differs from the FP64 oracle's 200-iteration value
+# by up to a few 1e-3 (on either side) on these small plans, so its bound is 1e-2
+@pytest.mark.parametrize("prec,obj_tol,switch", [(L.FP16, 1e-3, 0.0), (L.BF16, 1e-3, 0.0), (L.FP8E4M3, 1e-2, 1e-3)])
+def test_team_reduced_precision_with_polish(orc, tiny, prec, obj_tol, switch):
     case, lam0 = tiny
     ref = orc.solve(case, lambda0=lam0, max_iter=200)
     with Plan.from_case(case, Options(lambda0=lam0, precision=prec, max_iter=200, polish_iter=20,
-                                      solver=TEAM)) as plan:
+                                      polish_switch=switch, solver=TEAM)) as plan:
         res = plan.solve()
         x = plan.get_x()
     assert res.status == 0 and res.polish_iterations > 0
