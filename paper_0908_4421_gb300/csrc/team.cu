@@ -207,13 +207,15 @@ template <class F>
 __host__ __device__ constexpr int fwd_stages() { return kRingWarpBytes / fwd_stage_bytes<F>(); }
 template <class F>
 __host__ __device__ constexpr int fwd_ring_bytes() { return fwd_stages<F>() * fwd_stage_bytes<F>(); }
-// transposed stage: per lane one group of 8 entries (values, 16-bit offsets) and its segment
+// transposed stage: kBwdRounds rounds of a row; per round and lane one group of 8 entries
+// (values, 16-bit offsets) and its segment
+constexpr int kBwdRounds = 2;
 template <int PREC>
 __host__ __device__ constexpr int bwd_val_bytes() {
     return PREC == kFmtF32C16 ? 32 : PREC == IMRT_FP8E4M3 ? 8 : 16;
 }
 template <int PREC>
-__host__ __device__ constexpr int bwd_stage_bytes() { return 32 * bwd_val_bytes<PREC>() + 512 + 32 + 8; }
+__host__ __device__ constexpr int bwd_stage_bytes() { return kBwdRounds * (32 * bwd_val_bytes<PREC>() + 512 + 32) + 8; }
 template <int PREC>
 __host__ __device__ constexpr int bwd_stages() { return kRingWarpBytes / bwd_stage_bytes<PREC>(); }
 template <int PREC>
@@ -263,12 +265,31 @@ __device__ __forceinline__ GroupRegs group_from_chunks(const uint4* ch) {
     return g;
 }
 
-__device__ __forceinline__ TeamUnit load_unit(const TeamUnit* u) {
-    const int4 w = __ldg(reinterpret_cast<const int4*>(u));
+// A warp's unit records, 32 at a time: lane l holds record 32 b + l of the warp's sequence
+// (unit gw + k W for k = 0, 1, ...), the next batch in flight while the current one is used, so
+// a pass of one-group slices does not wait on a record load per slice.
+struct UnitQueue {
+    int4 cur, next;
+    int batch;  // batch index of `cur`
+};
+__device__ __forceinline__ int4 unit_batch(const TeamUnit* units, int nb, int gw, int W, int b, int lane) {
+    const int u = gw + (32 * b + lane) * W;
+    return u < nb ? __ldg(reinterpret_cast<const int4*>(units + u)) : make_int4(0, 0, 0, 0);
+}
+// Record k of the warp's sequence (warp-uniform k; every lane calls).
+__device__ __forceinline__ TeamUnit unit_at(UnitQueue& q, const TeamUnit* units, int nb, int gw, int W, int k,
+                                            int lane) {
+    if ((k >> 5) != q.batch) {  // k is the first record of the next batch
+        q.cur = q.next;
+        ++q.batch;
+        q.next = unit_batch(units, nb, gw, W, q.batch + 1, lane);
+    }
+    const int src = k & 31;
     TeamUnit t;
-    t.off = (int64_t)(((uint64_t)(uint32_t)w.y << 32) | (uint32_t)w.x);
-    t.s = w.z;
-    t.L = w.w;
+    t.off = (int64_t)(((uint64_t)(uint32_t)__shfl_sync(0xffffffffu, q.cur.y, src) << 32) |
+                      (uint32_t)__shfl_sync(0xffffffffu, q.cur.x, src));
+    t.s = __shfl_sync(0xffffffffu, q.cur.z, src);
+    t.L = __shfl_sync(0xffffffffu, q.cur.w, src);
     return t;
 }
 
@@ -298,10 +319,12 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
 #pragma unroll
     for (int q = 0; q < KT; ++q) lam[q] = lamp[q];
     const int nb = P.n_busy;
-    int pu = gw, pg = 0;  // producer: unit and group
-    TeamUnit pr{}, pn{};
-    if (pu < nb) pr = load_unit(P.units + pu);
-    if (pu + W < nb) pn = load_unit(P.units + pu + W);
+    int pu = gw, pk = 0, pg = 0;  // producer: unit (gw + pk W) and group
+    UnitQueue uq;
+    uq.batch = 0;
+    uq.cur = unit_batch(P.units, nb, gw, W, 0, lane);
+    uq.next = unit_batch(P.units, nb, gw, W, 1, lane);
+    TeamUnit pr = unit_at(uq, P.units, nb, gw, W, 0, lane);
     auto produce = [&](int st) {
         if (pu < nb) {
 #pragma unroll
@@ -320,9 +343,9 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
             if (lane == 0) meta[st] = make_int2(pr.s, (pg == 0 ? 1 : 0) | (last ? 2 : 0));
             if (last) {
                 pu += W;
-                pr = pn;
+                ++pk;
                 pg = 0;
-                if (pu + W < nb) pn = load_unit(P.units + pu + W);
+                if (pu < nb) pr = unit_at(uq, P.units, nb, gw, W, pk, lane);
             } else {
                 ++pg;
             }
@@ -384,23 +407,73 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
     __syncwarp();
 }
 
-// Transposed pass of a team through the warp's copy ring: a stage is one round of a row (group
-// 32 j + l for lane l, 8 entries each), its segment found when the copy is issued. The row's
-// records are fetched ahead: the next row's index two rows ahead and its segment table one row
-// ahead (lanes 0..H hold one entry each). The same fixed order as team_transposed's rows: lane l
-// accumulates its groups of the row in round order, then a shuffle tree.
+// The 8 values of one staged group as floats.
 template <int PREC>
+__device__ __forceinline__ void group_values(const unsigned char* vals, int lane, float (&v)[8]) {
+    if constexpr (PREC == kFmtF32C16) {
+        const uint4 a = *reinterpret_cast<const uint4*>(vals + (size_t)lane * 16);
+        const uint4 b = *reinterpret_cast<const uint4*>(vals + (size_t)(32 + lane) * 16);
+        const uint32_t ww[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(ww[t]);
+    } else if constexpr (PREC == IMRT_FP8E4M3) {
+        const uint2 w = *reinterpret_cast<const uint2*>(vals + (size_t)lane * 8);
+        const uint32_t ww[2] = {w.x, w.y};
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const float2 lo = e4m3x2f((uint16_t)(ww[t] & 0xffffu));
+            const float2 hi = e4m3x2f((uint16_t)(ww[t] >> 16));
+            v[4 * t + 0] = lo.x;
+            v[4 * t + 1] = lo.y;
+            v[4 * t + 2] = hi.x;
+            v[4 * t + 3] = hi.y;
+        }
+    } else {
+        const uint4 a = *reinterpret_cast<const uint4*>(vals + (size_t)lane * 16);
+        const uint32_t ww[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 f = PREC == IMRT_FP16 ? h2f(ww[t]) : b2f(ww[t]);
+            v[2 * t] = f.x;
+            v[2 * t + 1] = f.y;
+        }
+    }
+}
+
+// r at the 8 voxels of one group (offsets lw within segment base rb): through L2 for a team of
+// several CTAs (teammates wrote r), through L1 for a one-CTA team.
+template <bool MULTI>
+__device__ __forceinline__ void gather_r(const float* __restrict__ rb, uint4 lw, float (&q)[8]) {
+    const uint32_t l4[4] = {lw.x, lw.y, lw.z, lw.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if constexpr (MULTI) {
+            q[2 * t] = __ldcg(rb + (l4[t] & 0xffffu));
+            q[2 * t + 1] = __ldcg(rb + (l4[t] >> 16));
+        } else {
+            q[2 * t] = rb[l4[t] & 0xffffu];
+            q[2 * t + 1] = rb[l4[t] >> 16];
+        }
+    }
+}
+
+// Transposed pass of a team through the warp's copy ring: a stage is kBwdRounds rounds of a row
+// (round j: group 32 j + l for lane l, 8 entries each), their segments found when the copies
+// are issued; the r gathers of all rounds of a stage are issued before the first product, so a
+// lane has 8 kBwdRounds loads in flight. The row's records are fetched ahead: the next row's
+// index two rows ahead and its segment table one row ahead (lanes 0..H hold one entry each).
+// Lane l accumulates its groups of the row in round order, then a shuffle tree.
+template <int PREC, bool MULTI>
 __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float* __restrict__ r, int gw, int W,
                                                   unsigned char* ring, int64_t* sb) {
-    constexpr int NS = bwd_stages<PREC>(), VB = bwd_val_bytes<PREC>();
+    constexpr int NS = bwd_stages<PREC>(), VB = bwd_val_bytes<PREC>(), R = kBwdRounds;
     static_assert(NS >= 3, "the transposed ring needs three stages");
     const int lane = threadIdx.x & 31;
-    const bool multi = P.team_size > 1;
     const int H = P.H, n = P.n;
-    unsigned char* vals = ring;                                             // [NS][VB / 16][32] 16 B (or [NS][32] 8 B)
-    uint4* los = reinterpret_cast<uint4*>(ring + NS * 32 * VB);            // [NS][32]
-    int8_t* hh = reinterpret_cast<int8_t*>(los + NS * 32);                 // [NS][32]: segment, -1 no group
-    int2* meta = reinterpret_cast<int2*>(hh + NS * 32);                    // [NS]: row, 1 first | 2 last
+    unsigned char* vals = ring;                                         // [NS][R][VB / 16][32] 16 B (or [NS][R][32] 8 B)
+    uint4* los = reinterpret_cast<uint4*>(ring + NS * R * 32 * VB);    // [NS][R][32]
+    int8_t* hh = reinterpret_cast<int8_t*>(los + NS * R * 32);         // [NS][R][32]: segment, -1 no group
+    int2* meta = reinterpret_cast<int2*>(hh + NS * R * 32);            // [NS]: row, 1 first | 2 last
     // producer: row unit pu, row i, round j; the current row's segment table in sb
     int pu = gw, i = -1, j = 0, G = 0;
     int64_t r0 = 0;
@@ -427,30 +500,33 @@ __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float
     }
     auto produce = [&](int st) {
         if (pu < n) {
-            const int k = 32 * j + lane;
-            int h = -1;
-            if (k < G) {
-                const int64_t e = r0 + 8 * (int64_t)k;
-                h = 0;
-                while (h + 1 < H && e >= sb[h + 1]) ++h;
-                if constexpr (VB == 8) {
-                    cp_async8(vals + ((size_t)st * 32 + lane) * 8, static_cast<const uint8_t*>(P.tval) + e);
-                } else {
-                    const unsigned char* src = static_cast<const unsigned char*>(P.tval) + e * (VB / 8);
 #pragma unroll
-                    for (int c = 0; c < VB / 16; ++c)
-                        cp_async16(vals + (((size_t)st * (VB / 16) + c) * 32 + lane) * 16, src + 16 * c);
+            for (int t = 0; t < R; ++t) {
+                const int k = 32 * (j + t) + lane;
+                int h = -1;
+                if (k < G) {
+                    const int64_t e = r0 + 8 * (int64_t)k;
+                    h = 0;
+                    while (h + 1 < H && e >= sb[h + 1]) ++h;
+                    unsigned char* vd = vals + (size_t)(st * R + t) * 32 * VB;
+                    if constexpr (VB == 8) {
+                        cp_async8(vd + (size_t)lane * 8, static_cast<const uint8_t*>(P.tval) + e);
+                    } else {
+                        const unsigned char* src = static_cast<const unsigned char*>(P.tval) + e * (VB / 8);
+#pragma unroll
+                        for (int c = 0; c < VB / 16; ++c) cp_async16(vd + ((size_t)c * 32 + lane) * 16, src + 16 * c);
+                    }
+                    cp_async16(los + (st * R + t) * 32 + lane, P.lo + e);
                 }
-                cp_async16(los + st * 32 + lane, P.lo + e);
+                hh[(st * R + t) * 32 + lane] = (int8_t)h;
             }
-            hh[st * 32 + lane] = (int8_t)h;
-            const bool last = 32 * (j + 1) >= G;
+            const bool last = 32 * (j + R) >= G;
             if (lane == 0) meta[st] = make_int2(i, (j == 0 ? 1 : 0) | (last ? 2 : 0));
             if (last) {
                 pu += W;
                 if (pu < n) start_row();
             } else {
-                ++j;
+                j += R;
             }
         } else if (lane == 0) {
             meta[st] = make_int2(-1, 0);
@@ -465,51 +541,23 @@ __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float
         __syncwarp();
         const int2 mt = meta[cs];
         if (mt.x < 0) break;
-        const int h = hh[cs * 32 + lane];
-        float v[8];
-        uint4 lw = make_uint4(0u, 0u, 0u, 0u);
-        if (h >= 0) {
-            if constexpr (PREC == kFmtF32C16) {
-                const uint4 a = *reinterpret_cast<const uint4*>(vals + (((size_t)cs * 2) * 32 + lane) * 16);
-                const uint4 b = *reinterpret_cast<const uint4*>(vals + (((size_t)cs * 2 + 1) * 32 + lane) * 16);
-                const uint32_t ww[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        int h[R];
+        float q[R][8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(ww[t]);
-            } else if constexpr (PREC == IMRT_FP8E4M3) {
-                const uint2 w = *reinterpret_cast<const uint2*>(vals + ((size_t)cs * 32 + lane) * 8);
-                const uint32_t ww[2] = {w.x, w.y};
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const float2 lo = e4m3x2f((uint16_t)(ww[t] & 0xffffu));
-                    const float2 hi = e4m3x2f((uint16_t)(ww[t] >> 16));
-                    v[4 * t + 0] = lo.x;
-                    v[4 * t + 1] = lo.y;
-                    v[4 * t + 2] = hi.x;
-                    v[4 * t + 3] = hi.y;
-                }
-            } else {
-                const uint4 a = *reinterpret_cast<const uint4*>(vals + ((size_t)cs * 32 + lane) * 16);
-                const uint32_t ww[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float2 f = PREC == IMRT_FP16 ? h2f(ww[t]) : b2f(ww[t]);
-                    v[2 * t] = f.x;
-                    v[2 * t + 1] = f.y;
-                }
-            }
-            lw = los[cs * 32 + lane];
+        for (int t = 0; t < R; ++t) {
+            h[t] = hh[(cs * R + t) * 32 + lane];
+            if (h[t] >= 0) gather_r<MULTI>(r + ((size_t)h[t] << 16), los[(cs * R + t) * 32 + lane], q[t]);
         }
         if (mt.y & 1) acc = 0.0f;
-        produce((cs + NS - 1) % NS);
-        if (h >= 0) {
-            const float* rb = r + ((size_t)h << 16);
-            const uint32_t l4[4] = {lw.x, lw.y, lw.z, lw.w};
+        produce((cs + NS - 1) % NS);  // refills stage cs - 1; stage cs is read below
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                acc = fmaf(v[2 * t], ld_team(rb + (l4[t] & 0xffffu), multi), acc);
-                acc = fmaf(v[2 * t + 1], ld_team(rb + (l4[t] >> 16), multi), acc);
+        for (int t = 0; t < R; ++t)
+            if (h[t] >= 0) {
+                float v[8];
+                group_values<PREC>(vals + (size_t)(cs * R + t) * 32 * VB, lane, v);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc = fmaf(v[e], q[t][e], acc);
             }
-        }
         if (mt.y & 2) {
             const float t = warp_sum(acc);
             if (lane == 0) P.v.g[mt.x] = P.scale ? t * __ldg(P.scale + mt.x) : t;
@@ -591,7 +639,10 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
     else if (status == 0 && G == 0.0) stop = IMRT_STOP_EXACT;
 
     auto gradient = [&]() -> bool {  // g = D^T r at the accepted x, into gs
-        team_transposed_ring<bwd_prec<F>()>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
+        if (TS > 1)
+            team_transposed_ring<bwd_prec<F>(), true>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
+        else
+            team_transposed_ring<bwd_prec<F>(), false>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
         const bool ok = team_barrier(P, ++bar);
         float gm = 0.0f;
         for (int i = tid; i < n_pad; i += BW) {
