@@ -216,8 +216,14 @@ struct imrt_plan {
         TeamUnit* units = nullptr;
         int32_t* idle = nullptr;
         int32_t n_busy = -1, n_idle = 0;
+        int64_t n_groups = 0;  // SELL groups of the busy slices
     } team32, teamq;
     double* team_obj = nullptr;
+    // forward and transposed passes of the plan's last team solve in each storage kind
+    // (0 reduced precision, 1 FP32), the team partition's estimate for the next one
+    struct TeamHist {
+        int32_t fwd = -1, bwd = -1;
+    } team_hist[2];
 };
 
 namespace {
@@ -1439,10 +1445,6 @@ imrt_status run_batch_phase(const std::vector<imrt_plan*>& plans, const std::vec
 
 // --- persistent multi-plan solver -------------------------------------------------------
 
-#ifndef IMRT_TEAM_KT_COST
-#define IMRT_TEAM_KT_COST 2  // byte-equivalents per stored entry of each step size beyond the first
-#endif
-
 // The SELL copy's slices with entries (longest first) and without (built on first use).
 imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices** out) {
     imrt_plan::TeamSlices& t = precision == IMRT_FP32 ? p->team32 : p->teamq;
@@ -1452,9 +1454,12 @@ imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices
         for (int s = 0; s < p->n_slices; ++s) (c.host_cost[s] > 8 * kSlice ? busy : idle).push_back(s);
         std::stable_sort(busy.begin(), busy.end(), [&](int x, int y) { return c.host_cost[x] > c.host_cost[y]; });
         std::vector<TeamUnit> units(busy.size());
-        for (size_t k = 0; k < busy.size(); ++k)
+        int64_t groups = 0;
+        for (size_t k = 0; k < busy.size(); ++k) {
             units[k] = TeamUnit{c.host_off[busy[k]], busy[k],
                                 (int32_t)((c.host_cost[busy[k]] - 8 * kSlice) / ((int64_t)kSlice * c.ge))};
+            groups += units[k].L;
+        }
         TRY(dalloc(p, &t.busy, std::max<size_t>(busy.size(), 1)));
         TRY(dalloc(p, &t.units, std::max<size_t>(busy.size(), 1)));
         TRY(dalloc(p, &t.idle, std::max<size_t>(idle.size(), 1)));
@@ -1469,6 +1474,7 @@ imrt_status team_slices(imrt_plan* p, int precision, const imrt_plan::TeamSlices
         CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
         t.n_busy = (int32_t)busy.size();
         t.n_idle = (int32_t)idle.size();
+        t.n_groups = groups;
     }
     *out = &t;
     return IMRT_OK;
@@ -1484,47 +1490,74 @@ const char* team_unsupported(const imrt_plan* p, int precision, int max_smem) {
     return nullptr;
 }
 
-// Team sizes for one launch of `grid` CTAs: proportional to each plan's bytes per iteration
-// times its iteration budget (at least one CTA each, at most one CTA per 16 of the plan's
-// forward units or beamlet rows); plans beyond one CTA each share one-CTA teams, the longest
-// first to the least-loaded team. Fills team0 / team_size of every TeamPlan and the team lists.
-void team_partition(const std::vector<double>& cost, const std::vector<int>& cap, int grid,
-                    std::vector<TeamPlan>& tp, std::vector<int32_t>& cta_team, std::vector<int32_t>& team_first,
+// Estimated time (ns) of one plan's solve on a team of T CTAs: its forward passes deal the busy
+// slices round-robin over the team's 16 T warps, its transposed passes the beamlet rows; a team
+// of several CTAs also pays a barrier per pass. The per-slice and per-row warp times are linear
+// fits to per-plan timings of the persistent kernel on a GB300 (64 uneven FP16 plans and their
+// FP32 polish); the pass counts are the plan's last team solve's, else an estimate.
+struct TeamCost {
+    double fwd = 0.0, bwd = 0.0;  // passes
+    double slices = 1.0, rows = 1.0;
+    double slice_ns = 0.0, row_ns = 0.0, sync_ns = 0.0;
+    double at(int T) const {
+        const double w = (double)(kTeamThreads / 32) * T;
+        return fwd * std::ceil(slices / w) * slice_ns + bwd * std::ceil(rows / w) * row_ns +
+               (T > 1 ? (fwd + bwd) * sync_ns : 0.0);
+    }
+};
+
+#ifndef IMRT_TEAM_FIT
+// warp ns per slice: a + b (KT - 1) + L (c + d (KT - 1)) for L groups a slice; per row: e + f R
+// for R rounds of 256 entries; per pass barrier of a multi-CTA team (ns)
+#define IMRT_TEAM_FIT 761.0, 184.0, 382.0, 49.0, 311.0, 995.0, 1500.0
+#endif
+constexpr double kTeamFit[7] = {IMRT_TEAM_FIT};
+
+TeamCost team_cost(const imrt_plan* p, const imrt_plan::TeamSlices& ts, int kind, int max_iter, int kt) {
+    TeamCost c;
+    const imrt_plan::TeamHist& h = p->team_hist[kind];
+    const double it = (double)std::max(max_iter, 1);
+    c.fwd = h.fwd >= 0 ? (double)std::max(h.fwd, 1) : it * (kt == 1 ? 1.3 : 1.0) + 1.0;
+    c.bwd = h.bwd >= 0 ? (double)std::max(h.bwd, 1) : it + 1.0;
+    c.slices = std::max(ts.n_busy, 1);
+    c.rows = std::max(p->n, 1);
+    const double L = ts.n_busy > 0 ? (double)ts.n_groups / ts.n_busy : 0.0;
+    const double R = (double)p->nnz / c.rows / 256.0 + 0.5;
+    // FP32 groups move twice the bytes of 16-bit ones and half the entries (GE 8 either way)
+    const double wide = kind == 1 ? 1.4 : 1.0;
+    c.slice_ns = kTeamFit[0] + kTeamFit[1] * (kt - 1) + L * wide * (kTeamFit[2] + kTeamFit[3] * (kt - 1));
+    c.row_ns = kTeamFit[4] + kTeamFit[5] * R * wide;
+    c.sync_ns = kTeamFit[6];
+    return c;
+}
+
+// Team sizes for one launch of `grid` CTAs. With no more plans than CTAs every plan starts with
+// one CTA and the CTAs left go, one at a time, to the plan with the longest estimated time while
+// that shortens it (the makespan's longest-first greedy). With more plans than CTAs every team
+// is one CTA and takes several plans in turn, the longest first to the least-loaded team (LPT).
+// Fills team0 / team_size of every TeamPlan and the team lists.
+void team_partition(const std::vector<TeamCost>& cost, int grid, std::vector<TeamPlan>& tp,
+                    std::vector<int32_t>& cta_team, std::vector<int32_t>& team_first,
                     std::vector<int32_t>& team_plan) {
     const int n = (int)cost.size();
-    double total = 0.0;
-    for (double c : cost) total += c;
-    std::vector<int> T(n, 1);
-    int used = n;
-    if (n <= grid) {
-        used = 0;
-        for (int i = 0; i < n; ++i) {
-            T[i] = std::max(1, std::min(cap[i], (int)std::floor(grid * cost[i] / std::max(total, 1e-300))));
-            used += T[i];
-        }
-        while (used > grid) {  // the floor of 1 can overshoot: shrink the largest teams
-            int k = (int)(std::max_element(T.begin(), T.end()) - T.begin());
-            if (T[k] <= 1) break;
-            --T[k];
-            --used;
-        }
-        while (used < grid) {  // hand out the rest where a CTA saves the most time
-            int best = -1;
-            double gain = 0.0;
-            for (int i = 0; i < n; ++i) {
-                if (T[i] >= cap[i]) continue;
-                const double g = cost[i] / T[i] - cost[i] / (T[i] + 1);
-                if (g > gain) gain = g, best = i;
-            }
-            if (best < 0) break;
-            ++T[best];
-            ++used;
-        }
-    }
     cta_team.assign(grid, -1);
     team_first.clear();
     team_plan.clear();
-    if (n <= grid && used <= grid) {
+    if (n <= grid) {
+        std::vector<int> T(n, 1);
+        using Item = std::pair<double, int>;
+        std::priority_queue<Item> heap;  // longest estimated time first
+        for (int i = 0; i < n; ++i) heap.push(Item{cost[i].at(1), i});
+        for (int used = n; used < grid && !heap.empty();) {
+            const Item top = heap.top();
+            heap.pop();
+            const int i = top.second;
+            const double next = cost[i].at(T[i] + 1);
+            if (!(next < top.first)) break;  // the longest plan gains nothing from one more CTA
+            ++T[i];
+            ++used;
+            heap.push(Item{next, i});
+        }
         int c0 = 0;
         for (int i = 0; i < n; ++i) {
             tp[i].team0 = c0;
@@ -1537,10 +1570,9 @@ void team_partition(const std::vector<double>& cost, const std::vector<int>& cap
         team_first.push_back(n);
         return;
     }
-    // more plans than CTAs: one-CTA teams, plans dealt longest first to the least-loaded team
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a].at(1) > cost[b].at(1); });
     using Load = std::pair<double, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int t = 0; t < grid; ++t) heap.push(Load{0.0, t});
@@ -1551,7 +1583,7 @@ void team_partition(const std::vector<double>& cost, const std::vector<int>& cap
         lists[l.second].push_back(i);
         tp[i].team0 = l.second;
         tp[i].team_size = 1;
-        heap.push(Load{l.first + cost[i], l.second});
+        heap.push(Load{l.first + cost[i].at(1), l.second});
     }
     for (int t = 0; t < grid; ++t) {
         cta_team[t] = t;
@@ -1585,8 +1617,7 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
             if (copy_of(plans[i], precision[i]).fmt == fmt) idx.push_back(i);
         const size_t np = idx.size();
         std::vector<TeamPlan> tp(np);
-        std::vector<double> cost(np);
-        std::vector<int> cap(np);
+        std::vector<TeamCost> cost(np);
         size_t smem = 0;
         for (size_t k = 0; k < np; ++k) {
             imrt_plan* p = plans[idx[k]];
@@ -1624,20 +1655,14 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
             t.n_busy = ts->n_busy;
             t.n_idle = ts->n_idle;
             t.H = p->t_H;
-            // cost: bytes per iteration, plus the arithmetic of the step sizes beyond the first
-            // (each forms and accumulates one more trial point per entry), times the budget
-            const int64_t vb = (int64_t)elem_bytes(prec);
-            cost[k] = (double)std::max(max_iter[idx[k]], 1) *
-                      ((double)(p->nnz * 2 * (vb + 2) + (int64_t)p->m * 17 + (int64_t)p->n * 8) +
-                       (double)IMRT_TEAM_KT_COST * (double)p->nnz * (double)(p->opt.k_trials - 1));
-            cap[k] = std::max(1, std::min(ts->n_busy, p->n) / 16);
+            cost[k] = team_cost(p, *ts, fmt == kFmtF32C16 ? 1 : 0, max_iter[idx[k]], p->opt.k_trials);
             smem = std::max(smem, team_smem_bytes(p->n_pad, p->opt.k_trials, fmt));
         }
         const int per_sm = team_ctas_per_sm(fmt, smem);
         if (per_sm < 1) return set_error("the team solver does not fit on an SM"), IMRT_EUNSUPPORTED;
         const int grid = sm_count * per_sm;
         std::vector<int32_t> cta_team, team_first, team_plan;
-        team_partition(cost, cap, grid, tp, cta_team, team_first, team_plan);
+        team_partition(cost, grid, tp, cta_team, team_first, team_plan);
         const int n_teams = (int)team_first.size() - 1;
         // one device block: plans, CTA map, team lists, barrier / stop words (zero)
         auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -1681,6 +1706,9 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
     CK(cudaStreamSynchronize(s));
     for (size_t i = 0; i < n; ++i) {
         const DevState& d = *plans[i]->st_host;
+        imrt_plan::TeamHist& h = plans[i]->team_hist[copy_of(plans[i], precision[i]).fmt == kFmtF32C16 ? 1 : 0];
+        h.fwd = d.passes;
+        h.bwd = d.grad_passes;
         res[i].launches += (int)fmts.size();
         res[i].passes += d.passes;
         res[i].grad_passes += d.grad_passes;
@@ -1841,6 +1869,8 @@ imrt_status plan_update(imrt_plan* p, const imrt_csr* D, const uint8_t* structur
     fresh.cancel_host = p->cancel_host;
     fresh.cancel_dev = p->cancel_dev;
     for (int k = 0; k < 4; ++k) fresh.ev[k] = p->ev[k];
+    fresh.team_hist[0] = p->team_hist[0];  // a re-plan of similar size: the same pass estimate
+    fresh.team_hist[1] = p->team_hist[1];
     *p = std::move(fresh);
     imrt_status st = set_sizes(p, D, n_structures);
     if (st == IMRT_OK) st = alloc_vectors(p);
