@@ -75,10 +75,12 @@ template <int NQ>
 __device__ __forceinline__ void cta_sum(Df (&v)[NQ], double* out) {
     __shared__ Df red[kTW][kMaxTrials];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const Df t = warp_sum(v[q]);
-        if (lane == 0) red[wib][q] = t;
+    if constexpr (NQ == 1) {
+        const Df t = warp_sum(v[0]);
+        if (lane == 0) red[wib][0] = t;
+    } else {  // one butterfly for all values (each is warp_sum's tree)
+        const Df t = warp_sum_multi<NQ>(v, lane);
+        if ((lane & (32 / NQ - 1)) == 0) red[wib][warp_sum_multi_q<NQ>(lane)] = t;
     }
     __syncthreads();
     if (threadIdx.x < NQ) {
@@ -89,7 +91,8 @@ __device__ __forceinline__ void cta_sum(Df (&v)[NQ], double* out) {
     __syncthreads();
 }
 
-// G of every evaluated step size: the slice partials (double-float pairs) added in slice order.
+// The busy slices' part of G for every evaluated step size: their partials (double-float pairs,
+// stored by unit index) added in unit order.
 template <int NQ>
 __device__ __forceinline__ void sum_objective(const TeamPlan& P, const double* objb, int nq, double* out) {
     const bool multi = P.team_size > 1;
@@ -97,15 +100,28 @@ __device__ __forceinline__ void sum_objective(const TeamPlan& P, const double* o
     Df v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) v[q] = Df{0.0f, 0.0f};
-    for (int s = threadIdx.x; s < P.n_slices; s += kTeamThreads) {
+    for (int u = threadIdx.x; u < P.n_busy; u += kTeamThreads) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
             if (q < nq) {
-                const float2 w = ld_team(ob + (size_t)q * P.n_slices + s, multi);
+                const float2 w = ld_team(ob + (size_t)q * P.n_busy + u, multi);
                 v[q] = df_add(v[q], Df{w.x, w.y});
             }
     }
     cta_sum<NQ>(v, out);
+}
+
+// The slices without entries: their dose is 0 at every x, so their part of G is one constant,
+// summed once per solve from the partials the evaluation pass left (idle list order).
+__device__ __forceinline__ void sum_idle(const TeamPlan& P, double* out) {
+    const bool multi = P.team_size > 1;
+    const float2* ob = reinterpret_cast<const float2*>(P.obj) + (size_t)2 * kMaxTrials * P.n_busy;
+    Df v[1] = {Df{0.0f, 0.0f}};
+    for (int u = threadIdx.x; u < P.n_idle; u += kTeamThreads) {
+        const float2 w = ld_team(ob + u, multi);
+        v[0] = df_add(v[0], Df{w.x, w.y});
+    }
+    cta_sum<1>(v, out);
 }
 
 // The penalty epilogue of one slice (Eq. (1)): z and r of its 32 voxels for the evaluated step
@@ -113,7 +129,7 @@ __device__ __forceinline__ void sum_objective(const TeamPlan& P, const double* o
 template <int KT>
 __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T, int s, int lane,
                                                const float (&acc)[KT], float* const (&zq)[KT],
-                                               float* const (&rq)[KT], int nq, double* objb, int rows) {
+                                               float* const (&rq)[KT], int nq, double* objb, int slot) {
     const int p = s * kSlice + lane;
     Df Fq[KT];
 #pragma unroll
@@ -137,11 +153,7 @@ __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T
     for (int q = 0; q < KT; ++q) {
         if (q >= nq) continue;
         const Df g = warp_sum(Fq[q]);
-        if (lane == 0) {
-            if (rows == 1) ob[(size_t)q * P.n_slices + s] = make_float2(g.hi, g.lo);
-            else
-                for (int k = 0; k < rows; ++k) ob[(size_t)k * P.n_slices + s] = make_float2(g.hi, g.lo);
-        }
+        if (lane == 0) ob[(size_t)q * P.n_busy + slot] = make_float2(g.hi, g.lo);
     }
 }
 
@@ -149,8 +161,8 @@ __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T
 // of the two partial buffers, which alternate between passes so that a CTA may start the next
 // pass while a teammate still adds the last one). xs holds the (scaled) trial points
 // interleaved by step size. `eval`: one point into set `cur`, and the slices without entries
-// too, whose partial goes to every step size of both buffers (their dose is 0 at every x, so
-// the trial passes skip them).
+// too, whose partials go to the idle part of obj (their dose is 0 at every x: the trial passes
+// skip them and their part of G is summed once).
 template <class F, int KT>
 __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, const float* xs, int cur, bool eval, int gw,
                              int W, double* objb) {
@@ -170,7 +182,7 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
         for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
         slice_row_dot<F, KT, kTeamStage>(P.val, P.col, __ldg(P.slice_off + s), 0, __ldg(P.slice_len + s), lane, xs,
                                          acc);
-        slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, eval ? 1 : KT, objb, 1);
+        slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, eval ? 1 : KT, objb, u);
     }
     if (eval) {
         for (int u = gw; u < P.n_idle; u += W) {
@@ -178,7 +190,7 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
             float acc[KT];
 #pragma unroll
             for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-            slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, 1, P.obj, 2 * kMaxTrials);
+            slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, 1, P.obj + (size_t)2 * kMaxTrials * P.n_busy, u);
         }
     }
 }
@@ -192,10 +204,11 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
 // laid out [stage][chunk][lane] so the reads are free of bank conflicts; the few bytes one lane
 // copies for others (mask bytes) are read after the warp's cp.async wait and __syncwarp.
 // ---------------------------------------------------------------------------------------------
-// Each warp's ring gets about kRingWarpBytes: as many stages as fit (bytes in flight per SM is
-// what a latency-bound stream needs: about 66 KB per SM at the copy bandwidth and a loaded
-// DRAM latency near 1.5 us).
-constexpr int kRingWarpBytes = 10240;
+// Each warp's ring gets about kRingWarpBytes: as many stages as fit. Shared memory and L1 share
+// one array per SM, and the transposed pass's r gathers hit in L1: measured on GB300, rings of
+// 6 KB a warp (3 to 5 stages) made that pass 13% faster than rings of 10 KB and left the forward
+// pass as fast.
+constexpr int kRingWarpBytes = 6144;
 
 // forward stage: NCH 16-byte chunks of one group per lane, and, with a slice's last group, the
 // epilogue inputs of its 32 voxels (caller row index, target dose, mask and target bytes)
@@ -208,8 +221,8 @@ __host__ __device__ constexpr int fwd_stages() { return kRingWarpBytes / fwd_sta
 template <class F>
 __host__ __device__ constexpr int fwd_ring_bytes() { return fwd_stages<F>() * fwd_stage_bytes<F>(); }
 // transposed stage: kBwdRounds rounds of a row; per round and lane one group of 8 entries
-// (values, 16-bit offsets) and its segment
-constexpr int kBwdRounds = 2;
+// (values, 16-bit offsets) and its segment (two rounds a stage measured no faster than one)
+constexpr int kBwdRounds = 1;
 template <int PREC>
 __host__ __device__ constexpr int bwd_val_bytes() {
     return PREC == kFmtF32C16 ? 32 : PREC == IMRT_FP8E4M3 ? 8 : 16;
@@ -306,7 +319,7 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
     float* e_vt = reinterpret_cast<float*>(e_ro + NS * 32);             // [NS][32]
     uint8_t* e_mask = reinterpret_cast<uint8_t*>(e_vt + NS * 32);       // [NS][32]
     uint8_t* e_vtm = e_mask + NS * 32;                                   // [NS][32]
-    int2* meta = reinterpret_cast<int2*>(e_vtm + NS * 32);              // [NS]: slice, 1 first | 2 last
+    int2* meta = reinterpret_cast<int2*>(e_vtm + NS * 32);              // [NS]: slice, 1 first | 2 last | unit << 2
     float* zq[KT];
     float* rq[KT];
 #pragma unroll
@@ -318,6 +331,27 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
     float lam[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) lam[q] = lamp[q];
+    // The slice partials of NB consecutive slices (8 values) share one butterfly; each value's
+    // sum is warp_sum's xor tree, so the partials are those of one butterfly per slice.
+    constexpr int NB = 8 / KT;
+    Df pend[8];
+    int sid[NB];  // their unit indices (the partials' slots)
+#pragma unroll
+    for (int t = 0; t < 8; ++t) pend[t] = Df{0.0f, 0.0f};
+#pragma unroll
+    for (int t = 0; t < NB; ++t) sid[t] = 0;
+    int np = 0;  // slices pending
+    auto flush = [&]() {
+        const Df g = warp_sum_multi<8>(pend, lane);
+        const int vq = warp_sum_multi_q<8>(lane), j = vq / KT;
+        int sj = sid[0];
+#pragma unroll
+        for (int t = 1; t < NB; ++t)
+            if (j == t) sj = sid[t];
+        if ((lane & 3) == 0 && j < np)
+            reinterpret_cast<float2*>(objb)[(size_t)(vq % KT) * P.n_busy + sj] = make_float2(g.hi, g.lo);
+        np = 0;
+    };
     const int nb = P.n_busy;
     int pu = gw, pk = 0, pg = 0;  // producer: unit (gw + pk W) and group
     UnitQueue uq;
@@ -340,7 +374,7 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
                     if (lane < 8) cp_async4(e_vtm + st * 32 + 4 * lane, P.vtm + (size_t)pr.s * kSlice + 4 * lane);
                 }
             }
-            if (lane == 0) meta[st] = make_int2(pr.s, (pg == 0 ? 1 : 0) | (last ? 2 : 0));
+            if (lane == 0) meta[st] = make_int2(pr.s, (pg == 0 ? 1 : 0) | (last ? 2 : 0) | (pu << 2));
             if (last) {
                 pu += W;
                 ++pk;
@@ -396,13 +430,17 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
                     rq[q][ro] = rj[q];
                 }
             }
-            // every step size's slice partial in one butterfly (warp_sum's tree for each)
-            const Df g = warp_sum_multi<KT>(Fq, lane);
-            if ((lane & (32 / KT - 1)) == 0)
-                reinterpret_cast<float2*>(objb)[(size_t)warp_sum_multi_q<KT>(lane) * P.n_slices + s] =
-                    make_float2(g.hi, g.lo);
+#pragma unroll
+            for (int t = 0; t < NB; ++t)
+                if (np == t) {
+#pragma unroll
+                    for (int q = 0; q < KT; ++q) pend[t * KT + q] = Fq[q];
+                    sid[t] = mt.y >> 2;
+                }
+            if (++np == NB) flush();
         }
     }
+    if (np > 0) flush();
     cp_async_wait<0>();  // only empty groups can remain
     __syncwarp();
 }
@@ -621,11 +659,13 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
     if (lead && sp.trace >= 2 && sp.tr_x)
         for (int i = tid; i < n; i += BW) sp.tr_x[i] = xa[i];
     const bool multi = TS > 1;
-    const size_t obj_buf = (size_t)kMaxTrials * P.n_slices;
+    const size_t obj_buf = (size_t)kMaxTrials * P.n_busy;
     team_forward<F, 1>(P, sh.T, xs, 0, true, gw, W, P.obj);  // pass 0: buffer 0
     bool fail = !team_barrier(P, ++bar);
+    sum_idle(P, sh.sums);
+    const double G_idle = sh.sums[0];  // every CTA of the team holds the same
     sum_objective<1>(P, P.obj, 1, sh.sums);
-    double G = sh.sums[0];
+    double G = sh.sums[0] + G_idle;
     const double G0 = G;
     int status = bad_x ? (int)IMRT_EINVAL : 0, stop = 0;
     int cur = 0, iter = 0, total_bt = 0, passes = 1, grad_passes = 0;
@@ -732,7 +772,7 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
                     status = IMRT_ELINESEARCH;
                     break;
                 }
-                const double d = sh.d2[q], Gt = sh.sums[q];
+                const double d = sh.d2[q], Gt = sh.sums[q] + G_idle;
                 if (d == 0.0) {
                     stop = IMRT_STOP_STATIONARY;
                     break;
@@ -749,7 +789,7 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
                 eol = eol * sp.alpha;
             }
             if (accepted >= 0) {
-                const double Gt = sh.sums[accepted];
+                const double Gt = sh.sums[accepted] + G_idle;
                 const float la = lamf[accepted];
                 __syncthreads();
                 for (int i = tid; i < n_pad; i += BW) xa[i] = fmaxf(0.0f, fmaf(-la, gs[i], xa[i]));
