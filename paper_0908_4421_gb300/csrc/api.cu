@@ -1485,8 +1485,8 @@ const char* team_unsupported(const imrt_plan* p, int precision, int max_smem) {
     if (p->t_H <= 0) return "the team solver needs at most 1048576 voxels (segmented beamlet-major copy)";
     if (copy_of(p, precision).fmt == IMRT_FP32) return "the team solver needs at most 65536 beamlets";
     if (team_smem_bytes(p->n_pad, p->opt.k_trials, copy_of(p, precision).fmt) + 16384 > (size_t)max_smem)
-        return "the team solver stages x, g, the trial points (n * (2 + k_trials) * 4 bytes) and its copy rings "
-               "in shared memory: they exceed it";
+        return "the team solver stages x, g, the beamlet scales and the trial points (4 n (4 or 5) bytes) and its "
+               "copy rings in shared memory: they exceed it";
     return nullptr;
 }
 

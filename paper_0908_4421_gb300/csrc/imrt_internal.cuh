@@ -292,14 +292,14 @@ constexpr unsigned kTeamSpinLimit = 1u << 24;  // barrier polls before a team gi
 cudaError_t launch_team(int fmt, const TeamArgs& args, int grid, size_t smem, cudaStream_t stream);
 // Resident team CTAs per SM at `smem` dynamic bytes (0 if the format has no team kernel).
 int team_ctas_per_sm(int fmt, size_t smem);
-// Dynamic shared memory of a team CTA: x, g and the trial points of a plan of n_pad beamlets at
+// Dynamic shared memory of a team CTA: x, g, the beamlet scales and the trial points of a plan of n_pad beamlets at
 // k_trials step sizes, then the warps' copy rings for format `fmt` (team_ring_bytes).
 // Floats per beamlet of a team CTA's trial-point area: the trial point itself for one step size,
 // else the scaled pair (x s, g s) from which each step size's point is formed on the fly.
 __host__ __device__ constexpr int team_x_floats(int k_trials) { return k_trials == 1 ? 1 : 2; }
 size_t team_ring_bytes(int fmt);
 inline size_t team_smem_bytes(int n_pad, int k_trials, int fmt) {
-    return (((size_t)n_pad * 4u * (size_t)(2 + team_x_floats(k_trials)) + 127) & ~(size_t)127) +
+    return (((size_t)n_pad * 4u * (size_t)(3 + team_x_floats(k_trials)) + 127) & ~(size_t)127) +
            team_ring_bytes(fmt);
 }
 

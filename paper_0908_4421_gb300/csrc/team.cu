@@ -605,6 +605,12 @@ __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float
     __syncwarp();
 }
 
+// The Armijo controller's state of one team solve (written by one thread, read by all).
+struct TeamCtl {
+    double G, lam, eol, dG, lam_acc;
+    int status, stop, bt, total_bt, iter, cur, accepted;
+};
+
 struct TeamShared {
     TeamPlan P;
     float lam[kMaxTrials];  // the step sizes of the current trial pass
@@ -614,6 +620,7 @@ struct TeamShared {
     double d2[kMaxTrials];
     float ginf[kTW];
     int64_t sb[kTW][17];
+    TeamCtl c;
 };
 
 // Solves plan P (staged in sh.P) completely with this CTA as member `rank` of the plan's team.
@@ -627,8 +634,9 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
     float* xa = smem;             // accepted x
     float* gs = xa + n_pad;       // g at the accepted x
     float* xs = gs + n_pad;       // the scaled trial point (one step size), or the pairs (x s, g s)
+    float* ss = xs + (size_t)n_pad * team_x_floats(KT);  // the per-beamlet scales (1 for FP32)
     unsigned char* ring = reinterpret_cast<unsigned char*>(smem) +
-                          (((size_t)n_pad * 4u * (size_t)(2 + team_x_floats(KT)) + 127) & ~(size_t)127) +
+                          (((size_t)n_pad * 4u * (size_t)(3 + team_x_floats(KT)) + 127) & ~(size_t)127) +
                           (size_t)wib * warp_ring_bytes<F>();  // this warp's copy ring
     cta_copy_in(&sh.sp, P.sp);
     cta_copy_in(&sh.T, P.terms);  // P was staged by the caller before its __syncthreads
@@ -652,8 +660,10 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
                 if (!(x >= 0.0f) || !isfinite(x)) bad_x = 1;
             }
         }
+        const float sc = P.scale && i < n ? __ldg(P.scale + i) : 1.0f;
         xa[i] = x;
-        xs[i] = P.scale ? x * __ldg(P.scale + i) : x;
+        ss[i] = sc;
+        xs[i] = P.scale ? x * sc : x;
     }
     __syncthreads();
     if (lead && sp.trace >= 2 && sp.tr_x)
@@ -705,30 +715,50 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
         return ok;
     };
 
+    // The Armijo controller's scalars live in shared memory: one thread decides (its FP64
+    // arithmetic would otherwise run 512 times over on a part with a small FP64 rate) and every
+    // thread reads the outcome after a barrier.
+    TeamCtl& c = sh.c;
+    if (tid == 0) {
+        c.G = G;
+        c.dG = 0.0;
+        c.lam_acc = 0.0;
+        c.status = status;
+        c.stop = stop;
+        c.cur = 0;
+        c.iter = 0;
+        c.total_bt = 0;
+    }
+    __syncthreads();
     while (status == 0 && stop == 0) {
         if (!gradient()) {
             status = IMRT_ECUDA;
             break;
         }
-        double lam = sp.lambda0, eol = sp.eps_over_lambda0;
-        int bt = 0;
+        if (tid == 0) {
+            c.lam = sp.lambda0;
+            c.eol = sp.eps_over_lambda0;
+            c.bt = 0;
+        }
         while (status == 0 && stop == 0) {
             // trial points of the KT step sizes lam, lam / alpha, ... and their ||x_t - x||^2
-            float lamf[KT];
-            {
-                double l = lam;
+            if (tid == 0) {
+                double l = c.lam;
 #pragma unroll
                 for (int q = 0; q < KT; ++q) {
-                    lamf[q] = (float)l;
+                    sh.lam[q] = (float)l;
                     l = l / sp.alpha;
                 }
             }
+            __syncthreads();
+            float lamf[KT];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) lamf[q] = sh.lam[q];
             Df d2[KT];
 #pragma unroll
             for (int q = 0; q < KT; ++q) d2[q] = Df{0.0f, 0.0f};
             for (int i = tid; i < n_pad; i += BW) {
-                const float xv = xa[i], gv = gs[i];
-                const float sc = P.scale ? __ldg(P.scale + i) : 1.0f;
+                const float xv = xa[i], gv = gs[i], sc = ss[i];
                 // the dose pass forms max(0, x s - lambda g s) from the scaled pair (x s, g s),
                 // for one step size here, for several on the fly (the same expression either way)
                 const float xsc = xv * sc, gsc = gv * sc;
@@ -746,84 +776,101 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
                     d2[q] = df_add(d2[q], Df{sq.hi, fmaf(2.0f * dh, dl, sq.lo)});
                 }
             }
-            if (tid < KT) sh.lam[tid] = lamf[tid];
             cta_sum<KT>(d2, sh.d2);  // also makes xs visible to every warp
             double* objb = P.obj + (size_t)(passes & 1) * obj_buf;
             team_forward_ring<F, KT>(P, sh.T, xs, sh.lam, cur, gw, W, objb, ring);
             ++passes;
             // The stop request is the team lead's alone, so every CTA reads the same one; its two
-            // slots alternate with the barriers, as the partial buffers do.
+            // slots alternate with the barriers, as the partial buffers do. The cancel flag lives
+            // in host memory: it is polled every 8th pass.
             if (lead && tid == 0) {
                 unsigned req = 0;
-                if (sp.cancel && *sp.cancel) req = 1;
+                if (sp.cancel && (passes & 7) == 0 && *sp.cancel) req = 1;
                 else if (sp.timeout_ns && global_timer_ns() - t_start > sp.timeout_ns) req = 2;
                 P.sync[1 + ((bar + 1) & 1)] = req;
             }
             if (!team_barrier(P, ++bar)) {
                 status = IMRT_ECUDA;
+                if (tid == 0) c.status = status;
                 break;
             }
             sum_objective<KT>(P, objb, KT, sh.sums);
-            const unsigned req = ld_team(&P.sync[1 + (bar & 1)], multi);
-            // Eq. (5) for the step sizes in order (the sequential Armijo decisions)
-            int accepted = -1;
-            for (int q = 0; q < KT && status == 0 && stop == 0; ++q) {
-                if (bt + q > sp.max_bt) {
-                    status = IMRT_ELINESEARCH;
-                    break;
+            if (tid == 0) {
+                const unsigned req = ld_team(&P.sync[1 + (bar & 1)], multi);
+                // Eq. (5) for the step sizes in order (the sequential Armijo decisions)
+                int accepted = -1;
+                for (int q = 0; q < KT && c.status == 0 && c.stop == 0; ++q) {
+                    if (c.bt + q > sp.max_bt) {
+                        c.status = IMRT_ELINESEARCH;
+                        break;
+                    }
+                    const double d = sh.d2[q], Gt = sh.sums[q] + G_idle;
+                    if (d == 0.0) {
+                        c.stop = IMRT_STOP_STATIONARY;
+                        break;
+                    }
+                    if (!isfinite(Gt)) {
+                        c.status = IMRT_ENUMERIC;
+                        break;
+                    }
+                    if (Gt < c.G - c.eol * d) {
+                        accepted = q;
+                        break;
+                    }
+                    c.lam = c.lam * sp.inv_alpha;  // step 4
+                    c.eol = c.eol * sp.alpha;
                 }
-                const double d = sh.d2[q], Gt = sh.sums[q] + G_idle;
-                if (d == 0.0) {
-                    stop = IMRT_STOP_STATIONARY;
-                    break;
+                c.accepted = accepted;
+                if (accepted >= 0) {
+                    const double Gt = sh.sums[accepted] + G_idle;
+                    c.dG = fabs(Gt - c.G);
+                    if (lead) {
+                        if (sp.tr_lam) sp.tr_lam[c.iter] = c.lam;
+                        if (sp.tr_bt) sp.tr_bt[c.iter] = c.bt + accepted;
+                        if (sp.tr_G) sp.tr_G[c.iter + 1] = Gt;
+                    }
+                    c.total_bt += c.bt + accepted;
+                    c.cur = (c.cur + 1 + accepted) % kSets;
+                    c.G = Gt;
+                    c.lam_acc = c.lam;
+                    ++c.iter;
+                    if (Gt == 0.0) c.stop = IMRT_STOP_EXACT;
+                    else if (c.dG < sp.delta * Gt) c.stop = IMRT_STOP_REL;  // step 5: |dG| / G < delta
+                    else if (c.iter >= sp.max_iter) c.stop = IMRT_STOP_MAXITER;
+                    if (c.stop == 0 && req) c.status = req == 1 ? IMRT_ECANCELLED : IMRT_ETIMEOUT;
+                } else {
+                    if (c.status == 0 && c.stop == 0) {
+                        if (c.bt + KT - 1 >= sp.max_bt) c.status = IMRT_ELINESEARCH;
+                        else {
+                            c.bt += KT;
+                            if (req) c.status = req == 1 ? IMRT_ECANCELLED : IMRT_ETIMEOUT;
+                        }
+                    }
+                    if (c.status == IMRT_ELINESEARCH) c.total_bt += sp.max_bt;
                 }
-                if (!isfinite(Gt)) {
-                    status = IMRT_ENUMERIC;
-                    break;
-                }
-                if (Gt < G - eol * d) {
-                    accepted = q;
-                    break;
-                }
-                lam = lam * sp.inv_alpha;  // step 4
-                eol = eol * sp.alpha;
             }
-            if (accepted >= 0) {
-                const double Gt = sh.sums[accepted] + G_idle;
-                const float la = lamf[accepted];
-                __syncthreads();
+            __syncthreads();
+            status = c.status;
+            stop = c.stop;
+            if (c.accepted >= 0) {
+                const float la = lamf[c.accepted];
                 for (int i = tid; i < n_pad; i += BW) xa[i] = fmaxf(0.0f, fmaf(-la, gs[i], xa[i]));
                 __syncthreads();
-                dG = fabs(Gt - G);
-                if (lead && tid == 0) {
-                    if (sp.tr_lam) sp.tr_lam[iter] = lam;
-                    if (sp.tr_bt) sp.tr_bt[iter] = bt + accepted;
-                    if (sp.tr_G) sp.tr_G[iter + 1] = Gt;
-                }
                 if (lead && sp.trace >= 2 && sp.tr_x)
-                    for (int i = tid; i < n; i += BW) sp.tr_x[(size_t)(iter + 1) * n + i] = xa[i];
-                total_bt += bt + accepted;
-                cur = (cur + 1 + accepted) % kSets;
-                G = Gt;
-                lam_acc = lam;
-                ++iter;
+                    for (int i = tid; i < n; i += BW) sp.tr_x[(size_t)c.iter * n + i] = xa[i];
+                cur = c.cur;
                 g_current = false;
-                if (Gt == 0.0) stop = IMRT_STOP_EXACT;
-                else if (dG < sp.delta * Gt) stop = IMRT_STOP_REL;  // step 5: |dG| / G < delta
-                else if (iter >= sp.max_iter) stop = IMRT_STOP_MAXITER;
-                if (stop == 0 && req) status = req == 1 ? IMRT_ECANCELLED : IMRT_ETIMEOUT;
                 break;  // next iteration
             }
-            if (status == 0 && stop == 0) {
-                if (bt + KT - 1 >= sp.max_bt) status = IMRT_ELINESEARCH;
-                else {
-                    bt += KT;
-                    if (req) status = req == 1 ? IMRT_ECANCELLED : IMRT_ETIMEOUT;
-                }
-            }
-            if (status == IMRT_ELINESEARCH) total_bt += sp.max_bt;
         }
     }
+    if (tid == 0) c.status = status;  // a failed barrier is seen by every thread
+    __syncthreads();
+    G = c.G;
+    dG = c.dG;
+    lam_acc = c.lam_acc;
+    iter = c.iter;
+    total_bt = c.total_bt;
     // g at the final x for the KKT residual (Sec. 2.2: x - P(x - g) = 0 at a stationary point)
     if (status != IMRT_ECUDA && !g_current && !gradient()) status = IMRT_ECUDA;
     __shared__ float worst_w[kTW];
