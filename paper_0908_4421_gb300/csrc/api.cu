@@ -1491,27 +1491,30 @@ const char* team_unsupported(const imrt_plan* p, int precision, int max_smem) {
 }
 
 // Estimated time (ns) of one plan's solve on a team of T CTAs: its forward passes deal the busy
-// slices round-robin over the team's 16 T warps, its transposed passes the beamlet rows; a team
-// of several CTAs also pays a barrier per pass. The per-slice and per-row warp times are linear
-// fits to per-plan timings of the persistent kernel on a GB300 (64 uneven FP16 plans and their
-// FP32 polish); the pass counts are the plan's last team solve's, else an estimate.
+// slices round-robin over the team's 16 T warps, its transposed passes the beamlet rows; every
+// forward pass also pays the controller's serial part (objective sums, trial points, decision),
+// and a team of several CTAs a barrier. The constants are least-squares fits to per-plan
+// timings of the persistent kernel on a GB300 (64 uneven FP16 plans and their FP32 polish); the
+// pass counts are the plan's last team solve's, else an estimate.
 struct TeamCost {
     double fwd = 0.0, bwd = 0.0;  // passes
     double slices = 1.0, rows = 1.0;
-    double slice_ns = 0.0, row_ns = 0.0, sync_ns = 0.0;
+    double slice_ns = 0.0, row_ns = 0.0;  // one warp's time per slice / per row
+    double glue_ns = 0.0, glue_sum_ns = 0.0, sync_ns = 0.0;  // per forward pass
     double at(int T) const {
         const double w = (double)(kTeamThreads / 32) * T;
-        return fwd * std::ceil(slices / w) * slice_ns + bwd * std::ceil(rows / w) * row_ns +
-               (T > 1 ? (fwd + bwd) * sync_ns : 0.0);
+        return fwd * (std::ceil(slices / w) * slice_ns + glue_ns + glue_sum_ns / T + (T > 1 ? sync_ns : 0.0)) +
+               bwd * std::ceil(rows / w) * row_ns;
     }
 };
 
 #ifndef IMRT_TEAM_FIT
-// warp ns per slice: a + b (KT - 1) + L (c + d (KT - 1)) for L groups a slice; per row: e + f R
-// for R rounds of 256 entries; per pass barrier of a multi-CTA team (ns)
-#define IMRT_TEAM_FIT 761.0, 184.0, 382.0, 49.0, 311.0, 995.0, 1500.0
+// warp ns per slice: a + b (k - 1) + L (c + d (k - 1)) for L groups a slice and k step sizes;
+// per row: e R for R rounds of 256 entries; per forward pass: f + g n / 1000 + h (busy slices)
+// k / 1000 / T, and i for a team of several CTAs
+#define IMRT_TEAM_FIT 670.0, 197.0, 407.0, 48.0, 957.0, 5680.0, 7290.0, 3980.0, 3210.0
 #endif
-constexpr double kTeamFit[7] = {IMRT_TEAM_FIT};
+constexpr double kTeamFit[9] = {IMRT_TEAM_FIT};
 
 TeamCost team_cost(const imrt_plan* p, const imrt_plan::TeamSlices& ts, int kind, int max_iter, int kt) {
     TeamCost c;
@@ -1523,11 +1526,13 @@ TeamCost team_cost(const imrt_plan* p, const imrt_plan::TeamSlices& ts, int kind
     c.rows = std::max(p->n, 1);
     const double L = ts.n_busy > 0 ? (double)ts.n_groups / ts.n_busy : 0.0;
     const double R = (double)p->nnz / c.rows / 256.0 + 0.5;
-    // FP32 groups move twice the bytes of 16-bit ones and half the entries (GE 8 either way)
+    // FP32 groups move twice the bytes of 16-bit ones (GE 8 either way)
     const double wide = kind == 1 ? 1.4 : 1.0;
     c.slice_ns = kTeamFit[0] + kTeamFit[1] * (kt - 1) + L * wide * (kTeamFit[2] + kTeamFit[3] * (kt - 1));
-    c.row_ns = kTeamFit[4] + kTeamFit[5] * R * wide;
-    c.sync_ns = kTeamFit[6];
+    c.row_ns = kTeamFit[4] * R * wide;
+    c.glue_ns = kTeamFit[5] + kTeamFit[6] * p->n / 1000.0;
+    c.glue_sum_ns = kTeamFit[7] * ts.n_busy * kt / 1000.0;
+    c.sync_ns = kTeamFit[8];
     return c;
 }
 

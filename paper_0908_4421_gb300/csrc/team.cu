@@ -747,7 +747,7 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
 #pragma unroll
                 for (int q = 0; q < KT; ++q) {
                     sh.lam[q] = (float)l;
-                    l = l / sp.alpha;
+                    l = l * sp.inv_alpha;
                 }
             }
             __syncthreads();
@@ -794,9 +794,10 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
                 if (tid == 0) c.status = status;
                 break;
             }
+            // the stop request's load is issued before the sums, which hide its latency
+            const unsigned req = tid == 0 ? ld_team(&P.sync[1 + (bar & 1)], multi) : 0u;
             sum_objective<KT>(P, objb, KT, sh.sums);
             if (tid == 0) {
-                const unsigned req = ld_team(&P.sync[1 + (bar & 1)], multi);
                 // Eq. (5) for the step sizes in order (the sequential Armijo decisions)
                 int accepted = -1;
                 for (int q = 0; q < KT && c.status == 0 && c.stop == 0; ++q) {
