@@ -235,14 +235,15 @@ imrt_status plan_solve(imrt_plan* plan, const float* x0, imrt_result* res);
  * Solves several plans (Sec. 2.2, steps 1-5, each plan independently) in one
  * launch. When every plan has solver = IMRT_SOLVER_TEAM, the plans share one
  * persistent cooperative kernel per storage format: its CTAs are cut into teams
- * sized to each plan's bytes per pass (one plan per team, or, with more plans
- * than CTAs, one-CTA teams that take several plans in turn), and every team
- * runs its plans' whole solves without returning to the host. A plan's result
- * is bitwise the same as when it is solved alone with the team solver (fixed
- * reduction orders, independent of the team size). Otherwise every plan's solve
- * is one branch of a CUDA graph. Each plan keeps its own options (precision,
- * k_trials, x_init, max_iter, ...), and reduced-precision plans get their FP32
- * polish in a second launch.
+ * sized to each plan's estimated solve time (one plan per team, or, with more
+ * plans than CTAs, one-CTA teams that take several plans in turn), and every
+ * team runs its plans' whole solves without returning to the host, a
+ * reduced-precision plan's FP32 polish included (same team, same launch, from
+ * the x the team holds). A plan's result is bitwise the same as when it is
+ * solved alone with the team solver (fixed reduction orders, independent of the
+ * team size). Otherwise every plan's solve is one branch of a CUDA graph and
+ * reduced-precision plans get their FP32 polish in a second launch. Each plan
+ * keeps its own options (precision, k_trials, x_init, max_iter, ...).
  *   plans    count distinct plan handles.
  *   x0s      NULL, or count pointers read for plans with x_init = 2.
  *   results  count results (host).

@@ -111,6 +111,7 @@ struct SolveGraph {
 // plans running on other streams.
 struct PinnedBlock {
     DevState state;
+    DevState state2;  // the FP32 polish of a fused team solve
     int32_t cancel;
     int32_t pad[15];
 };
@@ -182,6 +183,8 @@ struct imrt_plan {
     Terms* terms_dev = nullptr;
     DevState* st = nullptr;
     SolveParams* sp = nullptr;
+    DevState* st2 = nullptr;    // the FP32 polish run in the same team launch
+    SolveParams* sp2 = nullptr;
     float* x_stage = nullptr;
     float* z_stage = nullptr;
     float* r_stage = nullptr;
@@ -190,6 +193,7 @@ struct imrt_plan {
     double* dscratch = nullptr;
     struct PinnedBlock* pinned = nullptr;  // from the process-wide pool
     DevState* st_host = nullptr;     // pinned
+    DevState* st2_host = nullptr;    // pinned: the polish phase of a fused team solve
     int32_t* cancel_host = nullptr;  // mapped pinned
     int32_t* cancel_dev = nullptr;
     // trace
@@ -1003,6 +1007,8 @@ imrt_status alloc_vectors(imrt_plan* p) {
     TRY(dalloc(p, &p->terms_dev, 1));
     TRY(dalloc(p, &p->st, 1));
     TRY(dalloc(p, &p->sp, 1));
+    TRY(dalloc(p, &p->st2, 1));
+    TRY(dalloc(p, &p->sp2, 1));
     cudaStream_t s = stream_of(p);
     CK(cudaMemsetAsync(p->v.x, 0, sizeof(float) * kSets * p->n_pad, s));
     CK(cudaMemsetAsync(p->v.g, 0, sizeof(float) * p->n_pad, s));
@@ -1017,6 +1023,7 @@ imrt_status alloc_vectors(imrt_plan* p) {
 imrt_status acquire_host_state(imrt_plan* p) {
     TRY(pinned_acquire(&p->pinned));
     p->st_host = &p->pinned->state;
+    p->st2_host = &p->pinned->state2;
     p->cancel_host = &p->pinned->cancel;
     *p->cancel_host = 0;
     CK(cudaHostGetDevicePointer((void**)&p->cancel_dev, p->cancel_host, 0));
@@ -1508,6 +1515,13 @@ struct TeamCost {
     }
 };
 
+// A plan's cost in one launch: its phase, and the FP32 polish the team goes on to, if any.
+struct PlanCost {
+    TeamCost a, b;
+    bool two = false;
+    double at(int T) const { return a.at(T) + (two ? b.at(T) : 0.0); }
+};
+
 #ifndef IMRT_TEAM_FIT
 // warp ns per slice: a + b (k - 1) + L (c + d (k - 1)) for L groups a slice and k step sizes;
 // per row: e R for R rounds of 256 entries; per forward pass: f + g n / 1000 + h (busy slices)
@@ -1541,7 +1555,7 @@ TeamCost team_cost(const imrt_plan* p, const imrt_plan::TeamSlices& ts, int kind
 // that shortens it (the makespan's longest-first greedy). With more plans than CTAs every team
 // is one CTA and takes several plans in turn, the longest first to the least-loaded team (LPT).
 // Fills team0 / team_size of every TeamPlan and the team lists.
-void team_partition(const std::vector<TeamCost>& cost, int grid, std::vector<TeamPlan>& tp,
+void team_partition(const std::vector<PlanCost>& cost, int grid, std::vector<TeamPlan>& tp,
                     std::vector<int32_t>& cta_team, std::vector<int32_t>& team_first,
                     std::vector<int32_t>& team_plan) {
     const int n = (int)cost.size();
@@ -1598,70 +1612,94 @@ void team_partition(const std::vector<TeamCost>& cost, int grid, std::vector<Tea
     team_first.push_back((int32_t)team_plan.size());
 }
 
-// One phase of the given plans in the team solver: one cooperative launch per storage format
-// (in the order of first appearance), then every plan's state read back.
+// The plans in the team solver: one cooperative launch per storage format (in the order of first
+// appearance), then every plan's state read back. A plan with polish[i] set goes on, in the same
+// launch and on the same team, to its FP32 polish (TeamPlan.polish) when its phase ends with
+// status 0 or IMRT_ELINESEARCH, for max(min(polish_iter, max_iter), max_iter - iterations)
+// iterations from the phase's x; that phase's state is read back into st2_host.
 imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vector<int>& precision,
                            const std::vector<int>& max_iter, const std::vector<int>& x_init,
                            const std::vector<const float*>& x0, const std::vector<double>& delta, cudaStream_t s,
-                           std::vector<imrt_result>& res) {
+                           std::vector<imrt_result>& res, const std::vector<char>* polish = nullptr) {
     const size_t n = plans.size();
     int dev = 0, sm_count = 0, max_smem = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto pol = [&](size_t i) { return polish && (*polish)[i] && precision[i] != IMRT_FP32; };
     std::vector<int> fmts;
     for (size_t i = 0; i < n; ++i) {
         const char* why = team_unsupported(plans[i], precision[i], max_smem);
+        if (!why && pol(i)) why = team_unsupported(plans[i], IMRT_FP32, max_smem);
         if (why) return set_error("plan %zu: %s", i, why), IMRT_EUNSUPPORTED;
         const int f = copy_of(plans[i], precision[i]).fmt;
         if (std::find(fmts.begin(), fmts.end(), f) == fmts.end()) fmts.push_back(f);
     }
+    // the TeamPlan of plan p at `prec` (team, sync, st, sp and the polish link are set later)
+    auto fill = [](TeamPlan& t, imrt_plan* p, int prec, const imrt_plan::TeamSlices* ts) {
+        const SellCopy& c = copy_of(p, prec);
+        t = TeamPlan{};
+        t.slice_off = c.slice_off;
+        t.slice_len = c.slice_len;
+        t.val = c.val;
+        t.col = c.col;
+        t.busy = ts->busy;
+        t.units = ts->units;
+        t.idle = ts->idle;
+        t.mask = p->mask;
+        t.r_index = p->perm;
+        t.scale = prec == IMRT_FP32 ? nullptr : p->scale;
+        t.vt = p->vt_on ? p->vt_p : nullptr;
+        t.vtm = p->vt_on ? p->vtm_p : nullptr;
+        t.terms = p->terms_dev;
+        t.rows = p->bwd_order;
+        t.seg = p->t_seg;
+        t.lo = p->t_lo;
+        t.tval = prec == IMRT_FP32 ? (const void*)p->t_vals : (const void*)p->t_valq;
+        t.v = p->v;
+        t.obj = p->team_obj;
+        t.m = p->m;
+        t.n = p->n;
+        t.n_pad = p->n_pad;
+        t.m_pad = p->m_pad;
+        t.n_slices = p->n_slices;
+        t.n_busy = ts->n_busy;
+        t.n_idle = ts->n_idle;
+        t.H = p->t_H;
+    };
     for (int fmt : fmts) {
         std::vector<size_t> idx;
         for (size_t i = 0; i < n; ++i)
             if (copy_of(plans[i], precision[i]).fmt == fmt) idx.push_back(i);
         const size_t np = idx.size();
-        std::vector<TeamPlan> tp(np);
-        std::vector<TeamCost> cost(np);
+        std::vector<TeamPlan> tp(np), tp2(np);
+        std::vector<PlanCost> cost(np);
         size_t smem = 0;
+        bool any_polish = false;
         for (size_t k = 0; k < np; ++k) {
-            imrt_plan* p = plans[idx[k]];
-            const int prec = precision[idx[k]];
+            const size_t i = idx[k];
+            imrt_plan* p = plans[i];
+            const int kt = p->opt.k_trials;
             const imrt_plan::TeamSlices* ts = nullptr;
-            TRY(team_slices(p, prec, &ts));
-            const SellCopy& c = copy_of(p, prec);
-            TeamPlan& t = tp[k];
-            t.slice_off = c.slice_off;
-            t.slice_len = c.slice_len;
-            t.val = c.val;
-            t.col = c.col;
-            t.busy = ts->busy;
-            t.units = ts->units;
-            t.idle = ts->idle;
-            t.mask = p->mask;
-            t.r_index = p->perm;
-            t.scale = prec == IMRT_FP32 ? nullptr : p->scale;
-            t.vt = p->vt_on ? p->vt_p : nullptr;
-            t.vtm = p->vt_on ? p->vtm_p : nullptr;
-            t.terms = p->terms_dev;
-            t.rows = p->bwd_order;
-            t.seg = p->t_seg;
-            t.lo = p->t_lo;
-            t.tval = prec == IMRT_FP32 ? (const void*)p->t_vals : (const void*)p->t_valq;
-            t.v = p->v;
-            t.obj = p->team_obj;
-            t.st = p->st;
-            t.sp = p->sp;
-            t.m = p->m;
-            t.n = p->n;
-            t.n_pad = p->n_pad;
-            t.m_pad = p->m_pad;
-            t.n_slices = p->n_slices;
-            t.n_busy = ts->n_busy;
-            t.n_idle = ts->n_idle;
-            t.H = p->t_H;
-            cost[k] = team_cost(p, *ts, fmt == kFmtF32C16 ? 1 : 0, max_iter[idx[k]], p->opt.k_trials);
-            smem = std::max(smem, team_smem_bytes(p->n_pad, p->opt.k_trials, fmt));
+            TRY(team_slices(p, precision[i], &ts));
+            fill(tp[k], p, precision[i], ts);
+            tp[k].st = p->st;
+            tp[k].sp = p->sp;
+            tp[k].max_iter = p->opt.max_iter;
+            cost[k].a = team_cost(p, *ts, fmt == kFmtF32C16 ? 1 : 0, max_iter[i], kt);
+            smem = std::max(smem, team_smem_bytes(p->n_pad, kt, fmt));
+            if (pol(i)) {
+                const imrt_plan::TeamSlices* t32 = nullptr;
+                TRY(team_slices(p, IMRT_FP32, &t32));
+                fill(tp2[k], p, IMRT_FP32, t32);
+                tp2[k].st = p->st2;
+                tp2[k].sp = p->sp2;
+                tp[k].polish_iter = p->opt.polish_iter;
+                cost[k].b = team_cost(p, *t32, 1, std::min(p->opt.polish_iter, p->opt.max_iter), kt);
+                cost[k].two = true;
+                smem = std::max(smem, team_smem_bytes(p->n_pad, kt, kFmtF32C16));
+                any_polish = true;
+            }
         }
         const int per_sm = team_ctas_per_sm(fmt, smem);
         if (per_sm < 1) return set_error("the team solver does not fit on an SM"), IMRT_EUNSUPPORTED;
@@ -1669,25 +1707,44 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
         std::vector<int32_t> cta_team, team_first, team_plan;
         team_partition(cost, grid, tp, cta_team, team_first, team_plan);
         const int n_teams = (int)team_first.size() - 1;
-        // one device block: plans, CTA map, team lists, barrier / stop words (zero)
+        // one device block: plans, their polish phases, CTA map, team lists, barrier / stop words (zero)
         auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-        const size_t o_plans = 0, o_cta = al(sizeof(TeamPlan) * np), o_first = o_cta + al(4 * cta_team.size()),
-                     o_list = o_first + al(4 * team_first.size()), o_sync = o_list + al(4 * team_plan.size()),
-                     total = o_sync + al(16 * np);
+        const size_t o_plans = 0, o_pol = al(sizeof(TeamPlan) * np),
+                     o_cta = o_pol + (any_polish ? al(sizeof(TeamPlan) * np) : 0),
+                     o_first = o_cta + al(4 * cta_team.size()), o_list = o_first + al(4 * team_first.size()),
+                     o_sync = o_list + al(4 * team_plan.size()), total = o_sync + al(32 * np);
         std::vector<uint8_t> host(total, 0);
         void* dbuf = nullptr;
         CK(pool_malloc(&dbuf, total, dev, s));
         uint8_t* d = static_cast<uint8_t*>(dbuf);
-        for (size_t k = 0; k < np; ++k) tp[k].sync = reinterpret_cast<unsigned int*>(d + o_sync) + 4 * k;
+        for (size_t k = 0; k < np; ++k) {
+            unsigned int* sync = reinterpret_cast<unsigned int*>(d + o_sync) + 8 * k;
+            tp[k].sync = sync;
+            if (pol(idx[k])) {
+                tp2[k].sync = sync + 4;
+                tp2[k].team0 = tp[k].team0;
+                tp2[k].team_size = tp[k].team_size;
+                tp[k].polish = reinterpret_cast<const TeamPlan*>(d + o_pol) + k;
+            }
+        }
         memcpy(host.data() + o_plans, tp.data(), sizeof(TeamPlan) * np);
+        if (any_polish) memcpy(host.data() + o_pol, tp2.data(), sizeof(TeamPlan) * np);
         memcpy(host.data() + o_cta, cta_team.data(), 4 * cta_team.size());
         memcpy(host.data() + o_first, team_first.data(), 4 * team_first.size());
         memcpy(host.data() + o_list, team_plan.data(), 4 * team_plan.size());
         cudaError_t e = cudaMemcpyAsync(d, host.data(), total, cudaMemcpyHostToDevice, s);
         for (size_t k = 0; k < np && e == cudaSuccess; ++k) {
             const size_t i = idx[k];
-            const SolveParams q = make_params(plans[i], nullptr, max_iter[i], x_init[i], x0[i], 0ull, delta[i]);
-            e = cudaMemcpyAsync(plans[i]->sp, &q, sizeof(q), cudaMemcpyHostToDevice, s);
+            imrt_plan* p = plans[i];
+            const SolveParams q = make_params(p, nullptr, max_iter[i], x_init[i], x0[i], 0ull, delta[i]);
+            e = cudaMemcpyAsync(p->sp, &q, sizeof(q), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && pol(i)) {  // the polish: untraced, from the phase's x, at the plan's delta
+                const int saved = p->opt.trace;
+                p->opt.trace = 0;
+                const SolveParams q2 = make_params(p, nullptr, p->opt.max_iter, 2, nullptr, 0ull, p->opt.delta);
+                p->opt.trace = saved;
+                e = cudaMemcpyAsync(p->sp2, &q2, sizeof(q2), cudaMemcpyHostToDevice, s);
+            }
         }
         if (e == cudaSuccess) {
             TeamArgs a{};
@@ -1706,22 +1763,33 @@ imrt_status run_team_phase(const std::vector<imrt_plan*>& plans, const std::vect
             return set_error("team solver launch failed: %s", cudaGetErrorString(e)), IMRT_ECUDA;
         }
     }
-    for (size_t i = 0; i < n; ++i)
+    for (size_t i = 0; i < n; ++i) {
         CK(cudaMemcpyAsync(plans[i]->st_host, plans[i]->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        if (pol(i))
+            CK(cudaMemcpyAsync(plans[i]->st2_host, plans[i]->st2, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
     for (size_t i = 0; i < n; ++i) {
-        const DevState& d = *plans[i]->st_host;
-        imrt_plan::TeamHist& h = plans[i]->team_hist[copy_of(plans[i], precision[i]).fmt == kFmtF32C16 ? 1 : 0];
+        imrt_plan* p = plans[i];
+        const DevState& d = *p->st_host;
+        imrt_plan::TeamHist& h = p->team_hist[copy_of(p, precision[i]).fmt == kFmtF32C16 ? 1 : 0];
         h.fwd = d.passes;
         h.bwd = d.grad_passes;
-        res[i].launches += (int)fmts.size();
+        res[i].launches += 1;
         res[i].passes += d.passes;
         res[i].grad_passes += d.grad_passes;
-        add_bytes(plans[i], precision[i], d.passes, d.grad_passes, &res[i]);
-        plans[i]->cur = d.cur;
+        add_bytes(p, precision[i], d.passes, d.grad_passes, &res[i]);
+        p->cur = d.cur;
+        if (pol(i) && (d.status == IMRT_OK || d.status == IMRT_ELINESEARCH)) {
+            const DevState& d2 = *p->st2_host;
+            p->team_hist[1].fwd = d2.passes;
+            p->team_hist[1].bwd = d2.grad_passes;
+            p->cur = d2.cur;  // the polish's passes are counted by the caller from st2_host
+        }
     }
     return IMRT_OK;
 }
+
 
 }  // namespace
 
@@ -1871,6 +1939,7 @@ imrt_status plan_update(imrt_plan* p, const imrt_csr* D, const uint8_t* structur
     fresh.opt = p->opt;
     fresh.pinned = p->pinned;
     fresh.st_host = p->st_host;
+    fresh.st2_host = p->st2_host;
     fresh.cancel_host = p->cancel_host;
     fresh.cancel_dev = p->cancel_dev;
     for (int k = 0; k < 4; ++k) fresh.ev[k] = p->ev[k];
@@ -2057,7 +2126,6 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
             if (ps[j] == ps[i]) return set_error("plan %d appears twice in the batch", i), IMRT_EINVAL;
         team = team && ps[i]->opt.solver == IMRT_SOLVER_TEAM;
     }
-    auto phase = team ? run_team_phase : run_batch_phase;
     std::vector<imrt_result> res(count);
     memset(res.data(), 0, sizeof(imrt_result) * count);
     std::vector<int> prec(count), iters(count), xinit(count);
@@ -2080,7 +2148,13 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         xinit[i] = o.x_init;
         delta[i] = polish && o.polish_switch > 0.0 ? std::max(o.delta, o.polish_switch) : o.delta;
     }
-    TRY(phase(ps, prec, iters, xinit, x0, delta, s, res));
+    // The team solver runs each reduced-precision plan's FP32 polish in the same launch; the
+    // graph batch runs it as a second phase.
+    std::vector<char> fused(count, 0);
+    for (int i = 0; i < count; ++i)
+        fused[i] = team && ps[i]->opt.precision != IMRT_FP32 && ps[i]->opt.polish_iter > 0;
+    if (team) TRY(run_team_phase(ps, prec, iters, xinit, x0, delta, s, res, &fused));
+    else TRY(run_batch_phase(ps, prec, iters, xinit, x0, delta, s, res));
     // FP32 polish of the reduced-precision plans that ended without an error
     std::vector<imrt_plan*> pp;
     std::vector<int> pidx, pprec, piters, pxinit;
@@ -2098,7 +2172,20 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         res[i].kkt = d.kkt;
         res[i].rel_change = d.rel;
         if (p->opt.precision != IMRT_FP32 && p->opt.polish_iter > 0 &&
-            (d.status == IMRT_OK || d.status == IMRT_ELINESEARCH)) {  // as in plan_solve
+            (d.status == IMRT_OK || d.status == IMRT_ELINESEARCH) && fused[i]) {  // ran in the same launch
+            const DevState& d2 = *p->st2_host;
+            imrt_result& r = res[i];
+            r.polish_iterations = d2.iter;
+            r.status = d2.status;
+            r.stop_reason = d2.stop;
+            r.objective = d2.G;
+            r.kkt = d2.kkt;
+            r.rel_change = d2.rel;
+            r.passes += d2.passes;
+            r.grad_passes += d2.grad_passes;
+            add_bytes(p, IMRT_FP32, d2.passes, d2.grad_passes, &r);
+        } else if (p->opt.precision != IMRT_FP32 && p->opt.polish_iter > 0 &&
+                   (d.status == IMRT_OK || d.status == IMRT_ELINESEARCH)) {  // as in plan_solve
             CK(cudaMemcpyAsync(p->g_stage, p->v.x + (size_t)d.cur * p->n_pad, sizeof(float) * p->n_pad,
                                cudaMemcpyDeviceToDevice, s));
             pp.push_back(p);
@@ -2118,7 +2205,7 @@ imrt_status plan_solve_batch(imrt_plan* const* plans, int32_t count, const float
         }
         std::vector<imrt_result> pres(pp.size());
         memset(pres.data(), 0, sizeof(imrt_result) * pp.size());
-        const imrt_status st = phase(pp, pprec, piters, pxinit, px0, pdelta, s, pres);
+        const imrt_status st = run_batch_phase(pp, pprec, piters, pxinit, px0, pdelta, s, pres);
         for (size_t k = 0; k < pp.size(); ++k) pp[k]->opt.trace = saved[k];
         TRY(st);
         for (size_t k = 0; k < pp.size(); ++k) {

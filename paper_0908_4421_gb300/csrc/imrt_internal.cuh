@@ -266,14 +266,19 @@ struct TeamPlan {
     const uint16_t* lo;
     const void* tval;
     Vecs v;
-    double* obj;              // 2 * kMaxTrials * n_slices: objective partial of each slice and step size,
-                              // in two buffers that alternate between forward passes
+    double* obj;              // 2 * kMaxTrials * n_busy objective partials of the busy slices by unit
+                              // and step size, in two buffers that alternate between forward passes,
+                              // then n_idle partials of the slices without entries
     DevState* st;
     const SolveParams* sp;
     unsigned int* sync;       // [4]: barrier arrivals, stop request; zeroed before every launch
     int32_t m, n, n_pad, m_pad, n_slices, n_busy, n_idle, H;
     int32_t team0, team_size; // the team's first CTA and its size
-    int32_t pad[2];
+    // The plan's FP32 polish in the same launch (a reduced-precision phase only), or NULL: after
+    // this phase ends with status 0 or IMRT_ELINESEARCH the team continues from its x for
+    // max(min(polish_iter, max_iter), max_iter - iterations of this phase) iterations.
+    int32_t polish_iter, max_iter;
+    const TeamPlan* polish;
 };
 
 struct TeamArgs {

@@ -623,9 +623,12 @@ struct TeamShared {
     TeamCtl c;
 };
 
-// Solves plan P (staged in sh.P) completely with this CTA as member `rank` of the plan's team.
+// Solves plan P (staged in sh.P) completely with this CTA as member `rank` of the plan's team;
+// `x_keep`: start from the x left in shared memory by the phase before (the FP32 polish), and
+// max_iter >= 0 replaces the parameters' iteration budget. Returns the status and iterations,
+// the same in every thread of the team.
 template <class F, int KT>
-__device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
+__device__ __noinline__ int2 team_solve(int rank, float* smem, TeamShared& sh, bool x_keep, int max_iter) {
     const TeamPlan& P = sh.P;
     constexpr int BW = kTeamThreads;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
@@ -649,12 +652,16 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
 
     // Initialization (x_1) and the initial evaluation
     __shared__ int bad_x;
-    if (tid == 0) bad_x = 0;
+    if (tid == 0) {
+        bad_x = 0;
+        if (max_iter >= 0) sh.sp.max_iter = max_iter;
+    }
     __syncthreads();
     for (int i = tid; i < n_pad; i += BW) {
         float x = 0.0f;
         if (i < n) {
-            if (sp.x_init == 0) x = (float)sp.x1_scale;
+            if (x_keep) x = xa[i];  // the same thread wrote it at the end of the phase before
+            else if (sp.x_init == 0) x = (float)sp.x1_scale;
             else if (sp.x_init == 2) {
                 x = sp.x0[i];
                 if (!(x >= 0.0f) || !isfinite(x)) bad_x = 1;
@@ -910,6 +917,7 @@ __device__ __noinline__ void team_solve(int rank, float* smem, TeamShared& sh) {
         }
     }
     __syncthreads();
+    return make_int2(status, iter);
 }
 
 template <class F>
@@ -923,11 +931,26 @@ __global__ void __launch_bounds__(kTeamThreads, 1) k_team_solve(const TeamArgs a
         __syncthreads();
         const int rank = (int)blockIdx.x - sh.P.team0;
         const int kt = sh.P.sp->k_trials;
+        int2 r;
         switch (kt) {
-            case 1: team_solve<F, 1>(rank, tsmem, sh); break;
-            case 2: team_solve<F, 2>(rank, tsmem, sh); break;
-            case 4: team_solve<F, 4>(rank, tsmem, sh); break;
-            default: team_solve<F, 8>(rank, tsmem, sh); break;
+            case 1: r = team_solve<F, 1>(rank, tsmem, sh, false, -1); break;
+            case 2: r = team_solve<F, 2>(rank, tsmem, sh, false, -1); break;
+            case 4: r = team_solve<F, 4>(rank, tsmem, sh, false, -1); break;
+            default: r = team_solve<F, 8>(rank, tsmem, sh, false, -1); break;
+        }
+        const TeamPlan* pol = sh.P.polish;
+        const int budget = max(min(sh.P.polish_iter, sh.P.max_iter), sh.P.max_iter - r.y);
+        __syncthreads();
+        if (pol && (r.x == IMRT_OK || r.x == IMRT_ELINESEARCH)) {
+            // the FP32 polish: the same team goes on from the x every CTA holds in shared memory
+            cta_copy_in(&sh.P, pol);
+            __syncthreads();
+            switch (kt) {
+                case 1: team_solve<FmtF32C16, 1>(rank, tsmem, sh, true, budget); break;
+                case 2: team_solve<FmtF32C16, 2>(rank, tsmem, sh, true, budget); break;
+                case 4: team_solve<FmtF32C16, 4>(rank, tsmem, sh, true, budget); break;
+                default: team_solve<FmtF32C16, 8>(rank, tsmem, sh, true, budget); break;
+            }
         }
         __syncthreads();
     }

@@ -226,6 +226,30 @@ def test_team_reduced_precision_with_polish(orc, tiny, prec, obj_tol, switch):
     assert abs(G_final - ref.objective) <= obj_tol * ref.objective, (G_final, ref.objective)
 
 
+@pytest.mark.parametrize("prec,switch", [(L.FP16, 0.0), (L.FP8E4M3, 1e-3)])
+def test_team_fused_polish_equals_two_solves(tiny, prec, switch):
+    """The FP32 polish runs in the reduced-precision phase's launch, on the same team, from the x
+    the team holds: bitwise the result of a reduced solve without polish followed by an FP32
+    team solve from its x, with the polish's iteration budget and the plan's delta."""
+    case, lam0 = tiny
+    mi, pit, delta = 200, 20, 1e-6
+    with Plan.from_case(case, Options(lambda0=lam0, precision=prec, max_iter=mi, polish_iter=pit,
+                                      polish_switch=switch, delta=delta, solver=TEAM)) as plan:
+        fused = plan.solve(raise_on_error=False)
+        x_fused = plan.get_x()
+        plan.set_options(polish_iter=0, max_iter=mi - pit, delta=max(delta, switch))
+        first = plan.solve(raise_on_error=False)
+        x1 = plan.get_x()
+        budget = max(min(pit, mi), mi - first.iterations)
+        plan.set_options(precision=L.FP32, max_iter=budget, delta=delta, x_init=2)
+        second = plan.solve(x0=x1, raise_on_error=False)
+        x2 = plan.get_x()
+    assert fused.polish_iterations > 0
+    assert (fused.iterations, fused.polish_iterations) == (first.iterations, second.iterations)
+    assert fused.objective == second.objective and fused.status == second.status
+    assert np.array_equal(x_fused, x2)
+
+
 def test_team_voxel_targets(orc, tiny):
     case, lam0 = tiny
     dose = orc.dose(case, orc.initial_point(case)) * 0.9
