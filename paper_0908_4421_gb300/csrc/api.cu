@@ -1507,11 +1507,12 @@ struct TeamCost {
     double fwd = 0.0, bwd = 0.0;  // passes
     double slices = 1.0, rows = 1.0;
     double slice_ns = 0.0, row_ns = 0.0;  // one warp's time per slice / per row
+    double row_multi_ns = 0.0;  // added per row in a team of several CTAs (r gathers bypass L1)
     double glue_ns = 0.0, glue_sum_ns = 0.0, sync_ns = 0.0;  // per forward pass
     double at(int T) const {
         const double w = (double)(kTeamThreads / 32) * T;
         return fwd * (std::ceil(slices / w) * slice_ns + glue_ns + glue_sum_ns / T + (T > 1 ? sync_ns : 0.0)) +
-               bwd * std::ceil(rows / w) * row_ns;
+               bwd * std::ceil(rows / w) * (row_ns + (T > 1 ? row_multi_ns : 0.0));
     }
 };
 
@@ -1524,11 +1525,11 @@ struct PlanCost {
 
 #ifndef IMRT_TEAM_FIT
 // warp ns per slice: a + b (k - 1) + L (c + d (k - 1)) for L groups a slice and k step sizes;
-// per row: e R for R rounds of 256 entries; per forward pass: f + g n / 1000 + h (busy slices)
-// k / 1000 / T, and i for a team of several CTAs
-#define IMRT_TEAM_FIT 670.0, 197.0, 407.0, 48.0, 957.0, 5680.0, 7290.0, 3980.0, 3210.0
+// per row: e + f R for R rounds of 256 entries, plus j R in a team of several CTAs; per forward
+// pass: g + h n / 1000 + i (busy slices) k / 1000 / T, and l for a team of several CTAs
+#define IMRT_TEAM_FIT 707.0, 215.0, 399.0, 36.0, 577.0, 663.0, 236.0, 5680.0, 7290.0, 3980.0, 3210.0
 #endif
-constexpr double kTeamFit[9] = {IMRT_TEAM_FIT};
+constexpr double kTeamFit[11] = {IMRT_TEAM_FIT};
 
 TeamCost team_cost(const imrt_plan* p, const imrt_plan::TeamSlices& ts, int kind, int max_iter, int kt) {
     TeamCost c;
@@ -1543,10 +1544,11 @@ TeamCost team_cost(const imrt_plan* p, const imrt_plan::TeamSlices& ts, int kind
     // FP32 groups move twice the bytes of 16-bit ones (GE 8 either way)
     const double wide = kind == 1 ? 1.4 : 1.0;
     c.slice_ns = kTeamFit[0] + kTeamFit[1] * (kt - 1) + L * wide * (kTeamFit[2] + kTeamFit[3] * (kt - 1));
-    c.row_ns = kTeamFit[4] * R * wide;
-    c.glue_ns = kTeamFit[5] + kTeamFit[6] * p->n / 1000.0;
-    c.glue_sum_ns = kTeamFit[7] * ts.n_busy * kt / 1000.0;
-    c.sync_ns = kTeamFit[8];
+    c.row_ns = kTeamFit[4] + kTeamFit[5] * R * wide;
+    c.row_multi_ns = kTeamFit[6] * R * wide;
+    c.glue_ns = kTeamFit[7] + kTeamFit[8] * p->n / 1000.0;
+    c.glue_sum_ns = kTeamFit[9] * ts.n_busy * kt / 1000.0;
+    c.sync_ns = kTeamFit[10];
     return c;
 }
 
