@@ -331,6 +331,9 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
     float lam[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) lam[q] = lamp[q];
+    unsigned long long nl2[(KT + 1) / 2];  // (-lambda_q, -lambda_q+1) pairs
+#pragma unroll
+    for (int q = 0; q + 1 < KT; q += 2) nl2[q / 2] = f2pack(-lam[q], -lam[q + 1]);
     // The slice partials of NB consecutive slices (8 values) share one butterfly; each value's
     // sum is warp_sum's xor tree, so the partials are those of one butterfly per slice.
     constexpr int NB = 8 / KT;
@@ -405,11 +408,19 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
         }
         if constexpr (KT == 1) {
             fma_group<F, 1>(group_from_chunks<F>(data + cs * NCH * 32 + lane), xs, acc);
-        } else {  // acc[q] += v * max(0, x s - lambda_q g s), the pair read once per entry
+        } else {  // acc[q] += v * max(0, x s - lambda_q g s), the pair read once per entry; two
+                  // step sizes per packed FMA (the same roundings as fmaf per step size)
             for_group_entries<F>(group_from_chunks<F>(data + cs * NCH * 32 + lane), [&](float v, int c) {
                 const float2 xg = *reinterpret_cast<const float2*>(xs + 2 * c);
+                const unsigned long long x2 = f2pack(xg.x, xg.x), g2 = f2pack(xg.y, xg.y), v2 = f2pack(v, v);
 #pragma unroll
-                for (int q = 0; q < KT; ++q) acc[q] = fmaf(v, fmaxf(0.0f, fmaf(-lam[q], xg.y, xg.x)), acc[q]);
+                for (int q = 0; q < KT; q += 2) {
+                    float t0, t1;
+                    f2unpack(ffma2(nl2[q / 2], g2, x2), t0, t1);
+                    const unsigned long long a =
+                        ffma2(v2, f2pack(fmaxf(0.0f, t0), fmaxf(0.0f, t1)), f2pack(acc[q], acc[q + 1]));
+                    f2unpack(a, acc[q], acc[q + 1]);
+                }
             });
         }
         if (mt.y & 2) {  // the slice is complete: Eq. (1)'s penalties and its objective partials
