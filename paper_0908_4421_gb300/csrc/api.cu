@@ -1507,7 +1507,7 @@ struct TeamCost {
     double fwd = 0.0, bwd = 0.0;  // passes
     double slices = 1.0, rows = 1.0;
     double slice_ns = 0.0, row_ns = 0.0;  // one warp's time per slice / per row
-    double row_multi_ns = 0.0;  // added per row in a team of several CTAs (r gathers bypass L1)
+    double row_multi_ns = 0.0;  // added per row in a team of several CTAs (fewer L1 hits on r)
     double glue_ns = 0.0, glue_sum_ns = 0.0, sync_ns = 0.0;  // per forward pass
     double at(int T) const {
         const double w = (double)(kTeamThreads / 32) * T;
@@ -1527,7 +1527,7 @@ struct PlanCost {
 // warp ns per slice: a + b (k - 1) + L (c + d (k - 1)) for L groups a slice and k step sizes;
 // per row: e + f R for R rounds of 256 entries, plus j R in a team of several CTAs; per forward
 // pass: g + h n / 1000 + i (busy slices) k / 1000 / T, and l for a team of several CTAs
-#define IMRT_TEAM_FIT 707.0, 215.0, 399.0, 36.0, 577.0, 663.0, 236.0, 5680.0, 7290.0, 3980.0, 3210.0
+#define IMRT_TEAM_FIT 699.0, 194.0, 400.0, 34.0, 219.0, 778.0, 87.0, 6850.0, 5740.0, 3530.0, 4330.0
 #endif
 constexpr double kTeamFit[11] = {IMRT_TEAM_FIT};
 

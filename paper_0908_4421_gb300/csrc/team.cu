@@ -489,20 +489,15 @@ __device__ __forceinline__ void group_values(const unsigned char* vals, int lane
     }
 }
 
-// r at the 8 voxels of one group (offsets lw within segment base rb): through L2 for a team of
-// several CTAs (teammates wrote r), through L1 for a one-CTA team.
-template <bool MULTI>
+// r at the 8 voxels of one group (offsets lw within segment base rb), through L1. Teammates wrote
+// r before the team barrier, whose GPU-scope acquire (ld.acquire.gpu, then a fence and
+// __syncthreads) orders these plain loads after their writes, so no stale L1 line is read.
 __device__ __forceinline__ void gather_r(const float* __restrict__ rb, uint4 lw, float (&q)[8]) {
     const uint32_t l4[4] = {lw.x, lw.y, lw.z, lw.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        if constexpr (MULTI) {
-            q[2 * t] = __ldcg(rb + (l4[t] & 0xffffu));
-            q[2 * t + 1] = __ldcg(rb + (l4[t] >> 16));
-        } else {
-            q[2 * t] = rb[l4[t] & 0xffffu];
-            q[2 * t + 1] = rb[l4[t] >> 16];
-        }
+        q[2 * t] = rb[l4[t] & 0xffffu];
+        q[2 * t + 1] = rb[l4[t] >> 16];
     }
 }
 
@@ -512,7 +507,7 @@ __device__ __forceinline__ void gather_r(const float* __restrict__ rb, uint4 lw,
 // lane has 8 kBwdRounds loads in flight. The row's records are fetched ahead: the next row's
 // index two rows ahead and its segment table one row ahead (lanes 0..H hold one entry each).
 // Lane l accumulates its groups of the row in round order, then a shuffle tree.
-template <int PREC, bool MULTI>
+template <int PREC>
 __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float* __restrict__ r, int gw, int W,
                                                   unsigned char* ring, int64_t* sb) {
     constexpr int NS = bwd_stages<PREC>(), VB = bwd_val_bytes<PREC>(), R = kBwdRounds;
@@ -595,7 +590,7 @@ __device__ __noinline__ void team_transposed_ring(const TeamPlan& P, const float
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             h[t] = hh[(cs * R + t) * 32 + lane];
-            if (h[t] >= 0) gather_r<MULTI>(r + ((size_t)h[t] << 16), los[(cs * R + t) * 32 + lane], q[t]);
+            if (h[t] >= 0) gather_r(r + ((size_t)h[t] << 16), los[(cs * R + t) * 32 + lane], q[t]);
         }
         if (mt.y & 1) acc = 0.0f;
         produce((cs + NS - 1) % NS);  // refills stage cs - 1; stage cs is read below
@@ -707,10 +702,7 @@ __device__ __noinline__ int2 team_solve(int rank, float* smem, TeamShared& sh, b
     else if (status == 0 && G == 0.0) stop = IMRT_STOP_EXACT;
 
     auto gradient = [&]() -> bool {  // g = D^T r at the accepted x, into gs
-        if (TS > 1)
-            team_transposed_ring<bwd_prec<F>(), true>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
-        else
-            team_transposed_ring<bwd_prec<F>(), false>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
+        team_transposed_ring<bwd_prec<F>()>(P, P.v.r + (size_t)cur * P.m_pad, gw, W, ring, sh.sb[wib]);
         const bool ok = team_barrier(P, ++bar);
         float gm = 0.0f;
         for (int i = tid; i < n_pad; i += BW) {
