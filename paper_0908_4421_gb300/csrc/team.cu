@@ -124,12 +124,14 @@ __device__ __forceinline__ void sum_idle(const TeamPlan& P, double* out) {
     cta_sum<1>(v, out);
 }
 
-// The penalty epilogue of one slice (Eq. (1)): z and r of its 32 voxels for the evaluated step
-// sizes and the slice's objective partials (fixed shuffle order) into rows [0, rows) of obj.
+// The penalty epilogue of one slice (Eq. (1)): r of its 32 voxels for the evaluated step sizes
+// and the slice's objective partials (fixed shuffle order) at `slot` of obj. The doses
+// themselves are not stored: nothing in a solve reads them (plan_dose computes a dose on
+// request).
 template <int KT>
 __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T, int s, int lane,
-                                               const float (&acc)[KT], float* const (&zq)[KT],
-                                               float* const (&rq)[KT], int nq, double* objb, int slot) {
+                                               const float (&acc)[KT], float* const (&rq)[KT], int nq, double* objb,
+                                               int slot) {
     const int p = s * kSlice + lane;
     Df Fq[KT];
 #pragma unroll
@@ -144,7 +146,6 @@ __device__ __forceinline__ void slice_epilogue(const TeamPlan& P, const Terms& T
             if (q >= nq) continue;
             float rj;
             penalty_df(acc[q], bits, T, Fq[q], rj, tj, tg);
-            zq[q][p] = acc[q];
             rq[q][ro] = rj;
         }
     }
@@ -167,14 +168,9 @@ template <class F, int KT>
 __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, const float* xs, int cur, bool eval, int gw,
                              int W, double* objb) {
     const int lane = threadIdx.x & 31;
-    float* zq[KT];
     float* rq[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        const int set = eval ? cur : (cur + 1 + q) % kSets;
-        zq[q] = P.v.z + (size_t)set * P.m_pad;
-        rq[q] = P.v.r + (size_t)set * P.m_pad;
-    }
+    for (int q = 0; q < KT; ++q) rq[q] = P.v.r + (size_t)(eval ? cur : (cur + 1 + q) % kSets) * P.m_pad;
     for (int u = gw; u < P.n_busy; u += W) {
         const int s = __ldg(P.busy + u);
         float acc[KT];
@@ -182,7 +178,7 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
         for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
         slice_row_dot<F, KT, kTeamStage>(P.val, P.col, __ldg(P.slice_off + s), 0, __ldg(P.slice_len + s), lane, xs,
                                          acc);
-        slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, eval ? 1 : KT, objb, u);
+        slice_epilogue<KT>(P, T, s, lane, acc, rq, eval ? 1 : KT, objb, u);
     }
     if (eval) {
         for (int u = gw; u < P.n_idle; u += W) {
@@ -190,7 +186,7 @@ __device__ __noinline__ void team_forward(const TeamPlan& P, const Terms& T, con
             float acc[KT];
 #pragma unroll
             for (int q = 0; q < KT; ++q) acc[q] = 0.0f;
-            slice_epilogue<KT>(P, T, s, lane, acc, zq, rq, 1, P.obj + (size_t)2 * kMaxTrials * P.n_busy, u);
+            slice_epilogue<KT>(P, T, s, lane, acc, rq, 1, P.obj + (size_t)2 * kMaxTrials * P.n_busy, u);
         }
     }
 }
@@ -320,14 +316,9 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
     uint8_t* e_mask = reinterpret_cast<uint8_t*>(e_vt + NS * 32);       // [NS][32]
     uint8_t* e_vtm = e_mask + NS * 32;                                   // [NS][32]
     int2* meta = reinterpret_cast<int2*>(e_vtm + NS * 32);              // [NS]: slice, 1 first | 2 last | unit << 2
-    float* zq[KT];
     float* rq[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        const int set = (cur + 1 + q) % kSets;
-        zq[q] = P.v.z + (size_t)set * P.m_pad;
-        rq[q] = P.v.r + (size_t)set * P.m_pad;
-    }
+    for (int q = 0; q < KT; ++q) rq[q] = P.v.r + (size_t)((cur + 1 + q) % kSets) * P.m_pad;
     float lam[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) lam[q] = lamp[q];
@@ -436,10 +427,7 @@ __device__ __noinline__ void team_forward_ring(const TeamPlan& P, const Terms& T
                 float rj[KT];
                 penalty_multi<KT>(acc, bits, T, Fq, rj, tj, tg);
 #pragma unroll
-                for (int q = 0; q < KT; ++q) {
-                    zq[q][p] = acc[q];
-                    rq[q][ro] = rj[q];
-                }
+                for (int q = 0; q < KT; ++q) rq[q][ro] = rj[q];
             }
 #pragma unroll
             for (int t = 0; t < NB; ++t)
