@@ -450,8 +450,12 @@ def main():
                 ev1.synchronize()
                 ts.append(ev0.elapsed_time(ev1) / 1e3)
             x_ = fp.get_x()
-            fp.set_options(mode=L.MODE_HOST, profile=1)
-            rp = fp.solve()
+            # per-pass bandwidth of the reduced-precision kernels: a host-driven solve without the
+            # FP32 polish, so the timed launches are all passes over the reduced copy whose bytes
+            # the division uses (the polish's FP32 passes would otherwise enter the average)
+            # (a reduced phase may end on its line-search cap near the optimum: still timed)
+            fp.set_options(mode=L.MODE_HOST, profile=1, polish_iter=0, polish_switch=0.0)
+            rp = fp.solve(raise_on_error=False)
             fi = fp.info()
             fp.close()
             f_s = rp.fwd_ms / max(rp.fwd_launches, 1) / 1e3
