@@ -96,6 +96,8 @@ struct FwdShape {
     size_t smem = 0;
     size_t smem1 = 0;
     FwdUnits units{};
+    int64_t* pf_tab = nullptr;  // warp streaming: the L2 prefetch targets (FwdArgs::nx_tab), or none
+    int pf_per_cta = 0;
 };
 
 struct SolveGraph {
@@ -556,7 +558,18 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
     TRY(upload(rec_slice, &U.unit_slice));
     TRY(upload(cta_unit, &U.cta_unit));
     TRY(upload(cta_slots, &U.cta_slots));
-    {
+    if (local) {
+        // CTA b's records at b * max_units (zero padding after them): a CTA's copy does not
+        // wait for its offset to be read
+        std::vector<UnitRec> padded((size_t)grid * std::max(U.max_units, 1), UnitRec{});
+        for (int b = 0; b < grid; ++b)
+            for (int k = cta_unit[b]; k < cta_unit[b + 1]; ++k) padded[(size_t)b * U.max_units + (k - cta_unit[b])] = recs[k];
+        void* d = nullptr;
+        TRY(dalloc_bytes(p, &d, sizeof(UnitRec) * padded.size()));
+        CK(cudaMemcpyAsync(d, padded.data(), sizeof(UnitRec) * padded.size(), cudaMemcpyHostToDevice, stream_of(p)));
+        U.unit = static_cast<const UnitRec*>(d);
+        CK(cudaStreamSynchronize(stream_of(p)));  // `padded` goes out of scope
+    } else {
         void* d = nullptr;
         TRY(dalloc_bytes(p, &d, sizeof(UnitRec) * std::max(n_units, 1)));
         if (n_units)
@@ -582,6 +595,18 @@ imrt_status make_shape(imrt_plan* p, const SellCopy& c, int k_trials, int varian
     TRY(dalloc(p, &U.next_unit, 1));
     CK(cudaMemsetAsync(U.ticket, 0, sizeof(int32_t), stream_of(p)));
     CK(cudaMemsetAsync(U.next_unit, 0, sizeof(int32_t), stream_of(p)));
+    // the next transposed pass's L2 prefetch pays only when its copy of D is far larger than L2
+    // could hold anyway (small plans stay L2-resident, and the prefetch would delay the ticket):
+    // warp w of CTA b hints the row that transposed CTA per_cta * b + w most likely takes first
+    const int64_t tq_bytes = p->tq_entries * ((int64_t)elem_bytes(c.precision) + 2);
+    if (variant != 1 && IMRT_BWD_PREFETCH_KB > 0 && p->t_H > 0 && p->bwd_order && tq_bytes > kPrefetchMinBytes) {
+        const int per_cta = std::min(kMaxPrefetchPerCta, (p->bwd_grid + grid - 1) / std::max(grid, 1));
+        const int count = per_cta * grid;
+        const int64_t cap = ((int64_t)IMRT_BWD_PREFETCH_KB * 1024 / (int64_t)(elem_bytes(c.precision) + 2)) & ~(int64_t)7;
+        TRY(dalloc(p, &out->pf_tab, (size_t)2 * count));
+        CK(launch_prefetch_table(p->bwd_order, p->t_seg, p->t_H, p->n, count, cap, out->pf_tab, stream_of(p)));
+        out->pf_per_cta = per_cta;
+    }
     CK(cudaStreamSynchronize(stream_of(p)));  // the host vectors above go out of scope
     return IMRT_OK;
 }
@@ -612,18 +637,12 @@ FwdArgs fwd_args(imrt_plan* p, const SellCopy& c, const FwdShape& sh, int mode) 
     a.stages = sh.stages;
     a.mask = p->mask;
     a.r_index = p->perm;
-    // the next transposed pass's L2 prefetch pays only when its copy of D is far larger than L2
-    // could hold anyway (small plans stay L2-resident, and the prefetch would delay the ticket)
-    const int64_t tq_bytes = p->tq_entries * ((int64_t)elem_bytes(c.precision) + 2);
-    if (p->t_H > 0 && p->bwd_order && tq_bytes > kPrefetchMinBytes) {
-        a.nx_order = p->bwd_order;
-        a.nx_seg = p->t_seg;
+    if (sh.pf_tab) {  // the next transposed pass's first rows, hinted into L2 (make_shape)
+        a.nx_tab = sh.pf_tab;
         a.nx_val = c.precision != IMRT_FP32 ? (const void*)p->t_valq : (const void*)p->t_vals;
         a.nx_lo = p->t_lo;
-        a.nx_H = p->t_H;
-        a.nx_n = p->n;
         a.nx_vb = (int32_t)elem_bytes(c.precision);
-        a.nx_per_cta = (p->bwd_grid + sh.grid - 1) / std::max(sh.grid, 1);
+        a.nx_per_cta = sh.pf_per_cta;
     }
     a.scale = c.precision == IMRT_FP32 ? nullptr : p->scale;
     a.vt = p->vt_on ? p->vt_p : nullptr;
@@ -705,8 +724,26 @@ imrt_status run_eval(imrt_plan* p, int mode, const float* x_src, float* z_dst, f
     return IMRT_OK;
 }
 
+// A kernel launch on the plan's stream that may begin while the kernel before it drains
+// (programmatic dependent launch): the kernel must read what its predecessor wrote only after
+// its griddepcontrol.wait.
+imrt_status launch_dependent(imrt_plan* p, const void* fn, int grid, int block, size_t smem, void** args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream_of(p);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelExC(&cfg, fn, args));
+    return IMRT_OK;
+}
+
 imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision = IMRT_FP32,
-                          float* power_v = nullptr, double* power_lam = nullptr) {
+                          float* power_v = nullptr, double* power_lam = nullptr, bool dependent = false) {
     BwdArgs a = bwd_args(p, precision, 0);
     a.m_pad = 0;  // the kernel reads r_sets + cur * m_pad = r
     a.g = g;
@@ -714,8 +751,9 @@ imrt_status run_bwd_fixed(imrt_plan* p, const float* r, float* g, int precision 
     a.pw_lam = power_lam;
     const float* r_sets = r;
     void* args[] = {&a, &r_sets};
-    CK(cudaLaunchKernel(bwd_fixed_kernel(bwd_fmt(p, precision)), dim3(p->bwd_grid), dim3(kBwdThreads), args, 0,
-                        stream_of(p)));
+    const void* fn = bwd_fixed_kernel(bwd_fmt(p, precision));
+    if (dependent) TRY(launch_dependent(p, fn, p->bwd_grid, kBwdThreads, 0, args));
+    else CK(cudaLaunchKernel(fn, dim3(p->bwd_grid), dim3(kBwdThreads), args, 0, stream_of(p)));
     void* pargs[] = {&a};
     if (power_v) CK(cudaLaunchKernel(power_step_kernel(), dim3(1), dim3(kBwdThreads), pargs, 0, stream_of(p)));
     return IMRT_OK;
@@ -784,10 +822,37 @@ imrt_status build_sell(imrt_plan* p, SellCopy* c, int precision, const int64_t* 
 imrt_status ensure_lambda0_rule(imrt_plan* p) {
     if (p->lambda0_rule > 0.0) return IMRT_OK;
     cudaStream_t s = stream_of(p);
+    constexpr int kPowerIters = 50;
     CK(launch_fill(p->x_stage, (float)(1.0 / std::sqrt((double)p->n)), p->n, s));
-    for (int it = 0; it < 50; ++it) {
+    FwdShape* sh = nullptr;
+    TRY(get_shape(p, IMRT_FP32, 1, &sh));
+    if (sh->variant == 1) {  // the bulk-copy forward kernel: a separate update kernel per step
+        for (int it = 0; it < kPowerIters; ++it) {
+            TRY(run_eval(p, kFwdPower, p->x_stage, p->z_stage, p->r_stage, nullptr));
+            TRY(run_bwd_fixed(p, p->r_stage, p->g_stage, IMRT_FP32, p->x_stage, p->dscratch));
+        }
+    } else {
+        // w = D^T C D v; each later forward pass forms v = w / ||w|| itself (and leaves it in
+        // x_stage), and every pass may launch while the one before it drains; after the last
+        // pass the update kernel gives lambda = v . w
         TRY(run_eval(p, kFwdPower, p->x_stage, p->z_stage, p->r_stage, nullptr));
-        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage, IMRT_FP32, p->x_stage, p->dscratch));
+        TRY(run_bwd_fixed(p, p->r_stage, p->g_stage, IMRT_FP32, nullptr, nullptr, true));
+        for (int it = 1; it < kPowerIters; ++it) {
+            FwdArgs a = fwd_args(p, copy_of(p, IMRT_FP32), *sh, kFwdPowerNext);
+            a.x_src = p->g_stage;
+            a.v_dst = p->x_stage;
+            a.z_dst = p->z_stage;
+            a.r_dst = p->r_stage;
+            void* args[] = {&a};
+            TRY(launch_dependent(p, sh->fn1, sh->grid, sh->block, sh->smem1, args));
+            TRY(run_bwd_fixed(p, p->r_stage, p->g_stage, IMRT_FP32, nullptr, nullptr, true));
+        }
+        BwdArgs b = bwd_args(p, IMRT_FP32, 0);
+        b.g = p->g_stage;
+        b.pw_v = p->x_stage;
+        b.pw_lam = p->dscratch;
+        void* pargs[] = {&b};
+        CK(cudaLaunchKernel(power_step_kernel(), dim3(1), dim3(kBwdThreads), pargs, 0, s));
     }
     double lam = 0.0;
     CK(cudaMemcpyAsync(&lam, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));

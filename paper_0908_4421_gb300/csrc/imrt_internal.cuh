@@ -42,6 +42,10 @@ constexpr int kBwdPerSm = 2048 / kBwdThreads;   // resident transposed CTAs per 
 // entries of a warp's groups are sg consecutive voxels of the row.
 constexpr int kTqBlock = 256;
 constexpr int64_t kPrefetchMinBytes = 64ll << 20;  // beamlet-major copies above this get the L2 prefetch
+constexpr int kMaxPrefetchPerCta = 8;  // forward CTA's L2 prefetch targets (transposed CTAs per forward CTA)
+#ifndef IMRT_BWD_PREFETCH_KB
+#define IMRT_BWD_PREFETCH_KB 64  // forward tail: L2 prefetch (KB per row) of the next transposed pass's first rows
+#endif
 // Beamlet-major build: voxel rows per counting-sort chunk (doubled while the chunk x beamlet
 // count table would exceed kTCountBytes).
 constexpr int kTChunkRows = 512;
@@ -57,6 +61,7 @@ enum FwdMode : int32_t {
     kFwdEval = 0,   // z, r, G at a given x (no step)
     kFwdTrial = 1,  // x_t = max(0, x - lambda_q g) for k_trials step sizes, then z, r, G
     kFwdPower = 2,  // z = D v and u = Cdiag z (power iteration of the step-size rule)
+    kFwdPowerNext = 3,  // the same at v = w / ||w|| for w = x_src, the last transposed pass's output
 };
 
 // Per-structure penalty terms (Eq. (1) with per-structure thresholds, c = w / |V_s|).
@@ -198,16 +203,18 @@ struct FwdArgs {
     int32_t control;     // 1: the last CTA runs the Armijo controller (inside a solve)
     int32_t stages;      // bulk-copy kernel: ring stages per consumer warp
     const volatile int32_t* cancel;  // mapped host flag: nonzero asks the solve to stop
-    const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x
+    const float* x_src;  // kFwdEval / kFwdPower: x (n_pad); NULL => accepted x; kFwdPowerNext: w
+    float* v_dst;        // kFwdPowerNext: CTA 0 stores v = w / ||w|| here (n_pad)
     float* z_dst;        // kFwdEval / kFwdPower; NULL => accepted set
     float* r_dst;
     // the transposed pass that follows (segmented copies), for an L2 prefetch of its first rows
-    // at the end of this pass; nx_order NULL: none
-    const int32_t* nx_order;
-    const int64_t* nx_seg;
+    // at the end of this pass; nx_tab NULL: none. nx_tab holds nx_per_cta (first entry, entries)
+    // pairs per CTA (entries 0: nothing), one per warp w < nx_per_cta: the row that CTA
+    // nx_per_cta * b + w of the transposed pass most likely takes first
+    const int64_t* nx_tab;
     const void* nx_val;
     const uint16_t* nx_lo;
-    int32_t nx_H, nx_n, nx_vb, nx_per_cta;
+    int32_t nx_vb, nx_per_cta;
 };
 
 struct BwdArgs {
@@ -359,5 +366,9 @@ cudaError_t launch_col_absmax(const int64_t* row_ptr, const int32_t* col, const 
 cudaError_t launch_scales(const uint32_t* absmax_bits, int32_t n, int32_t n_pad, float qmax, float* scale,
                           float* inv_scale, cudaStream_t stream);
 cudaError_t launch_g_objective(const double* gpart, int32_t count, double* out, cudaStream_t stream);
+// The forward pass's L2 prefetch targets (FwdArgs::nx_tab): for t < count, the first entry of row
+// order[t] of the segmented beamlet-major copy and min(its entries, cap); (0, 0) for t >= n.
+cudaError_t launch_prefetch_table(const int32_t* order, const int64_t* seg, int32_t H, int32_t n, int32_t count,
+                                  int64_t cap, int64_t* tab, cudaStream_t stream);
 
 }  // namespace imrt

@@ -330,7 +330,7 @@ __device__ __forceinline__ void unit_epilogue(const FwdArgs& a, const Terms& T, 
         const float tj = a.vt ? a.vt[p] : 0.0f;
         const uint32_t tg = a.vt ? a.vtm[p] : 0u;
         const int ro = a.r_index[p];
-        if (mode == kFwdPower) {
+        if (mode == kFwdPower || mode == kFwdPowerNext) {
             zq[0][p] = acc[0];
             rq[0][ro] = cdiag(bits, T, tg) * acc[0];
         } else {
@@ -369,6 +369,96 @@ __device__ __forceinline__ UnitRec load_unit(const UnitRec* r, bool shared) {
     return R;
 }
 
+// A warp that is done with D hints the start of one first-wave row of the transposed pass that
+// follows into L2 (D is constant), while the other CTAs finish: the warp's target from the
+// CTA's prefetch table, staged in shared memory with the unit records.
+__device__ __forceinline__ void prefetch_next_rows(const FwdArgs& a, const int64_t* s_pf, int wib, int lane) {
+#if IMRT_BWD_PREFETCH_KB > 0
+    if (a.nx_tab && lane == 0 && wib < a.nx_per_cta) {
+        const int64_t e0 = s_pf[2 * wib], n_e = s_pf[2 * wib + 1];
+        if (n_e > 0) {
+            prefetch_l2(static_cast<const char*>(a.nx_val) + e0 * a.nx_vb, n_e * a.nx_vb);
+            prefetch_l2(a.nx_lo + e0, n_e * 2);
+        }
+    }
+#endif
+}
+
+// The trial-point inputs of one thread: x, g and the beamlet scales of the float4 groups
+// tid + k * kFwdThreads, k < R, loaded together; store() forms the trial points
+// x_t = max(0, x - lambda_q g) * scale, trial-interleaved, exactly as Sec. 2.2 step 2 projects.
+template <class F>
+struct TrialIn {
+    static constexpr int R = 2;
+    float4 x[R], g[R], s[R];
+    int base = 0, n4 = 0;
+    __device__ __forceinline__ void load(const float* xg, const float* g_, const float* sc, int n4_, int tid) {
+        base = tid;
+        n4 = n4_;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int i4 = tid + k * kFwdThreads;
+            if (i4 < n4) {
+                x[k] = __ldcg(reinterpret_cast<const float4*>(xg) + i4);
+                g[k] = __ldcg(reinterpret_cast<const float4*>(g_) + i4);
+                s[k] = sc ? __ldg(reinterpret_cast<const float4*>(sc) + i4) : make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+            }
+        }
+    }
+    __device__ __forceinline__ void load_one(const float* xg, const float* g_, const float* sc, int i4) {
+        x[0] = __ldcg(reinterpret_cast<const float4*>(xg) + i4);
+        g[0] = __ldcg(reinterpret_cast<const float4*>(g_) + i4);
+        s[0] = sc ? __ldg(reinterpret_cast<const float4*>(sc) + i4) : make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+    }
+    template <int KT>
+    __device__ __forceinline__ void put(float* xs, const float (&lamf)[KT], int k, int i4) const {
+        const float xv[4] = {x[k].x, x[k].y, x[k].z, x[k].w}, gv[4] = {g[k].x, g[k].y, g[k].z, g[k].w},
+                    sv[4] = {s[k].x, s[k].y, s[k].z, s[k].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+                xs[(size_t)(4 * i4 + e) * KT + q] = fmaxf(0.0f, fmaf(-lamf[q], gv[e], xv[e])) * sv[e];
+    }
+    template <int KT>
+    __device__ __forceinline__ void store(float* xs, const float (&lamf)[KT]) const {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (base + k * kFwdThreads < n4) put<KT>(xs, lamf, k, base + k * kFwdThreads);
+    }
+    template <int KT>
+    __device__ __forceinline__ void store_one(float* xs, const float (&lamf)[KT], int i4) const {
+        put<KT>(xs, lamf, 0, i4);
+    }
+};
+
+// The power iteration's next vector inside the forward pass that uses it: v = w / ||w||
+// (w = 0: v = 0) into shared memory, and by one CTA to v_out. Every CTA adds ||w||^2 in the
+// same fixed order (FP64: per thread, the xor tree of each warp, then the warps in order), so
+// all CTAs hold the same v and no separate update kernel runs between the passes.
+__device__ __forceinline__ void power_next_x(const float* __restrict__ w, int n, int n_pad, float* xs,
+                                             float* __restrict__ v_out) {
+    __shared__ double part[kFwdThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    double ww = 0.0;
+    for (int i = tid; i < n_pad; i += kFwdThreads) {
+        const float v = i < n ? __ldcg(w + i) : 0.0f;
+        xs[i] = v;
+        ww += (double)v * (double)v;
+    }
+    ww = warp_sum(ww);
+    if (lane == 0) part[wib] = ww;
+    __syncthreads();
+    double tot = 0.0;
+    for (int k = 0; k < kFwdThreads / 32; ++k) tot += part[k];
+    const float inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.0f;
+    for (int i = tid; i < n_pad; i += kFwdThreads) {  // the entries this thread stored above
+        const float v = xs[i] * inv;
+        xs[i] = v;
+        if (v_out) v_out[i] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward pass (fused step + dose + penalty + objective partials).
 // ---------------------------------------------------------------------------
@@ -377,16 +467,15 @@ __global__ void __launch_bounds__(kFwdThreads,
                                   KT <= 2 ? ((F::KIND == 2 || F::KIND == 3) ? IMRT_FWD_MINB_Q : IMRT_FWD_MINB1) : 1)
     k_forward(const FwdArgs a) {
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar, bar_g, bar_r;
+    __shared__ __align__(8) uint64_t bar, bar_r;
+    __shared__ __align__(16) int64_t s_pf[2 * kMaxPrefetchPerCta];  // this CTA's L2 prefetch targets
     __shared__ Terms T;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int n_pad = a.n_pad;
     DevState* st = a.st;
     const int mode = a.mode;
 
-    float* xs = smem;                  // n_pad * KT, trial-interleaved
-    float* gs = smem + (size_t)n_pad * KT;  // g (trial mode)
-    float* xr = gs + n_pad;            // raw x (trial mode, KT > 1)
+    float* xs = smem;                  // n_pad * KT, trial-interleaved (then room the layout keeps)
     const uint32_t bytes = (uint32_t)n_pad * 4u;
 
     const FwdUnits& U = a.u;
@@ -405,22 +494,25 @@ __global__ void __launch_bounds__(kFwdThreads,
     // only what the previous forward pass (complete by then) or the plan wrote; g comes after.
     if (tid == 0) {
         mbar_init(&bar, 1);
-        mbar_init(&bar_g, 1);
         mbar_init(&bar_r, 1);
         fence_mbar_init();
         s_next = 0;
+        // the prefetch targets (constant per plan) travel with the unit records
+        const uint32_t pb = a.nx_tab ? (uint32_t)a.nx_per_cta * 16u : 0u;
         if (U.local) {
-            const int c0 = U.cta_unit[blockIdx.x], c1 = U.cta_unit[blockIdx.x + 1];
-            s_units = c1 - c0;
+            // every CTA's records sit at a stride of max_units records, so the copy starts before
+            // this CTA's count is known
+            const uint32_t rb = (uint32_t)U.max_units * (uint32_t)sizeof(UnitRec);
+            mbar_arrive_expect_tx(&bar_r, rb + pb);
+            if (rb) bulk_g2s(recs, U.unit + (size_t)blockIdx.x * U.max_units, rb, &bar_r);
+            s_units = U.cta_unit[blockIdx.x + 1] - U.cta_unit[blockIdx.x];
             s_slots = U.cta_slots[blockIdx.x];
-            const uint32_t rb = (uint32_t)(c1 - c0) * (uint32_t)sizeof(UnitRec);
-            mbar_arrive_expect_tx(&bar_r, rb);
-            if (rb) bulk_g2s(recs, U.unit + c0, rb, &bar_r);
         } else {
             s_units = 0;
             s_slots = 0;
-            mbar_arrive_expect_tx(&bar_r, 0u);
+            mbar_arrive_expect_tx(&bar_r, pb);
         }
+        if (pb) bulk_g2s(s_pf, a.nx_tab + (size_t)2 * a.nx_per_cta * blockIdx.x, pb, &bar_r);
     }
     if (U.local)
         for (int i = tid; i < U.max_splits; i += kFwdThreads) lt.cnt[i] = 0;
@@ -441,29 +533,34 @@ __global__ void __launch_bounds__(kFwdThreads,
         if (tid == 0) (void)mbar_wait_bounded(&bar_r, 0);
         return;
     }
-    const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)(mode == kFwdTrial ? cur : st->cur) * n_pad;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && mode != kFwdTrial && mode != kFwdPowerNext) {  // x staged by the bulk-copy engine
+        const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)st->cur * n_pad;
         mbar_arrive_expect_tx(&bar, bytes);
-        bulk_g2s(mode == kFwdTrial && KT > 1 ? xr : xs, xsrc, bytes, &bar);
+        bulk_g2s(xs, xsrc, bytes, &bar);
     }
     pdl_wait();  // the transposed pass before this one (g, state) is complete
-    if (tid == 0 && mode == kFwdTrial) {
-        mbar_arrive_expect_tx(&bar_g, bytes);
-        bulk_g2s(gs, a.v.g, bytes, &bar_g);
-    }
     pdl_launch_dependents();
-    // the controller's inputs, staged while the copies are in flight (used only by the last
-    // CTA; the mapped cancel flag's latency is hidden behind the whole pass)
+    // Trial passes: x, g (and the beamlet scales) with plain 16-byte loads, all issued at once
+    // after the wait, so the trial points cost one L2 round trip rather than a bulk copy
+    // issued after the wait and then waited for.
+    TrialIn<F> tin;
+    if (mode == kFwdTrial) tin.load(a.v.x + (size_t)cur * n_pad, a.v.g, a.scale, n_pad >> 2, tid);
+    // the controller's inputs (used only by the last CTA): loaded now, stored to shared memory
+    // once the trial points are formed, so their latency stays off the prologue; the mapped
+    // cancel flag's latency is hidden behind the whole pass
+    static_assert(sizeof(DevState) % 4 == 0 && sizeof(SolveParams) % 4 == 0 &&
+                      sizeof(DevState) / 4 <= kFwdThreads && sizeof(SolveParams) / 4 <= kFwdThreads,
+                  "one word of each per thread");
+    uint32_t cs_s = 0u, cs_p = 0u;
     if (a.control) {
-        cta_copy_in(&cs.S, st);
-        cta_copy_in(&cs.P, a.sp);
+        if (tid < (int)(sizeof(DevState) / 4)) cs_s = __ldcg(reinterpret_cast<const uint32_t*>(st) + tid);
+        if (tid < (int)(sizeof(SolveParams) / 4)) cs_p = __ldcg(reinterpret_cast<const uint32_t*>(a.sp) + tid);
         if (tid == 0 && mode == kFwdTrial && a.cancel) cancel_req = *a.cancel;
     }
     // Bounded waits: on expiry the CTA flags a device error, skips its work, and still
     // reports to the ticket so the controller runs and ends the solve.
-    bool bad = !mbar_wait_bounded(&bar, 0);
-    if (mode == kFwdTrial) bad = !mbar_wait_bounded(&bar_g, 0) || bad;
+    bool bad = mode != kFwdTrial && mode != kFwdPowerNext && !mbar_wait_bounded(&bar, 0);
     bad = !mbar_wait_bounded(&bar_r, 0) || bad;
     const bool failed = __syncthreads_or(bad) != 0;
     if (failed && tid == 0) atomicExch(&st->status, (int)IMRT_ECUDA);
@@ -478,15 +575,21 @@ __global__ void __launch_bounds__(kFwdThreads,
         }
     }
     if (mode == kFwdTrial) {
-        const float* xraw = (KT == 1) ? xs : xr;
-        for (int i = tid; i < n_pad; i += kFwdThreads) {
-            const float xv = xraw[i], gv = gs[i];
-            const float sc = a.scale ? a.scale[i] : 1.0f;
-#pragma unroll
-            for (int q = 0; q < KT; ++q) xs[(size_t)i * KT + q] = fmaxf(0.0f, fmaf(-lamf[q], gv, xv)) * sc;
+        tin.template store<KT>(xs, lamf);
+        // n_pad beyond the first round (more than 4 * kFwdThreads * kTrialRounds beamlets)
+        for (int i4 = tid + kFwdThreads * TrialIn<F>::R; i4 < (n_pad >> 2); i4 += kFwdThreads) {
+            TrialIn<F> t2;
+            t2.load_one(a.v.x + (size_t)cur * n_pad, a.v.g, a.scale, i4);
+            t2.template store_one<KT>(xs, lamf, i4);
         }
+    } else if (mode == kFwdPowerNext) {
+        power_next_x(a.x_src, a.n, n_pad, xs, blockIdx.x == 0 ? a.v_dst : nullptr);
     } else if (a.scale) {
         for (int i = tid; i < n_pad; i += kFwdThreads) xs[i] *= a.scale[i];
+    }
+    if (a.control) {
+        if (tid < (int)(sizeof(DevState) / 4)) reinterpret_cast<uint32_t*>(&cs.S)[tid] = cs_s;
+        if (tid < (int)(sizeof(SolveParams) / 4)) reinterpret_cast<uint32_t*>(&cs.P)[tid] = cs_p;
     }
     __syncthreads();
 
@@ -510,14 +613,12 @@ __global__ void __launch_bounds__(kFwdThreads,
                 d2[q] += e * e;
             }
         }
-        __threadfence();  // x_t is read by the controller's trace copy in this launch
+        // x_t (the controller's trace copy) and the partials are read by the controller in this
+        // launch: the release fence before this CTA's ticket publishes them
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
             const double s = warp_sum(d2[q]);
-            if (lane == 0) {
-                a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = s;
-                __threadfence();
-            }
+            if (lane == 0) a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = s;
         }
     }
 
@@ -561,10 +662,7 @@ __global__ void __launch_bounds__(kFwdThreads,
             Df t{0.0f, 0.0f};
             for (int i = lane; i < s_slots; i += 32) t = df_add(t, reinterpret_cast<const Df*>(lt.slots)[(size_t)i * KT + q]);
             t = warp_sum(t);
-            if (lane == 0) {
-                U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : df_to_double(t);
-                __threadfence();
-            }
+            if (lane == 0) U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : df_to_double(t);
         }
     } else {
         // all units from the device-wide counter
@@ -585,26 +683,19 @@ __global__ void __launch_bounds__(kFwdThreads,
             u = __shfl_sync(0xffffffffu, u_next, 0);
         }
     }
-#if IMRT_BWD_PREFETCH_KB > 0
-    // this warp is done with D: hint the start of one first-wave row of the transposed pass
-    // that follows into L2, while the other warps and CTAs finish (D is constant)
-    if (a.nx_order && lane == 0 && wib < a.nx_per_cta) {
-        const int idx = (int)blockIdx.x * a.nx_per_cta + wib;
-        if (idx < a.nx_n) {
-            const int i = a.nx_order[idx];
-            const int64_t e0 = a.nx_seg[(int64_t)i * a.nx_H], e1 = a.nx_seg[(int64_t)i * a.nx_H + a.nx_H];
-            const int64_t cap = ((int64_t)IMRT_BWD_PREFETCH_KB * 1024 / (a.nx_vb + 2)) & ~(int64_t)7;
-            const int64_t n_e = e1 - e0 < cap ? e1 - e0 : cap;
-            prefetch_l2(static_cast<const char*>(a.nx_val) + e0 * a.nx_vb, n_e * a.nx_vb);
-            prefetch_l2(a.nx_lo + e0, n_e * 2);
-        }
-    }
-#endif
-    // count finished CTAs: the last one resets the schedule and, inside a solve, runs the controller
-    // (every write the controller reads was fenced by its writer)
+    // (CTA-local schedule: once every warp of the CTA is done; issued earlier, per warp, the
+    // prefetch was measured to delay the last CTAs' streaming more than it saved)
+    if (!failed) prefetch_next_rows(a, s_pf, wib, lane);
+    // count finished CTAs: the last one resets the schedule and, inside a solve, runs the
+    // controller. One release fence after the barrier publishes every write of this CTA the
+    // controller reads (objective and step-length partials, x_t); the last CTA's fence after
+    // its ticket is the matching acquire.
     __shared__ int is_last;
     __syncthreads();
-    if (tid == 0) is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
+    if (tid == 0) {
+        fence_acq_rel_gpu();
+        is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
+    }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -1321,6 +1412,28 @@ __global__ void __launch_bounds__(kCtlThreads) k_finish(DevState* st, const Solv
 // ---------------------------------------------------------------------------
 // Function pointers for graph nodes and launches.
 // ---------------------------------------------------------------------------
+__global__ void k_prefetch_table(const int32_t* __restrict__ order, const int64_t* __restrict__ seg, int H, int n,
+                                 int count, int64_t cap, int64_t* __restrict__ tab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    int64_t e0 = 0, n_e = 0;
+    if (t < n) {
+        const int i = order[t];
+        e0 = seg[(int64_t)i * H];
+        const int64_t len = seg[(int64_t)i * H + H] - e0;
+        n_e = len < cap ? len : cap;
+    }
+    tab[2 * t] = e0;
+    tab[2 * t + 1] = n_e;
+}
+
+cudaError_t launch_prefetch_table(const int32_t* order, const int64_t* seg, int32_t H, int32_t n, int32_t count,
+                                  int64_t cap, int64_t* tab, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    k_prefetch_table<<<(count + 255) / 256, 256, 0, stream>>>(order, seg, H, n, count, cap, tab);
+    return cudaGetLastError();
+}
+
 template <class F>
 static const void* fwd_for_kt(int kt) {
     switch (kt) {

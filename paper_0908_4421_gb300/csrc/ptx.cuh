@@ -69,6 +69,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Programmatic dependent launch. `pdl_wait` returns once the grid this launch depends on
 // programmatically has completed and its writes are visible (at once when the launch has no
 // such dependency); `pdl_launch_dependents` lets the next grid start launching.
+// Release/acquire fence at GPU scope. Issued by one thread after a CTA barrier and before that
+// thread's ticket atomic, it makes every write the CTA made before the barrier visible to the
+// thread that later observes the ticket and fences in turn (fences are cumulative); lighter
+// than the sequentially consistent fence of __threadfence().
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 // A hint that brings [p, p + bytes) into L2; there is no completion to wait for. The bulk
 // prefetch needs a 16-byte aligned start and a multiple of 16 bytes, so the start is rounded

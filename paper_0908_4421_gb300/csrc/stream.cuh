@@ -26,9 +26,6 @@ namespace imrt {
 #ifndef IMRT_FWD_UNROLL
 #define IMRT_FWD_UNROLL 8  // groups in flight per lane (FP8: half as many, each is 48 bytes)
 #endif
-#ifndef IMRT_BWD_PREFETCH_KB
-#define IMRT_BWD_PREFETCH_KB 64  // forward tail: L2 prefetch (KB per row) of the next transposed pass's first rows
-#endif
 
 // ---------------------------------------------------------------------------
 // Per-voxel penalty (Eq. (1)): penalty_df below gives F_j and r_j = dF_j / dz_j at dose z.
