@@ -1381,7 +1381,15 @@ imrt_status run_phase(imrt_plan* p, int precision, int max_iter, int x_init, con
         CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const bool prof = p->opt.profile != 0;
+        // profiled: a short device-side delay ahead of the first timed kernel after each host
+        // synchronisation, so that the kernels are already queued when their start events are
+        // recorded and each event interval is the kernel's own (with the stream's launch gap)
+        constexpr unsigned long long kProfileDelayNs = 30000;
         while (!p->st_host->done) {
+            if (prof) {
+                CK(launch_delay(kProfileDelayNs, s));
+                ++launches;
+            }
             if (p->st_host->need_grad) {
                 if (prof) CK(cudaEventRecord(p->ev[2], s));
                 TRY(launch_now(K.bwd, s));

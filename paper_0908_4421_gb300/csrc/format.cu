@@ -22,25 +22,36 @@ inline int blocks_for(int64_t count, int threads) { return (int)((count + thread
 __global__ void k_row_check(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const float* __restrict__ val, int32_t m, int32_t n, int32_t* __restrict__ len,
                             int32_t* __restrict__ flags) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+    // one warp per row: lane l reads entries l, l + 32, ... (coalesced), and each column is
+    // compared with the one before it in the row (the previous lane's, or the last of the
+    // previous round for lane 0)
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= m) return;  // uniform over the warp
     const int64_t a = row_ptr[j], b = row_ptr[j + 1];
     int f = 0;
     if (b < a) {
-        f |= 1;
-        len[j] = 0;
+        f = 1;
+        if (lane == 0) len[j] = 0;
     } else {
-        len[j] = (int32_t)(b - a);
-        int prev = -1;
-        for (int64_t k = a; k < b; ++k) {
-            const int c = col[k];
-            if (c < 0 || c >= n) f |= 2;
-            if (c <= prev) f |= 4;
-            prev = c;
-            if (!isfinite(val[k])) f |= 8;
+        if (lane == 0) len[j] = (int32_t)(b - a);
+        int last = -1;
+        for (int64_t kb = a; kb < b; kb += 32) {
+            const int64_t k = kb + lane;
+            const bool in = k < b;
+            const int c = in ? col[k] : 0x7fffffff;
+            const float v = in ? val[k] : 0.0f;
+            int before = __shfl_up_sync(0xffffffffu, c, 1);
+            if (lane == 0) before = last;
+            if (in) {
+                if (c < 0 || c >= n) f |= 2;
+                if (c <= before) f |= 4;
+                if (!isfinite(v)) f |= 8;
+            }
+            last = __shfl_sync(0xffffffffu, c, 31);
         }
     }
-    if (f) atomicOr(flags, f);
+    f = __reduce_or_sync(0xffffffffu, f);
+    if (lane == 0 && f) atomicOr(flags, f);
 }
 
 // One CTA per window of kSigma rows: sort by (length desc, row asc); bitonic sort in shared memory.
@@ -202,7 +213,15 @@ __global__ void k_t_count(const int64_t* __restrict__ row_ptr, const int32_t* __
     const int j0 = blockIdx.x * chunk_rows, j1 = min(m, j0 + chunk_rows);
     if (j0 < j1) {  // the chunk's rows are consecutive, so their entries are one range
         const int64_t k1 = row_ptr[j1];
-        for (int64_t k = row_ptr[j0] + threadIdx.x; k < k1; k += blockDim.x) atomicAdd(&hist[col[k]], 1);
+        constexpr int kU = 8;  // loads in flight per thread
+        for (int64_t kb = row_ptr[j0] + threadIdx.x; kb < k1; kb += (int64_t)kU * blockDim.x) {
+            int cc[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) cc[u] = kb + (int64_t)u * blockDim.x < k1 ? col[kb + (int64_t)u * blockDim.x] : -1;
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (cc[u] >= 0) atomicAdd(&hist[cc[u]], 1);
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += blockDim.x) counts[(size_t)blockIdx.x * n + c] = hist[c];
@@ -259,14 +278,16 @@ __global__ void k_t_scatter(const int64_t* __restrict__ row_ptr, const int32_t* 
 // beamlet row is the beamlet's cursor plus the number of the block's lower rows holding that
 // beamlet (the mask bits below its own), so each beamlet row still receives its voxels in
 // ascending index, with no ordering between the threads. Step c: each cursor advances by its
-// mask's population and the masks are cleared. A warp takes whole rows (coalesced loads).
+// mask's population and the masks are cleared. A warp takes whole rows (coalesced loads, eight
+// in flight per lane). (Splitting the launch into beamlet ranges whose writes stay in L2 was
+// measured slower: every range re-reads the column indices.)
 constexpr int kTBlockRows = 32;
 __global__ void k_t_scatter_blocks(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                    const float* __restrict__ val, int32_t m, int32_t n, int32_t chunk_rows,
                                    const int32_t* __restrict__ counts, const int64_t* __restrict__ t_off,
                                    float* __restrict__ t_val, int32_t* __restrict__ t_row) {
-    extern __shared__ int32_t cursor[];                          // n: position within the beamlet row
-    uint32_t* mask = reinterpret_cast<uint32_t*>(cursor + n);    // n: rows of the block holding the beamlet
+    extern __shared__ int32_t cursor[];                      // n: position within the beamlet row
+    uint32_t* mask = reinterpret_cast<uint32_t*>(cursor + n);  // n: rows of the block holding the beamlet
     __shared__ int64_t rp[kTBlockRows + 1];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
     for (int c = tid; c < n; c += blockDim.x) {
@@ -278,16 +299,40 @@ __global__ void k_t_scatter_blocks(const int64_t* __restrict__ row_ptr, const in
         const int nb = min(kTBlockRows, j1 - jb);
         if (tid <= nb) rp[tid] = row_ptr[jb + tid];
         __syncthreads();  // rp, and the previous block's cursors and cleared masks
-        for (int r = wib; r < nb; r += nw)
-            for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) atomicOr(&mask[col[k]], 1u << r);
+        // a warp's row in rounds of kU * 32 entries, every load of a round issued before any use
+        constexpr int kU = 8;
+        for (int r = wib; r < nb; r += nw) {
+            const int64_t e = rp[r + 1];
+            for (int64_t kb = rp[r] + lane; kb < e; kb += kU * 32) {
+                int cc[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) cc[u] = kb + u * 32 < e ? col[kb + u * 32] : -1;
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (cc[u] >= 0) atomicOr(&mask[cc[u]], 1u << r);
+            }
+        }
         __syncthreads();
         for (int r = wib; r < nb; r += nw) {
             const uint32_t below = (1u << r) - 1u;
-            for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) {
-                const int c = col[k];
-                const int64_t dst = __ldg(t_off + c) + cursor[c] + __popc(mask[c] & below);
-                t_val[dst] = val[k];
-                t_row[dst] = jb + r;
+            const int64_t e = rp[r + 1];
+            for (int64_t kb = rp[r] + lane; kb < e; kb += kU * 32) {
+                int cc[kU];
+                float vv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int64_t k = kb + u * 32;
+                    cc[u] = k < e ? col[k] : -1;
+                    vv[u] = k < e ? val[k] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int c = cc[u];
+                    if (c < 0) continue;
+                    const int64_t dst = __ldg(t_off + c) + cursor[c] + __popc(mask[c] & below);
+                    t_val[dst] = vv[u];
+                    t_row[dst] = jb + r;
+                }
             }
         }
         __syncthreads();
@@ -485,7 +530,7 @@ cudaError_t set_max_dynamic_smem(K kernel) {
 
 cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
                              int32_t* len, int32_t* flags, cudaStream_t stream) {
-    k_row_check<<<blocks_for(m, 256), 256, 0, stream>>>(row_ptr, col, val, m, n, len, flags);
+    k_row_check<<<blocks_for((int64_t)m * 32, 256), 256, 0, stream>>>(row_ptr, col, val, m, n, len, flags);
     return cudaGetLastError();
 }
 
@@ -628,6 +673,22 @@ cudaError_t launch_permute_in(const float* src, const uint8_t* src_mask, const i
 
 cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* dst, cudaStream_t stream) {
     k_pad_copy<<<blocks_for(n_pad, 256), 256, 0, stream>>>(src, n, n_pad, dst);
+    return cudaGetLastError();
+}
+
+// One thread that returns after `ns` nanoseconds of the device's global timer (a wait on time
+// only, so it always ends).
+__global__ void k_delay(unsigned long long ns) {
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do {
+        __nanosleep(1000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    } while (t - t0 < ns);
+}
+
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t stream) {
+    k_delay<<<1, 1, 0, stream>>>(ns);
     return cudaGetLastError();
 }
 

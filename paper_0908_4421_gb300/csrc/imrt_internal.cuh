@@ -356,6 +356,9 @@ cudaError_t launch_mask_counts(const uint8_t* mask, int32_t m, int32_t* counts, 
 cudaError_t launch_unpermute(const float* zp, const int32_t* perm, int32_t m, float* z, cudaStream_t stream);
 cudaError_t launch_pad_copy(const float* src, int32_t n, int32_t n_pad, float* dst, cudaStream_t stream);
 cudaError_t launch_fill(float* dst, float v, int32_t count, cudaStream_t stream);
+// Keeps the stream busy for `ns` nanoseconds of device time (profiled host-driven solves: the
+// host enqueues the next timed kernel meanwhile, so its event interval holds no host latency).
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t stream);
 constexpr int kSumParts = 256;  // CTAs (and partials) of the masked sum
 cudaError_t launch_sum_masked(const float* z, const uint8_t* mask, int32_t bit, int32_t m, double* out,
                               double* scratch, cudaStream_t stream);
