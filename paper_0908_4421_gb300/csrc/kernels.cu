@@ -84,11 +84,13 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
         gs[q] = (q < nq && tid < W) ? __ldcg(U.obj + (size_t)q * W + tid) : 0.0;
         ds[q] = (phase == 1 && q < nq && tid < grid) ? __ldcg(v.dpart + (size_t)q * grid + tid) : 0.0;
     }
+    // ||g(x_1)||_inf is taken once, at the first trial pass (S is uniform over the CTA)
+    const bool want_g1 = phase == 1 && !S.g1_done;
     float ga[8];
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
         const int i = tid + h * B;
-        ga[h] = (phase == 1 && i < n) ? fabsf(__ldcg(v.g + i)) : 0.0f;
+        ga[h] = (want_g1 && i < n) ? fabsf(__ldcg(v.g + i)) : 0.0f;
     }
     if (tid == 0) S.status = status_now;
     // sizes beyond one element per thread (fixed order per thread)
@@ -102,7 +104,7 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
     float ginf = 0.0f;
 #pragma unroll
     for (int h = 0; h < 8; ++h) ginf = fmaxf(ginf, ga[h]);
-    if (phase == 1)
+    if (want_g1)
         for (int i = tid + 8 * B; i < n; i += B) ginf = fmaxf(ginf, fabsf(__ldcg(v.g + i)));
     // FP64 is scarce: only warps holding partials reduce them
     const bool has_g = wib * 32 < W, has_d = phase == 1 && wib * 32 < grid;
@@ -118,11 +120,12 @@ __device__ void control_step(int phase, DevState* st, const Vecs& v, const FwdUn
             red[wib][kMaxTrials + q] = d;
         }
     }
+    if (want_g1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ginf = fmaxf(ginf, __shfl_xor_sync(0xffffffffu, ginf, o));
-    if (lane == 0) shf[wib] = ginf;
+        for (int o = 16; o > 0; o >>= 1) ginf = fmaxf(ginf, __shfl_xor_sync(0xffffffffu, ginf, o));
+        if (lane == 0) shf[wib] = ginf;
+    }
     __syncthreads();
-    const bool want_g1 = phase == 1 && !S.g1_done;
     if (tid < 2 * kMaxTrials) {
         const int q = tid % kMaxTrials;
         double t = 0.0;
@@ -374,8 +377,10 @@ __device__ __forceinline__ UnitRec load_unit(const UnitRec* r, bool shared) {
 // CTA's prefetch table, staged in shared memory with the unit records.
 __device__ __forceinline__ void prefetch_next_rows(const FwdArgs& a, const int64_t* s_pf, int wib, int lane) {
 #if IMRT_BWD_PREFETCH_KB > 0
-    if (a.nx_tab && lane == 0 && wib < a.nx_per_cta) {
-        const int64_t e0 = s_pf[2 * wib], n_e = s_pf[2 * wib + 1];
+    // the CTA's last warps issue them, while its first warps add the objective partials
+    const int w = wib - (kFwdThreads / 32 - a.nx_per_cta);
+    if (a.nx_tab && lane == 0 && w >= 0) {
+        const int64_t e0 = s_pf[2 * w], n_e = s_pf[2 * w + 1];
         if (n_e > 0) {
             prefetch_l2(static_cast<const char*>(a.nx_val) + e0 * a.nx_vb, n_e * a.nx_vb);
             prefetch_l2(a.nx_lo + e0, n_e * 2);
@@ -614,12 +619,13 @@ __global__ void __launch_bounds__(kFwdThreads,
             }
         }
         // x_t (the controller's trace copy) and the partials are read by the controller in this
-        // launch: the release fence before this CTA's ticket publishes them
+        // launch: published by this warp's release fence
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
             const double s = warp_sum(d2[q]);
             if (lane == 0) a.v.dpart[(size_t)q * gridDim.x + blockIdx.x] = s;
         }
+        fence_acq_rel_gpu();
     }
 
     // Rows: work units taken dynamically, longest first.
@@ -663,6 +669,7 @@ __global__ void __launch_bounds__(kFwdThreads,
             for (int i = lane; i < s_slots; i += 32) t = df_add(t, reinterpret_cast<const Df*>(lt.slots)[(size_t)i * KT + q]);
             t = warp_sum(t);
             if (lane == 0) U.obj[(size_t)q * gridDim.x + blockIdx.x] = failed ? 0.0 : df_to_double(t);
+            fence_acq_rel_gpu();
         }
     } else {
         // all units from the device-wide counter
@@ -687,15 +694,13 @@ __global__ void __launch_bounds__(kFwdThreads,
     // prefetch was measured to delay the last CTAs' streaming more than it saved)
     if (!failed) prefetch_next_rows(a, s_pf, wib, lane);
     // count finished CTAs: the last one resets the schedule and, inside a solve, runs the
-    // controller. One release fence after the barrier publishes every write of this CTA the
-    // controller reads (objective and step-length partials, x_t); the last CTA's fence after
-    // its ticket is the matching acquire.
+    // controller. Each write the controller reads was followed by a release fence of its warp
+    // (x_t and the step-length partials: warp 0 in the prologue; the CTA's objective partials:
+    // warps < KT; the device-wide schedule's group sums: their writers), ordered before the
+    // ticket by the barrier and paired with the last CTA's fence after its ticket.
     __shared__ int is_last;
     __syncthreads();
-    if (tid == 0) {
-        fence_acq_rel_gpu();
-        is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
-    }
+    if (tid == 0) is_last = atomicAdd(U.ticket, 1) == (int)gridDim.x - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
