@@ -181,6 +181,10 @@ void imrt_default_options(imrt_options* opt);
  *   opt         options (NULL => defaults); copied into the plan.
  *   out         receives the plan; NULL on failure.
  * The caller may free every input when this returns.
+ * D is checked before any layout is built: row_ptr[0] = 0, row_ptr[m] = nnz, every offset
+ * inside [0, nnz] and non-decreasing, columns in [0, n) and strictly increasing within a
+ * row, values finite; a violation returns IMRT_EINVAL naming it, and no entry of a row with
+ * bad offsets is read.
  * Errors: IMRT_EINVAL (bad sizes or CSR structure, bad options),
  * IMRT_EUNSUPPORTED (size limits: the forward pass stages x, and g in a solve, in shared
  * memory, about 8 * n * k_trials bytes, so n is limited to about 28,000 beamlets at

@@ -912,12 +912,13 @@ imrt_status plan_build(imrt_plan* p, const imrt_csr* D, const uint8_t* structure
     TRY(talloc(tlen, &len, m));
     TRY(talloc(tflags, &flags, 1));
     CK(cudaMemsetAsync(flags, 0, sizeof(int32_t), s));
-    CK(launch_row_check(row_ptr, col, val, m, n, len, flags, s));
+    CK(launch_row_check(row_ptr, col, val, m, n, nnz, len, flags, s));
     int32_t hflags = 0;
     CK(cudaMemcpyAsync(&hflags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hflags) {
-        return set_error("invalid CSR:%s%s%s%s", (hflags & 1) ? " decreasing row_ptr;" : "",
+        return set_error("invalid CSR:%s%s%s%s%s", (hflags & 1) ? " decreasing row_ptr;" : "",
+                         (hflags & 16) ? " row_ptr outside [0, nnz];" : "",
                          (hflags & 2) ? " column index out of [0, n);" : "",
                          (hflags & 4) ? " columns not strictly increasing within a row;" : "",
                          (hflags & 8) ? " non-finite value;" : ""),

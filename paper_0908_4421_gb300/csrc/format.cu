@@ -18,10 +18,11 @@ namespace {
 
 inline int blocks_for(int64_t count, int threads) { return (int)((count + threads - 1) / threads); }
 
-// Row lengths and CSR checks: column range, strictly increasing columns, finite values.
+// Row lengths and CSR checks: row offsets inside [0, nnz] and not decreasing, column range,
+// strictly increasing columns, finite values.
 __global__ void k_row_check(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                            const float* __restrict__ val, int32_t m, int32_t n, int32_t* __restrict__ len,
-                            int32_t* __restrict__ flags) {
+                            const float* __restrict__ val, int32_t m, int32_t n, int64_t nnz,
+                            int32_t* __restrict__ len, int32_t* __restrict__ flags) {
     // one warp per row: lane l reads entries l, l + 32, ... (coalesced), and each column is
     // compared with the one before it in the row (the previous lane's, or the last of the
     // previous round for lane 0)
@@ -29,8 +30,8 @@ __global__ void k_row_check(const int64_t* __restrict__ row_ptr, const int32_t* 
     if (j >= m) return;  // uniform over the warp
     const int64_t a = row_ptr[j], b = row_ptr[j + 1];
     int f = 0;
-    if (b < a) {
-        f = 1;
+    if (b < a || a < 0 || b > nnz) {  // no entry of such a row is read
+        f = b < a ? 1 : 16;
         if (lane == 0) len[j] = 0;
     } else {
         if (lane == 0) len[j] = (int32_t)(b - a);
@@ -529,8 +530,8 @@ cudaError_t set_max_dynamic_smem(K kernel) {
 }  // namespace
 
 cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
-                             int32_t* len, int32_t* flags, cudaStream_t stream) {
-    k_row_check<<<blocks_for((int64_t)m * 32, 256), 256, 0, stream>>>(row_ptr, col, val, m, n, len, flags);
+                             int64_t nnz, int32_t* len, int32_t* flags, cudaStream_t stream) {
+    k_row_check<<<blocks_for((int64_t)m * 32, 256), 256, 0, stream>>>(row_ptr, col, val, m, n, nnz, len, flags);
     return cudaGetLastError();
 }
 

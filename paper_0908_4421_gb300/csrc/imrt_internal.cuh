@@ -332,7 +332,7 @@ int fwd_group_entries(int fmt);
 
 // Setup kernels (format.cu), all on `stream`.
 cudaError_t launch_row_check(const int64_t* row_ptr, const int32_t* col, const float* val, int32_t m, int32_t n,
-                             int32_t* len, int32_t* flags, cudaStream_t stream);
+                             int64_t nnz, int32_t* len, int32_t* flags, cudaStream_t stream);
 cudaError_t launch_sigma_sort(const int32_t* len, int32_t m, int32_t m_pad, int32_t* perm, cudaStream_t stream);
 cudaError_t launch_slice_sizes(const int32_t* len, const int32_t* perm, int32_t m, int32_t n_slices, int ge,
                                int32_t* slice_len, int64_t* slice_entries, cudaStream_t stream);

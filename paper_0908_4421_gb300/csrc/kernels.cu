@@ -392,7 +392,6 @@ __device__ __forceinline__ void prefetch_next_rows(const FwdArgs& a, const int64
 // The trial-point inputs of one thread: x, g and the beamlet scales of the float4 groups
 // tid + k * kFwdThreads, k < R, loaded together; store() forms the trial points
 // x_t = max(0, x - lambda_q g) * scale, trial-interleaved, exactly as Sec. 2.2 step 2 projects.
-template <class F>
 struct TrialIn {
     static constexpr int R = 2;
     float4 x[R], g[R], s[R];
@@ -549,7 +548,7 @@ __global__ void __launch_bounds__(kFwdThreads,
     // Trial passes: x, g (and the beamlet scales) with plain 16-byte loads, all issued at once
     // after the wait, so the trial points cost one L2 round trip rather than a bulk copy
     // issued after the wait and then waited for.
-    TrialIn<F> tin;
+    TrialIn tin;
     if (mode == kFwdTrial) tin.load(a.v.x + (size_t)cur * n_pad, a.v.g, a.scale, n_pad >> 2, tid);
     // the controller's inputs (used only by the last CTA): loaded now, stored to shared memory
     // once the trial points are formed, so their latency stays off the prologue; the mapped
@@ -580,12 +579,12 @@ __global__ void __launch_bounds__(kFwdThreads,
         }
     }
     if (mode == kFwdTrial) {
-        tin.template store<KT>(xs, lamf);
+        tin.store<KT>(xs, lamf);
         // n_pad beyond the first round (more than 4 * kFwdThreads * kTrialRounds beamlets)
-        for (int i4 = tid + kFwdThreads * TrialIn<F>::R; i4 < (n_pad >> 2); i4 += kFwdThreads) {
-            TrialIn<F> t2;
+        for (int i4 = tid + kFwdThreads * TrialIn::R; i4 < (n_pad >> 2); i4 += kFwdThreads) {
+            TrialIn t2;
             t2.load_one(a.v.x + (size_t)cur * n_pad, a.v.g, a.scale, i4);
-            t2.template store_one<KT>(xs, lamf, i4);
+            t2.store_one<KT>(xs, lamf, i4);
         }
     } else if (mode == kFwdPowerNext) {
         power_next_x(a.x_src, a.n, n_pad, xs, blockIdx.x == 0 ? a.v_dst : nullptr);

@@ -257,6 +257,36 @@ def test_error_paths(tiny):
         Plan(bad.row_ptr, bad.col, val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n)
 
 
+def test_invalid_csr_offsets_and_long_rows():
+    """Malformed row offsets and unsorted columns are rejected by the CSR check with
+    IMRT_EINVAL before any other kernel reads D: an offset beyond nnz, a negative offset, and
+    two columns out of order across the first 32-entry round of a long row."""
+    bad = phantom.random_case(3, m=40, n=120, density=0.5)
+    nnz = int(bad.row_ptr[-1])
+    for mid in (nnz + 40, -5):
+        rp = bad.row_ptr.copy()
+        rp[1] = mid
+        with pytest.raises(L.ImrtError) as e:
+            Plan(rp, bad.col, bad.val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n)
+        assert e.value.status == L.IMRT_EINVAL
+        assert "row_ptr" in str(e.value)
+    lens = np.diff(bad.row_ptr)
+    k = int(np.argmax(lens >= 40))
+    assert lens[k] >= 40
+    a = int(bad.row_ptr[k])
+    for i, j in ((a + 31, a + 32), (a + 30, a + 31)):  # across the round boundary, and inside a round
+        col = bad.col.copy()
+        col[i], col[j] = col[j], col[i]
+        with pytest.raises(L.ImrtError) as e:
+            Plan(bad.row_ptr, col, bad.val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n)
+        assert e.value.status == L.IMRT_EINVAL
+        assert "strictly increasing" in str(e.value)
+    # the unmodified matrix is accepted
+    with Plan(bad.row_ptr, bad.col, bad.val, bad.mask, bad.thresholds, bad.weights, m=bad.m, n=bad.n,
+              options=Options(lambda0=1.0, max_iter=1)) as plan:
+        assert plan.info()["nnz"] == nnz
+
+
 def test_cancel_from_another_thread(tiny):
     case, lam0 = tiny
     with Plan.from_case(case, Options(lambda0=lam0, max_iter=1_000_000, delta=0.0, max_backtracks=60)) as plan:
