@@ -389,34 +389,34 @@ __device__ __forceinline__ void prefetch_next_rows(const FwdArgs& a, const int64
 #endif
 }
 
-// The trial-point inputs of one thread: x, g and the beamlet scales of the float4 groups
-// tid + k * kFwdThreads, k < R, loaded together; store() forms the trial points
-// x_t = max(0, x - lambda_q g) * scale, trial-interleaved, exactly as Sec. 2.2 step 2 projects.
+// The trial-point inputs of one thread: g and the beamlet scales of the float4 groups
+// tid + k * kFwdThreads, k < R, loaded together (x is already in shared memory); store()
+// forms the trial points x_t = max(0, x - lambda_q g) * scale, trial-interleaved, exactly as
+// Sec. 2.2 step 2 projects (for one step size in place: each thread rewrites only its own x).
 struct TrialIn {
     static constexpr int R = 2;
-    float4 x[R], g[R], s[R];
+    float4 g[R], s[R];
     int base = 0, n4 = 0;
-    __device__ __forceinline__ void load(const float* xg, const float* g_, const float* sc, int n4_, int tid) {
+    __device__ __forceinline__ void load(const float* g_, const float* sc, int n4_, int tid) {
         base = tid;
         n4 = n4_;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int i4 = tid + k * kFwdThreads;
             if (i4 < n4) {
-                x[k] = __ldcg(reinterpret_cast<const float4*>(xg) + i4);
                 g[k] = __ldcg(reinterpret_cast<const float4*>(g_) + i4);
                 s[k] = sc ? __ldg(reinterpret_cast<const float4*>(sc) + i4) : make_float4(1.0f, 1.0f, 1.0f, 1.0f);
             }
         }
     }
-    __device__ __forceinline__ void load_one(const float* xg, const float* g_, const float* sc, int i4) {
-        x[0] = __ldcg(reinterpret_cast<const float4*>(xg) + i4);
+    __device__ __forceinline__ void load_one(const float* g_, const float* sc, int i4) {
         g[0] = __ldcg(reinterpret_cast<const float4*>(g_) + i4);
         s[0] = sc ? __ldg(reinterpret_cast<const float4*>(sc) + i4) : make_float4(1.0f, 1.0f, 1.0f, 1.0f);
     }
     template <int KT>
-    __device__ __forceinline__ void put(float* xs, const float (&lamf)[KT], int k, int i4) const {
-        const float xv[4] = {x[k].x, x[k].y, x[k].z, x[k].w}, gv[4] = {g[k].x, g[k].y, g[k].z, g[k].w},
+    __device__ __forceinline__ void put(float* xs, const float* xraw, const float (&lamf)[KT], int k, int i4) const {
+        const float4 x = *reinterpret_cast<const float4*>(xraw + 4 * i4);
+        const float xv[4] = {x.x, x.y, x.z, x.w}, gv[4] = {g[k].x, g[k].y, g[k].z, g[k].w},
                     sv[4] = {s[k].x, s[k].y, s[k].z, s[k].w};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
@@ -425,14 +425,14 @@ struct TrialIn {
                 xs[(size_t)(4 * i4 + e) * KT + q] = fmaxf(0.0f, fmaf(-lamf[q], gv[e], xv[e])) * sv[e];
     }
     template <int KT>
-    __device__ __forceinline__ void store(float* xs, const float (&lamf)[KT]) const {
+    __device__ __forceinline__ void store(float* xs, const float* xraw, const float (&lamf)[KT]) const {
 #pragma unroll
         for (int k = 0; k < R; ++k)
-            if (base + k * kFwdThreads < n4) put<KT>(xs, lamf, k, base + k * kFwdThreads);
+            if (base + k * kFwdThreads < n4) put<KT>(xs, xraw, lamf, k, base + k * kFwdThreads);
     }
     template <int KT>
-    __device__ __forceinline__ void store_one(float* xs, const float (&lamf)[KT], int i4) const {
-        put<KT>(xs, lamf, 0, i4);
+    __device__ __forceinline__ void store_one(float* xs, const float* xraw, const float (&lamf)[KT], int i4) const {
+        put<KT>(xs, xraw, lamf, 0, i4);
     }
 };
 
@@ -479,7 +479,8 @@ __global__ void __launch_bounds__(kFwdThreads,
     DevState* st = a.st;
     const int mode = a.mode;
 
-    float* xs = smem;                  // n_pad * KT, trial-interleaved (then room the layout keeps)
+    float* xs = smem;                          // n_pad * KT, trial-interleaved
+    float* xr = smem + (size_t)n_pad * KT + n_pad;  // raw x (trial passes, KT > 1)
     const uint32_t bytes = (uint32_t)n_pad * 4u;
 
     const FwdUnits& U = a.u;
@@ -538,18 +539,21 @@ __global__ void __launch_bounds__(kFwdThreads,
         return;
     }
     __syncthreads();
-    if (tid == 0 && mode != kFwdTrial && mode != kFwdPowerNext) {  // x staged by the bulk-copy engine
-        const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)st->cur * n_pad;
+    // x staged in shared memory by the bulk-copy engine before the grid-dependency wait (the
+    // accepted x of a trial pass was written before the pass preceding this one started)
+    float* xraw = (mode == kFwdTrial && KT > 1) ? xr : xs;
+    if (tid == 0 && mode != kFwdPowerNext) {
+        const float* xsrc = a.x_src ? a.x_src : a.v.x + (size_t)(mode == kFwdTrial ? cur : st->cur) * n_pad;
         mbar_arrive_expect_tx(&bar, bytes);
-        bulk_g2s(xs, xsrc, bytes, &bar);
+        bulk_g2s(xraw, xsrc, bytes, &bar);
     }
     pdl_wait();  // the transposed pass before this one (g, state) is complete
     pdl_launch_dependents();
-    // Trial passes: x, g (and the beamlet scales) with plain 16-byte loads, all issued at once
-    // after the wait, so the trial points cost one L2 round trip rather than a bulk copy
-    // issued after the wait and then waited for.
+    // Trial passes: g (and the beamlet scales) with plain 16-byte loads, all issued at once after
+    // the wait: one L2 round trip, which a bulk copy issued after the wait and then waited for
+    // did not beat.
     TrialIn tin;
-    if (mode == kFwdTrial) tin.load(a.v.x + (size_t)cur * n_pad, a.v.g, a.scale, n_pad >> 2, tid);
+    if (mode == kFwdTrial) tin.load(a.v.g, a.scale, n_pad >> 2, tid);
     // the controller's inputs (used only by the last CTA): loaded now, stored to shared memory
     // once the trial points are formed, so their latency stays off the prologue; the mapped
     // cancel flag's latency is hidden behind the whole pass
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(kFwdThreads,
     }
     // Bounded waits: on expiry the CTA flags a device error, skips its work, and still
     // reports to the ticket so the controller runs and ends the solve.
-    bool bad = mode != kFwdTrial && mode != kFwdPowerNext && !mbar_wait_bounded(&bar, 0);
+    bool bad = mode != kFwdPowerNext && !mbar_wait_bounded(&bar, 0);
     bad = !mbar_wait_bounded(&bar_r, 0) || bad;
     const bool failed = __syncthreads_or(bad) != 0;
     if (failed && tid == 0) atomicExch(&st->status, (int)IMRT_ECUDA);
@@ -579,12 +583,12 @@ __global__ void __launch_bounds__(kFwdThreads,
         }
     }
     if (mode == kFwdTrial) {
-        tin.store<KT>(xs, lamf);
-        // n_pad beyond the first round (more than 4 * kFwdThreads * kTrialRounds beamlets)
+        tin.store<KT>(xs, xraw, lamf);
+        // n_pad beyond the first round (more than 4 * kFwdThreads * TrialIn::R beamlets)
         for (int i4 = tid + kFwdThreads * TrialIn::R; i4 < (n_pad >> 2); i4 += kFwdThreads) {
             TrialIn t2;
-            t2.load_one(a.v.x + (size_t)cur * n_pad, a.v.g, a.scale, i4);
-            t2.store_one<KT>(xs, lamf, i4);
+            t2.load_one(a.v.g, a.scale, i4);
+            t2.store_one<KT>(xs, xraw, lamf, i4);
         }
     } else if (mode == kFwdPowerNext) {
         power_next_x(a.x_src, a.n, n_pad, xs, blockIdx.x == 0 ? a.v_dst : nullptr);
