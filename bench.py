@@ -135,6 +135,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+class gc_paused:
+    """Python's cyclic garbage collector off inside a timed region (as timeit does): a
+    collection pass of this process's objects is not part of the library's path."""
+
+    def __enter__(self):
+        gc.collect()
+        gc.disable()
+        return self
+
+    def __exit__(self, *exc):
+        gc.enable()
+
+
 def pinned(a: np.ndarray):
     import torch
     t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
@@ -335,9 +348,7 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    gc.collect()
-    gc.disable()
-    with ClockSampler(local_rank) as clocks:
+    with gc_paused(), ClockSampler(local_rank) as clocks:
         for _ in range(args.steps):
             ev0.record(stream)
             res = plan.solve()
@@ -345,7 +356,6 @@ def main():
             ev1.synchronize()
             times.append(ev0.elapsed_time(ev1) / 1e3)
             results.append(res)
-    gc.enable()
     torch.cuda.synchronize()
     barrier()
     step_s = max_over_ranks(statistics.mean(times))
@@ -378,8 +388,6 @@ def main():
         fwd_avg_s * res.passes + bwd_avg_s * res.grad_passes, 1e-12) / 1e9
 
     # end to end through the C ABI with host buffers: create from pinned host CSR, solve, read x and z back
-    # (as timeit does, the cyclic garbage collector is off inside the timed regions: a
-    # collection pass of this process's objects is not part of the library's path)
     e2e_times, create_times = [], []
     h_rp, t_rp = pinned(case.row_ptr)
     h_col, t_col = pinned(case.col)
@@ -394,17 +402,15 @@ def main():
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         barrier()
-        gc.collect()
-        gc.disable()
-        t0 = time.perf_counter()
-        with Plan(h_rp, h_col, h_val, h_mask, case.thresholds, case.weights, m=case.m, n=case.n,
-                  options=e2e_opts) as p2:
-            dc = time.perf_counter() - t0  # plan_create returns once the plan is built
-            r2 = p2.solve()
-            p2.get_x(x_out)
-            p2.dose(x_out, z_out)
-        dt = time.perf_counter() - t0
-        gc.enable()
+        with gc_paused():
+            t0 = time.perf_counter()
+            with Plan(h_rp, h_col, h_val, h_mask, case.thresholds, case.weights, m=case.m, n=case.n,
+                      options=e2e_opts) as p2:
+                dc = time.perf_counter() - t0  # plan_create returns once the plan is built
+                r2 = p2.solve()
+                p2.get_x(x_out)
+                p2.dose(x_out, z_out)
+            dt = time.perf_counter() - t0
         if i > 0:  # the first one also pays one-time CUDA module loading
             e2e_times.append(dt)
             create_times.append(dc)

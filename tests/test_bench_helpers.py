@@ -75,3 +75,20 @@ def test_both_arms_print_the_same_config():
     a = bench.common_config("tiny-40x40x30-5mm-5beam", case, 200, 1)
     b = bench.common_config("tiny-40x40x30-5mm-5beam", case, 200, 1)
     assert a == b and set(a) >= {"workload", "m", "n", "nnz", "l2", "parallelism"}
+
+
+def test_gc_paused_restores_the_collector():
+    """The timed regions run with the cyclic garbage collector off and turn it back on, also
+    when the region raises."""
+    import gc
+
+    assert gc.isenabled()
+    with bench.gc_paused():
+        assert not gc.isenabled()
+    assert gc.isenabled()
+    try:
+        with bench.gc_paused():
+            raise RuntimeError("inside the timed region")
+    except RuntimeError:
+        pass
+    assert gc.isenabled()
