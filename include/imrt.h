@@ -107,7 +107,10 @@ typedef struct {
     int32_t precision;      /* imrt_precision of the stored D; default IMRT_FP32 */
     int32_t k_trials;       /* Armijo step sizes evaluated per pass over D: 1, 2, 4 or 8; default 1 */
     int32_t mode;           /* imrt_mode; default IMRT_MODE_GRAPH */
-    int32_t profile;        /* 1: time every forward and transposed-product launch with CUDA events */
+    int32_t profile;        /* 1 (with IMRT_MODE_HOST): time every forward and transposed-product launch
+                               with CUDA events; a 30 us one-thread delay kernel ahead of the first timed
+                               launch after each host synchronisation keeps the host's launch latency
+                               out of the intervals (counted in imrt_result.launches) */
     int32_t trace;          /* 1: record G, lambda and backtracks per iteration; 2: also every x_k */
     int32_t polish_iter;    /* reduced precision: the last polish_iter of max_iter iterations use the FP32 copy
                                (more when the reduced phase stops early: the polish gets the rest of
